@@ -1,0 +1,142 @@
+"""Model descriptions and workload recipes for Coherent Fusion pose scoring.
+
+A model description is a plain dict; the CUDA path converts it to the C
+struct ``fusion_model_desc`` and the oracle reads it directly.  Nothing here
+computes any part of the method.
+
+Architecture readings (the paper gives the components, Fig. 1 and Tables
+I-V, but defers voxel sizing, atom propagation and layer equations to the
+earlier FAST work):
+
+* 3D-CNN: same-padded convolutions with bias and ReLU, optional residual
+  blocks y = x + ReLU(conv(x)), a 2^3 max-pool and one dense layer + ReLU
+  (Section 3.3.1, Table III; no batch norm).
+* SG-CNN: PotentialNet-style gated graph convolution (Section 3.3.1, Table II):
+  GRU-updated message passing over covalent and non-covalent edges found by
+  distance cutoff, optional per-node gate between stages, and a sum over
+  ligand atoms.
+* Fusion head: concatenated latents through dense layers with SELU
+  (Section 3.3.3, Table V); dropout is the identity at inference.
+"""
+
+from __future__ import annotations
+
+import copy
+
+EDGE_COV = 1
+EDGE_NC = 2
+
+N_FEAT = 19
+
+
+def _conv(c_in, c_out, k, stride=1, residual=0):
+    return dict(c_in=c_in, c_out=c_out, k=k, stride=stride, residual=residual)
+
+
+# Small single-pose model: 24^3 grid, conv 19->32 (5^3), one residual 32->32
+# (5^3) block, 2^3 max-pool, dense 64; two gated graph steps (hidden 32) over
+# both edge types, ligand sum-pool to 64; head 128 -> 64 -> 1.
+FUSION_TINY = dict(
+    name="fusion-24grid-c32",
+    n_feat=N_FEAT,
+    grid_n=24, grid_h=1.0, sigma=1.0, support=3,
+    conv=[_conv(19, 32, 5), _conv(32, 32, 5, residual=1)],
+    pool=2,
+    cnn_dense=64,
+    sg_hidden=32,
+    sg_stages=[dict(steps=2, edges=EDGE_COV | EDGE_NC)],
+    sg_gate=0,
+    sg_gather="linear",
+    sg_gather_width=64,
+    cut_cov=1.6, cut_nc=4.5,
+    head=[64, 1],
+    dtype="f32",
+)
+
+# Full-size model: 48^3 x 19 grid at 1 A; conv 19->64 (7^3), two residual
+# 64-channel 7^3 blocks, conv 64->128 (5^3, stride 2), 2^3 pool, dense 256;
+# 3 covalent gated steps, per-node gate, 3 covalent+non-covalent steps at
+# hidden 64, gated ligand pooling to 128; head 384 -> 256 -> 64 -> 1.
+FUSION_FULL = dict(
+    name="fusion-48grid-c64",
+    n_feat=N_FEAT,
+    grid_n=48, grid_h=1.0, sigma=1.0, support=3,
+    conv=[_conv(19, 64, 7), _conv(64, 64, 7, residual=1),
+          _conv(64, 64, 7, residual=1), _conv(64, 128, 5, stride=2)],
+    pool=2,
+    cnn_dense=256,
+    sg_hidden=64,
+    sg_stages=[dict(steps=3, edges=EDGE_COV), dict(steps=3, edges=EDGE_COV | EDGE_NC)],
+    sg_gate=1,
+    sg_gather="gated",
+    sg_gather_width=128,
+    cut_cov=1.6, cut_nc=4.5,
+    head=[256, 64, 1],
+    dtype="f32",
+)
+
+# Same structure as the full-size model at a size the oracle finishes in a
+# second: a 20^3 grid (not a multiple of any tile edge), 3^3 kernels, a
+# strided conv, a stage gate and gated gather.  Used for ragged-tail parity.
+FUSION_RAGGED = dict(
+    name="fusion-20grid-ragged",
+    n_feat=N_FEAT,
+    grid_n=20, grid_h=1.0, sigma=1.0, support=3,
+    conv=[_conv(19, 32, 3), _conv(32, 32, 3, residual=1), _conv(32, 64, 3, stride=2)],
+    pool=2,
+    cnn_dense=32,
+    sg_hidden=32,
+    sg_stages=[dict(steps=2, edges=EDGE_COV), dict(steps=1, edges=EDGE_COV | EDGE_NC)],
+    sg_gate=1,
+    sg_gather="gated",
+    sg_gather_width=24,
+    cut_cov=1.6, cut_nc=4.5,
+    head=[32, 16, 1],
+    dtype="f32",
+)
+
+# The architecture of the final models in Tables II, III and V: 3D-CNN with
+# 32 then 64 filters, 5^3 then 3^3 kernels, residual option 2, dense 128;
+# SG-CNN covalent K=6 at 2.24 A, non-covalent K=3 at 5.22 A, gather width 128;
+# four SELU fusion layers.  Grid 48^3 at 1 A.
+FUSION_PAPER = dict(
+    name="fusion-paper-final",
+    n_feat=N_FEAT,
+    grid_n=48, grid_h=1.0, sigma=1.0, support=3,
+    conv=[_conv(19, 32, 5), _conv(32, 32, 5, residual=1),
+          _conv(32, 64, 3, stride=2), _conv(64, 64, 3, residual=1)],
+    pool=2,
+    cnn_dense=128,
+    sg_hidden=64,
+    sg_stages=[dict(steps=6, edges=EDGE_COV), dict(steps=3, edges=EDGE_COV | EDGE_NC)],
+    sg_gate=1,
+    sg_gather="gated",
+    sg_gather_width=128,
+    cut_cov=2.24, cut_nc=5.22,
+    head=[128, 64, 24, 1],
+    dtype="f32",
+)
+
+MODELS = {m["name"]: m for m in (FUSION_TINY, FUSION_FULL, FUSION_RAGGED, FUSION_PAPER)}
+
+
+def model(name: str, dtype: str | None = None) -> dict:
+    """A deep copy of a preset, optionally with another compute dtype."""
+    d = copy.deepcopy(MODELS[name])
+    if dtype is not None:
+        d["dtype"] = dtype
+    return d
+
+
+# Workload recipes.  Each pose p is generated from its own seed; atom counts
+# are drawn from that pose's generator inside the stated ranges.
+WORKLOADS = {
+    # one pose, seed 0: 24 ligand atoms (2 rings) and 200 pocket atoms
+    "pose1-lig24-pocket200": dict(seeds=[0], n_lig=(24, 24), n_pocket=(200, 200), rings=2),
+    # batch of 64 poses, seeds 1..64, ligands 20-50, pockets 300-600
+    "batch64-lig20to50-pocket300to600": dict(seeds=list(range(1, 65)), n_lig=(20, 50),
+                                             n_pocket=(300, 600), rings=None),
+    # batch of 256 poses, ligands 15-60, pockets 250-800
+    "batch256-lig15to60-pocket250to800": dict(seeds=list(range(1001, 1257)), n_lig=(15, 60),
+                                              n_pocket=(250, 800), rings=None),
+}
