@@ -1,0 +1,171 @@
+/*
+ * fusion.h - C ABI of the GB300 Coherent Fusion pose-scoring library.
+ *
+ * The library scores docked protein-ligand poses with a Coherent Fusion model
+ * (a 3D-CNN over a voxel grid and a spatial-graph CNN, fused by dense layers;
+ * Section 2.2, Fig. 1 and Section 3.3 of "High-Throughput Virtual Screening of
+ * Small Molecule Inhibitors for SARS-CoV-2 Protein Targets with Deep Fusion
+ * Models").  The output of each pose is a predicted binding affinity in pK
+ * units (Eq. 1).  Every step of the scoring path runs in CUDA kernels compiled
+ * for sm_103a; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *  - Return value: FUSION_OK (0) or a negative FUSION_E* code; the message of
+ *    the last failure on the calling thread is in fusion_last_error().
+ *  - The library never keeps a caller pointer after a call returns.
+ *  - On error, outputs are left untouched and the model stays usable.
+ */
+#ifndef FUSION_H
+#define FUSION_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define FUSION_OK            0
+#define FUSION_EINVAL       -1  /* bad argument, descriptor or pose (NaN/Inf coordinate, n_lig outside [1, N], N above capacity) */
+#define FUSION_EWEIGHTS     -2  /* weights blob length differs from fusion_weights_bytes(desc) */
+#define FUSION_ENOMEM       -3  /* device or pinned-host allocation failed */
+#define FUSION_ECAPACITY    -4  /* a device capacity flag was raised (edge capacity of a pose exceeded) */
+#define FUSION_ECUDA        -5  /* a CUDA runtime call failed */
+#define FUSION_ETIMEOUT     -6  /* a bounded device wait ran out */
+#define FUSION_EUNSUPPORTED -7  /* descriptor valid but not supported by this build (dtype or shape) */
+
+/* Compute dtypes of the CNN contractions (density, distances, pooling and head stay FP32). */
+#define FUSION_F32  0
+#define FUSION_BF16 1
+#define FUSION_FP8  2
+
+/* Edge-type bits of a graph-convolution stage (Section 1, Table II: covalent and non-covalent edges). */
+#define FUSION_EDGE_COV 1
+#define FUSION_EDGE_NC  2
+
+/* Ligand gather kinds (Section 3.3.1, PotentialNet gather). */
+#define FUSION_GATHER_LINEAR 0   /* sum_i (W h_i + b) over ligand atoms i */
+#define FUSION_GATHER_GATED  1   /* sum_i sigmoid(W_g [h_i, x_i] + b_g) * (W_o h_i + b_o) */
+
+#define FUSION_MAX_CONV   8
+#define FUSION_MAX_STAGES 2
+#define FUSION_MAX_HEAD   6
+
+/* One 3D convolution (Section 3.3.1, Table III): same padding k/2, bias, ReLU.
+ * residual != 0: y = x + ReLU(conv(x)) (needs c_in == c_out and stride 1). */
+typedef struct {
+    int32_t c_in, c_out, k, stride, residual;
+} fusion_conv_desc;
+
+/* Model description.  Layer widths and kernel sizes follow the paper's
+ * hyper-parameter tables (Tables I-III, V); all fields are plain values. */
+typedef struct {
+    int32_t n_feat;            /* atom features per atom = grid channels; must be 19 */
+    int32_t grid_n;            /* voxels per grid side (4..96) */
+    float   grid_h;            /* voxel edge, Angstrom (> 0) */
+    float   sigma;             /* Gaussian width of an atom's density, Angstrom (> 0) */
+    int32_t support;           /* k: an atom reaches voxels within +-k of its own voxel (1..5) */
+    int32_t n_conv;            /* number of conv layers (1..FUSION_MAX_CONV) */
+    fusion_conv_desc conv[FUSION_MAX_CONV];
+    int32_t pool;              /* 2: 2^3 max-pool stride 2 after the convs; 0 or 1: none */
+    int32_t cnn_dense;         /* width of the CNN dense layer (ReLU) */
+    int32_t sg_hidden;         /* H: node-state width (32 or 64) */
+    int32_t sg_n_stages;       /* graph-convolution stages (1 or 2) */
+    int32_t sg_steps[FUSION_MAX_STAGES];  /* GRU steps per stage (0..16) */
+    int32_t sg_edges[FUSION_MAX_STAGES];  /* FUSION_EDGE_* bits used by each stage */
+    int32_t sg_gate;           /* 1: per-node gate between stage 0 and stage 1 */
+    int32_t sg_gather;         /* FUSION_GATHER_* */
+    int32_t sg_gather_width;   /* G: width of the SG latent (<= 256) */
+    float   cut_cov;           /* covalent cutoff, Angstrom */
+    float   cut_nc;            /* non-covalent cutoff, Angstrom (> cut_cov) */
+    int32_t n_head;            /* fusion (head) layers (1..FUSION_MAX_HEAD) */
+    int32_t head[FUSION_MAX_HEAD];  /* output widths; the last must be 1 */
+    int32_t dtype;             /* FUSION_F32 / FUSION_BF16 / FUSION_FP8 */
+    int32_t max_poses;         /* batch capacity of one fusion_score call */
+    int32_t max_atoms;         /* atom capacity of one pose (<= 4096) */
+    int32_t max_degree;        /* edge capacity per atom and edge type (mean over a pose) */
+    int32_t keep_stages;       /* 1: keep every intermediate for fusion_fetch_stage (more memory) */
+} fusion_model_desc;
+
+/* A batch of poses in packed structure-of-arrays form.  Ligand atoms come
+ * first in each pose.  Caller-owned, read-only during the call. */
+typedef struct {
+    int32_t        n_poses;
+    const int32_t *atom_off;   /* [n_poses + 1]: atoms of pose p are [atom_off[p], atom_off[p+1]); atom_off[0] == 0 */
+    const int32_t *n_lig;      /* [n_poses]: ligand atoms of pose p are its first n_lig[p] atoms */
+    const float   *xyz;        /* [atom_off[n_poses]][3] float32 coordinates, Angstrom */
+    const float   *feat;       /* [atom_off[n_poses]][19] float32 atom features */
+    int32_t        on_device;  /* 0: host pointers (copied in); 1: device pointers valid on the model's stream */
+} fusion_poses;
+
+typedef struct fusion_model fusion_model;
+
+/* Bytes of the weights blob for `desc`: every tensor row-major float32
+ * little-endian, no header, in this order (PyTorch shape conventions):
+ *   per conv i: W [c_out][c_in][k][k][k], b [c_out]
+ *   CNN dense: W [cnn_dense][C*S*S*S] (input in (C, D, H, W) flatten order of the pooled map), b
+ *   per stage s: per edge type present (covalent first): W_e [H][H], b_e [H];
+ *                GRU W_ih [3H][H], W_hh [3H][H], b_ih [3H], b_hh [3H] (gate rows reset, update, new);
+ *                if sg_gate and s is not the last stage: W_i [H][2H], b_i [H], W_j [H][H], b_j [H]
+ *   gather: gated: W_g [G][2H], b_g [G], W_o [G][H], b_o [G]; linear: W [G][H], b [G]
+ *   per head layer l: W [out][in], b [out]  (in = cnn_dense + G for l = 0)
+ * Returns 0 if the descriptor is invalid. */
+size_t fusion_weights_bytes(const fusion_model_desc *desc);
+
+/* Create a model on the current CUDA device.  Copies and reformats the
+ * weights to device memory and allocates the workspace for max_poses poses of
+ * max_atoms atoms.  `cuda_stream` is a cudaStream_t the model launches on
+ * (NULL: the model creates and owns a non-blocking stream).  `*out` receives
+ * the model (owned by the library until fusion_destroy). */
+int fusion_create(const fusion_model_desc *desc, const void *weights, size_t weights_bytes,
+                  void *cuda_stream, fusion_model **out);
+
+/* Score `n_poses` poses (Section 4.2: each pose gets a predicted affinity):
+ * voxelize, 3D-CNN, radius graph, gated graph convolution, ligand gather and
+ * fusion head.  `out_affinity` is [n_poses] float32: a host pointer when
+ * poses->on_device == 0, a device pointer when 1.  Returns after the results
+ * are written (synchronous on the model's stream).  n_poses == 0 is a no-op. */
+int fusion_score(fusion_model *m, const fusion_poses *poses, int32_t n_poses, float *out_affinity);
+
+/* Free the model and everything it allocated.  NULL-safe. */
+void fusion_destroy(fusion_model *m);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *fusion_last_error(void);
+
+/* ---- diagnostics: intermediate results of the last fusion_score call ---- */
+
+#define FUSION_STAGE_ORIGIN      1   /* float[3] grid origin of pose `index` */
+#define FUSION_STAGE_GRID        2   /* float[n][n][n][19] voxel grid of pose `index` (z, y, x, c) */
+#define FUSION_STAGE_CONV        3   /* float[S][S][S][C] output of conv layer (index >> 16) for pose (index & 0xffff); needs keep_stages */
+#define FUSION_STAGE_POOL        4   /* float[S][S][S][C] pooled map of pose `index` */
+#define FUSION_STAGE_CNN_LATENT  5   /* float[cnn_dense] of pose `index` */
+#define FUSION_STAGE_EDGES_COV   6   /* int32 row_ptr[N+1] then col[E], local atom indices, of pose `index` */
+#define FUSION_STAGE_EDGES_NC    7   /* same for non-covalent edges */
+#define FUSION_STAGE_SG_STATE    8   /* float[N][H] final node states of pose `index` */
+#define FUSION_STAGE_SG_LATENT   9   /* float[G] of pose `index` */
+#define FUSION_STAGE_AFFINITY   10   /* float[n_poses] */
+
+/* Bytes that fusion_fetch_stage would write (negative status on error). */
+int64_t fusion_stage_bytes(fusion_model *m, int32_t stage, int32_t index);
+
+/* Copy an intermediate of the last fusion_score call into the host buffer
+ * `dst` of `bytes` bytes (must be >= fusion_stage_bytes). */
+int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst, size_t bytes);
+
+/* Device time in milliseconds of each kernel group of the last fusion_score
+ * call, measured with CUDA events on the model's stream.  Index:
+ *   0 pose prep (validation, grid origin, per-atom weights)   1 voxelize
+ *   2..9 conv layer 0..7                                      10 max-pool
+ *   11 CNN dense                                              12 radius graph
+ *   13 graph-convolution steps                                14 ligand gather
+ *   15 fusion head
+ * Entries of absent layers are 0.  `n` entries are written (n <= 16). */
+int fusion_last_timings(fusion_model *m, float *out, int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FUSION_H */

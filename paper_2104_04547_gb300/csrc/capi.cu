@@ -1,0 +1,831 @@
+// C ABI of the Coherent Fusion scoring library: descriptor validation,
+// weights-blob parsing and reformatting, device workspace, and the launch
+// sequence of one scoring call (Fig. 1: voxel grid -> 3D-CNN and spatial graph
+// -> SG-CNN, fused by dense layers into an affinity, Eq. 1).
+#include "fusion_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace fusion;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? FUSION_ENOMEM : FUSION_ECUDA,            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+struct Shape {
+    int c, n;
+};
+
+// Spatial side and channels after the conv stack (and the pool if present).
+Shape conv_out(const fusion_model_desc &d, int upto) {
+    Shape s{d.n_feat, d.grid_n};
+    for (int i = 0; i < upto; ++i) {
+        const fusion_conv_desc &c = d.conv[i];
+        s.n = (s.n + 2 * (c.k / 2) - c.k) / c.stride + 1;
+        s.c = c.c_out;
+    }
+    return s;
+}
+
+Shape cnn_final(const fusion_model_desc &d) {
+    Shape s = conv_out(d, d.n_conv);
+    if (d.pool > 1) s.n /= d.pool;
+    return s;
+}
+
+bool check_desc(const fusion_model_desc *d, std::string *why) {
+#define REQ(cond, msg)             \
+    do {                           \
+        if (!(cond)) {             \
+            *why = msg;            \
+            return false;          \
+        }                          \
+    } while (0)
+    REQ(d, "descriptor is NULL");
+    REQ(d->n_feat == kFeat, "n_feat must be 19");
+    REQ(d->grid_n >= 4 && d->grid_n <= 96, "grid_n must be in [4, 96]");
+    REQ(std::isfinite(d->grid_h) && d->grid_h > 0.f, "grid_h must be > 0");
+    REQ(std::isfinite(d->sigma) && d->sigma > 0.f, "sigma must be > 0");
+    REQ(d->support >= 1 && d->support <= 5, "support must be in [1, 5]");
+    REQ(d->n_conv >= 1 && d->n_conv <= FUSION_MAX_CONV, "n_conv must be in [1, 8]");
+    int c = kFeat, n = d->grid_n;
+    for (int i = 0; i < d->n_conv; ++i) {
+        const fusion_conv_desc &cv = d->conv[i];
+        REQ(cv.c_in == c, "conv c_in must equal the previous layer's channels (19 for the first)");
+        REQ(cv.c_out >= 32 && cv.c_out <= 256 && cv.c_out % 32 == 0, "conv c_out must be a multiple of 32 in [32, 256]");
+        REQ(cv.k >= 1 && cv.k <= 9 && (cv.k & 1), "conv k must be odd in [1, 9]");
+        REQ(cv.stride == 1 || cv.stride == 2, "conv stride must be 1 or 2");
+        REQ(!cv.residual || (cv.c_in == cv.c_out && cv.stride == 1), "residual conv needs c_in == c_out and stride 1");
+        n = (n + 2 * (cv.k / 2) - cv.k) / cv.stride + 1;
+        REQ(n >= 1, "conv stack shrinks the grid to nothing");
+        c = cv.c_out;
+    }
+    REQ(d->pool == 0 || d->pool == 1 || d->pool == 2, "pool must be 0, 1 or 2");
+    if (d->pool == 2) REQ(n >= 2, "grid too small to pool");
+    REQ(d->cnn_dense >= 1 && d->cnn_dense <= 512, "cnn_dense must be in [1, 512]");
+    REQ(d->sg_hidden == 32 || d->sg_hidden == 64, "sg_hidden must be 32 or 64");
+    REQ(d->sg_n_stages == 1 || d->sg_n_stages == 2, "sg_n_stages must be 1 or 2");
+    for (int s = 0; s < d->sg_n_stages; ++s) {
+        REQ(d->sg_steps[s] >= 0 && d->sg_steps[s] <= 16, "sg_steps must be in [0, 16]");
+        REQ(d->sg_edges[s] >= 1 && d->sg_edges[s] <= 3, "sg_edges must be a non-empty FUSION_EDGE_* mask");
+    }
+    REQ(d->sg_gate == 0 || d->sg_gate == 1, "sg_gate must be 0 or 1");
+    REQ(d->sg_gather == FUSION_GATHER_LINEAR || d->sg_gather == FUSION_GATHER_GATED, "bad sg_gather");
+    REQ(d->sg_gather_width >= 1 && d->sg_gather_width <= 256, "sg_gather_width must be in [1, 256]");
+    REQ(d->cnn_dense + d->sg_gather_width <= 512, "cnn_dense + sg_gather_width must be <= 512");
+    REQ(std::isfinite(d->cut_cov) && std::isfinite(d->cut_nc) && d->cut_cov > 0.f && d->cut_nc > d->cut_cov,
+        "cutoffs must satisfy 0 < cut_cov < cut_nc");
+    REQ(d->n_head >= 1 && d->n_head <= FUSION_MAX_HEAD, "n_head must be in [1, 6]");
+    for (int l = 0; l < d->n_head; ++l) REQ(d->head[l] >= 1 && d->head[l] <= 512, "head widths must be in [1, 512]");
+    REQ(d->head[d->n_head - 1] == 1, "the last head layer must have width 1");
+    REQ(d->dtype == FUSION_F32 || d->dtype == FUSION_BF16 || d->dtype == FUSION_FP8, "bad dtype");
+    REQ(d->max_poses >= 1 && d->max_poses <= 65535, "max_poses must be in [1, 65535]");
+    REQ(d->max_atoms >= 1 && d->max_atoms <= 4096, "max_atoms must be in [1, 4096]");
+    REQ(d->max_degree >= 1 && d->max_degree <= 1024, "max_degree must be in [1, 1024]");
+    const Shape f = cnn_final(*d);
+    REQ(((long long)f.c * f.n * f.n * f.n) % 8 == 0, "flattened CNN width must be a multiple of 8");
+    return true;
+#undef REQ
+}
+
+struct TensorSpec {
+    std::string name;
+    size_t count;
+};
+
+// Tensors of the weights blob in order (the order the header documents).
+std::vector<TensorSpec> blob_layout(const fusion_model_desc &d) {
+    std::vector<TensorSpec> L;
+    for (int i = 0; i < d.n_conv; ++i) {
+        const fusion_conv_desc &c = d.conv[i];
+        L.push_back({"conv" + std::to_string(i) + ".w", (size_t)c.c_out * c.c_in * c.k * c.k * c.k});
+        L.push_back({"conv" + std::to_string(i) + ".b", (size_t)c.c_out});
+    }
+    const Shape f = cnn_final(d);
+    const size_t flat = (size_t)f.c * f.n * f.n * f.n;
+    L.push_back({"cnn_dense.w", (size_t)d.cnn_dense * flat});
+    L.push_back({"cnn_dense.b", (size_t)d.cnn_dense});
+    const size_t H = d.sg_hidden;
+    for (int s = 0; s < d.sg_n_stages; ++s) {
+        const std::string p = "sg" + std::to_string(s);
+        if (d.sg_edges[s] & FUSION_EDGE_COV) {
+            L.push_back({p + ".cov.w", H * H});
+            L.push_back({p + ".cov.b", H});
+        }
+        if (d.sg_edges[s] & FUSION_EDGE_NC) {
+            L.push_back({p + ".nc.w", H * H});
+            L.push_back({p + ".nc.b", H});
+        }
+        L.push_back({p + ".gru.w_ih", 3 * H * H});
+        L.push_back({p + ".gru.w_hh", 3 * H * H});
+        L.push_back({p + ".gru.b_ih", 3 * H});
+        L.push_back({p + ".gru.b_hh", 3 * H});
+        if (d.sg_gate && s + 1 < d.sg_n_stages) {
+            L.push_back({p + ".gate.wi", H * 2 * H});
+            L.push_back({p + ".gate.bi", H});
+            L.push_back({p + ".gate.wj", H * H});
+            L.push_back({p + ".gate.bj", H});
+        }
+    }
+    const size_t G = d.sg_gather_width;
+    if (d.sg_gather == FUSION_GATHER_GATED) {
+        L.push_back({"gather.wg", G * 2 * H});
+        L.push_back({"gather.bg", G});
+        L.push_back({"gather.wo", G * H});
+        L.push_back({"gather.bo", G});
+    } else {
+        L.push_back({"gather.w", G * H});
+        L.push_back({"gather.b", G});
+    }
+    size_t fin = d.cnn_dense + G;
+    for (int l = 0; l < d.n_head; ++l) {
+        L.push_back({"head" + std::to_string(l) + ".w", (size_t)d.head[l] * fin});
+        L.push_back({"head" + std::to_string(l) + ".b", (size_t)d.head[l]});
+        fin = d.head[l];
+    }
+    return L;
+}
+
+constexpr int kGridCxF32 = 24;   // FP32 grid channels (19 padded for 8-channel K steps)
+
+}  // namespace
+
+struct fusion_model {
+    fusion_model_desc d{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void *> allocs;
+    std::vector<void *> host_allocs;
+
+    // weights (device)
+    struct ConvW {
+        float *w = nullptr, *b = nullptr;
+        int cx_in = 0, n_in = 0, n_out = 0;
+    } conv[FUSION_MAX_CONV];
+    float *dense_w = nullptr, *dense_b = nullptr;
+    int pool_n = 0, pool_c = 0, flat = 0, splits = 1;
+    float *we_t[FUSION_MAX_STAGES][2] = {}, *be[FUSION_MAX_STAGES][2] = {};
+    float *wih_t[FUSION_MAX_STAGES] = {}, *whh_t[FUSION_MAX_STAGES] = {}, *bih[FUSION_MAX_STAGES] = {}, *bhh[FUSION_MAX_STAGES] = {};
+    float *gi_t = nullptr, *gbi = nullptr, *gj_t = nullptr, *gbj = nullptr;
+    float *gat_wg_t = nullptr, *gat_bg = nullptr, *gat_wo_t = nullptr, *gat_bo = nullptr;
+    float *head_wt[FUSION_MAX_HEAD] = {}, *head_b[FUSION_MAX_HEAD] = {};
+
+    // workspace (device)
+    int32_t *in_off = nullptr, *in_nlig = nullptr;
+    float *in_xyz = nullptr, *in_feat = nullptr;
+    float *origin = nullptr;
+    int4 *atom_vox = nullptr;
+    float *atom_w = nullptr;
+    void *grid = nullptr;
+    int grid_cx = kGridCxF32;
+    float *act[FUSION_MAX_CONV] = {};
+    float *pool_out = nullptr, *dense_part = nullptr, *cnn_lat = nullptr;
+    int32_t *e_beg[2] = {}, *e_deg[2] = {}, *e_col[2] = {};
+    float *hbuf[2] = {}, *Tbuf[2][2] = {}, *xin = nullptr, *sg_lat = nullptr, *aff = nullptr;
+    unsigned *err = nullptr;
+
+    // pinned host staging
+    int32_t *h_off = nullptr;
+    unsigned *h_err = nullptr;
+    float *h_aff = nullptr;
+
+    cudaEvent_t ev[18] = {};
+
+    // last call
+    int last_B = 0;
+    std::vector<int32_t> last_off, last_nlig;
+    const float *last_conv_out[FUSION_MAX_CONV] = {};
+    const float *last_h = nullptr;
+    float last_ms[16] = {};
+    int ev_map[16] = {};
+};
+
+namespace {
+
+template <typename T>
+int dalloc(fusion_model *m, T **p, size_t count) {
+    void *q = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FUSION_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                       " bytes failed: " + cudaGetErrorString(e));
+    }
+    m->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return FUSION_OK;
+}
+
+template <typename T>
+int halloc(fusion_model *m, T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMallocHost(&q, (count ? count : 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FUSION_ENOMEM, std::string("cudaMallocHost failed: ") + cudaGetErrorString(e));
+    }
+    m->host_allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return FUSION_OK;
+}
+
+int upload(fusion_model *m, float **dst, const std::vector<float> &src) {
+    int rc = dalloc(m, dst, src.size());
+    if (rc) return rc;
+    CU(cudaMemcpy(*dst, src.data(), src.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return FUSION_OK;
+}
+
+std::vector<float> transpose(const float *w, int rows, int cols) {   // [rows][cols] -> [cols][rows]
+    std::vector<float> t((size_t)rows * cols);
+    for (int r = 0; r < rows; ++r)
+        for (int c = 0; c < cols; ++c) t[(size_t)c * rows + r] = w[(size_t)r * cols + c];
+    return t;
+}
+
+#define RC(x)                 \
+    do {                      \
+        int rc_ = (x);        \
+        if (rc_) return rc_;  \
+    } while (0)
+
+int load_weights(fusion_model *m, const float *blob) {
+    const fusion_model_desc &d = m->d;
+    const std::vector<TensorSpec> L = blob_layout(d);
+    size_t off = 0;
+    auto next = [&](const char *expect_suffix) -> const float * {
+        (void)expect_suffix;
+        return blob + off;
+    };
+    size_t li = 0;
+    auto take = [&]() -> const float * {
+        const float *p = next(nullptr);
+        off += L[li].count;
+        ++li;
+        return p;
+    };
+    // convs: [co][ci][k^3] -> [k^3][cx_in][co]
+    for (int i = 0; i < d.n_conv; ++i) {
+        const fusion_conv_desc &c = d.conv[i];
+        const int k3 = c.k * c.k * c.k;
+        const int cx = (i == 0) ? m->grid_cx : c.c_in;
+        const float *w = take();
+        const float *b = take();
+        std::vector<float> t((size_t)k3 * cx * c.c_out, 0.f);
+        for (int o = 0; o < c.c_out; ++o)
+            for (int ci = 0; ci < c.c_in; ++ci)
+                for (int q = 0; q < k3; ++q) t[((size_t)q * cx + ci) * c.c_out + o] = w[((size_t)o * c.c_in + ci) * k3 + q];
+        RC(upload(m, &m->conv[i].w, t));
+        RC(upload(m, &m->conv[i].b, std::vector<float>(b, b + c.c_out)));
+        m->conv[i].cx_in = cx;
+    }
+    // dense: input index c*S^3 + sp  ->  sp*C + c
+    {
+        const Shape f = cnn_final(d);
+        const size_t S3 = (size_t)f.n * f.n * f.n;
+        const float *w = take();
+        const float *b = take();
+        std::vector<float> t((size_t)d.cnn_dense * m->flat);
+        for (int o = 0; o < d.cnn_dense; ++o)
+            for (int c = 0; c < f.c; ++c)
+                for (size_t sp = 0; sp < S3; ++sp)
+                    t[(size_t)o * m->flat + sp * f.c + c] = w[(size_t)o * m->flat + (size_t)c * S3 + sp];
+        RC(upload(m, &m->dense_w, t));
+        RC(upload(m, &m->dense_b, std::vector<float>(b, b + d.cnn_dense)));
+    }
+    const int H = d.sg_hidden;
+    for (int s = 0; s < d.sg_n_stages; ++s) {
+        for (int e = 0; e < 2; ++e) {
+            if (!(d.sg_edges[s] & (1 << e))) continue;
+            const float *w = take();
+            const float *b = take();
+            RC(upload(m, &m->we_t[s][e], transpose(w, H, H)));
+            RC(upload(m, &m->be[s][e], std::vector<float>(b, b + H)));
+        }
+        const float *wih = take();
+        const float *whh = take();
+        const float *bih = take();
+        const float *bhh = take();
+        RC(upload(m, &m->wih_t[s], transpose(wih, 3 * H, H)));
+        RC(upload(m, &m->whh_t[s], transpose(whh, 3 * H, H)));
+        RC(upload(m, &m->bih[s], std::vector<float>(bih, bih + 3 * H)));
+        RC(upload(m, &m->bhh[s], std::vector<float>(bhh, bhh + 3 * H)));
+        if (d.sg_gate && s + 1 < d.sg_n_stages) {
+            const float *wi = take();
+            const float *bi = take();
+            const float *wj = take();
+            const float *bj = take();
+            RC(upload(m, &m->gi_t, transpose(wi, H, 2 * H)));
+            RC(upload(m, &m->gbi, std::vector<float>(bi, bi + H)));
+            RC(upload(m, &m->gj_t, transpose(wj, H, H)));
+            RC(upload(m, &m->gbj, std::vector<float>(bj, bj + H)));
+        }
+    }
+    const int G = d.sg_gather_width;
+    if (d.sg_gather == FUSION_GATHER_GATED) {
+        const float *wg = take();
+        const float *bg = take();
+        const float *wo = take();
+        const float *bo = take();
+        RC(upload(m, &m->gat_wg_t, transpose(wg, G, 2 * H)));
+        RC(upload(m, &m->gat_bg, std::vector<float>(bg, bg + G)));
+        RC(upload(m, &m->gat_wo_t, transpose(wo, G, H)));
+        RC(upload(m, &m->gat_bo, std::vector<float>(bo, bo + G)));
+    } else {
+        const float *w = take();
+        const float *b = take();
+        RC(upload(m, &m->gat_wo_t, transpose(w, G, H)));
+        RC(upload(m, &m->gat_bo, std::vector<float>(b, b + G)));
+    }
+    int fin = d.cnn_dense + G;
+    for (int l = 0; l < d.n_head; ++l) {
+        const float *w = take();
+        const float *b = take();
+        RC(upload(m, &m->head_wt[l], transpose(w, d.head[l], fin)));
+        RC(upload(m, &m->head_b[l], std::vector<float>(b, b + d.head[l])));
+        fin = d.head[l];
+    }
+    if (li != L.size()) return fail(FUSION_EWEIGHTS, "internal: weights layout walk incomplete");
+    return FUSION_OK;
+}
+
+int alloc_workspace(fusion_model *m) {
+    const fusion_model_desc &d = m->d;
+    const size_t B = d.max_poses;
+    const size_t A = B * d.max_atoms;
+    const int KW = 2 * d.support + 1;
+    RC(dalloc(m, &m->in_off, B + 1));
+    RC(dalloc(m, &m->in_nlig, B));
+    RC(dalloc(m, &m->in_xyz, A * 3));
+    RC(dalloc(m, &m->in_feat, A * kFeat));
+    RC(dalloc(m, &m->origin, B * 3));
+    RC(dalloc(m, &m->atom_vox, A));
+    RC(dalloc(m, &m->atom_w, A * 3 * KW));
+    const size_t n3 = (size_t)d.grid_n * d.grid_n * d.grid_n;
+    float *g = nullptr;
+    RC(dalloc(m, &g, B * n3 * m->grid_cx));
+    m->grid = g;
+    size_t biggest = 0;
+    for (int i = 0; i < d.n_conv; ++i) {
+        const Shape s = conv_out(d, i + 1);
+        const size_t sz = B * (size_t)s.n * s.n * s.n * s.c;
+        m->conv[i].n_in = conv_out(d, i).n;
+        m->conv[i].n_out = s.n;
+        if (d.keep_stages) RC(dalloc(m, &m->act[i], sz));
+        if (sz > biggest) biggest = sz;
+    }
+    if (!d.keep_stages) {
+        RC(dalloc(m, &m->act[0], biggest));
+        if (d.n_conv > 1) RC(dalloc(m, &m->act[1], biggest));
+        for (int i = 2; i < d.n_conv; ++i) m->act[i] = m->act[i % 2];
+    }
+    if (d.pool > 1) RC(dalloc(m, &m->pool_out, B * m->flat));
+    RC(dalloc(m, &m->dense_part, (size_t)m->splits * B * d.cnn_dense));
+    RC(dalloc(m, &m->cnn_lat, B * d.cnn_dense));
+    for (int e = 0; e < 2; ++e) {
+        RC(dalloc(m, &m->e_beg[e], A));
+        RC(dalloc(m, &m->e_deg[e], A));
+        RC(dalloc(m, &m->e_col[e], A * d.max_degree));
+    }
+    const size_t H = d.sg_hidden;
+    RC(dalloc(m, &m->hbuf[0], A * H));
+    RC(dalloc(m, &m->hbuf[1], A * H));
+    RC(dalloc(m, &m->xin, A * H));
+    for (int e = 0; e < 2; ++e)
+        for (int q = 0; q < 2; ++q) RC(dalloc(m, &m->Tbuf[e][q], A * H));
+    RC(dalloc(m, &m->sg_lat, B * d.sg_gather_width));
+    RC(dalloc(m, &m->aff, B));
+    RC(dalloc(m, &m->err, 4));
+    RC(halloc(m, &m->h_off, B + 1));
+    RC(halloc(m, &m->h_err, 4));
+    RC(halloc(m, &m->h_aff, B));
+    for (auto &e : m->ev) CU(cudaEventCreate(&e));
+    return FUSION_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fusion_weights_bytes(const fusion_model_desc *desc) {
+    std::string why;
+    if (!check_desc(desc, &why)) {
+        g_err = why;
+        return 0;
+    }
+    size_t n = 0;
+    for (const TensorSpec &t : blob_layout(*desc)) n += t.count;
+    return n * sizeof(float);
+}
+
+const char *fusion_last_error(void) { return g_err.c_str(); }
+
+void fusion_destroy(fusion_model *m) {
+    if (!m) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    for (auto &e : m->ev)
+        if (e) cudaEventDestroy(e);
+    for (void *p : m->allocs) cudaFree(p);
+    for (void *p : m->host_allocs) cudaFreeHost(p);
+    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+    cudaSetDevice(prev);
+    delete m;
+}
+
+int fusion_create(const fusion_model_desc *desc, const void *weights, size_t weights_bytes, void *cuda_stream,
+                  fusion_model **out) {
+    if (!out) return fail(FUSION_EINVAL, "out is NULL");
+    std::string why;
+    if (!check_desc(desc, &why)) return fail(FUSION_EINVAL, why);
+    if (desc->dtype != FUSION_F32)
+        return fail(FUSION_EUNSUPPORTED, "this build computes the FP32 path only for this dtype");
+    const size_t need = fusion_weights_bytes(desc);
+    if (!weights || weights_bytes != need)
+        return fail(FUSION_EWEIGHTS, "weights blob has " + std::to_string(weights_bytes) + " bytes, layout needs " +
+                                         std::to_string(need));
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FUSION_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    fusion_model *m = new (std::nothrow) fusion_model();
+    if (!m) return fail(FUSION_ENOMEM, "host allocation failed");
+    m->d = *desc;
+    m->device = dev;
+    if (cuda_stream) {
+        m->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete m;
+            return fail(FUSION_ECUDA, "cudaStreamCreate failed");
+        }
+        m->own_stream = true;
+    }
+    const Shape f = cnn_final(m->d);
+    m->pool_n = f.n;
+    m->pool_c = f.c;
+    m->flat = f.c * f.n * f.n * f.n;
+    m->splits = dense_splits(m->flat);
+    int rc = alloc_workspace(m);
+    if (!rc) rc = load_weights(m, static_cast<const float *>(weights));
+    if (rc) {
+        std::string keep = g_err;
+        fusion_destroy(m);
+        g_err = keep;
+        return rc;
+    }
+    *out = m;
+    return FUSION_OK;
+}
+
+static int check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(FUSION_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return FUSION_OK;
+}
+
+int fusion_score(fusion_model *m, const fusion_poses *poses, int32_t n_poses, float *out_affinity) {
+    if (!m || !poses) return fail(FUSION_EINVAL, "model or poses is NULL");
+    if (n_poses == 0) return FUSION_OK;
+    if (n_poses < 0 || n_poses != poses->n_poses) return fail(FUSION_EINVAL, "n_poses disagrees with poses->n_poses");
+    if (n_poses > m->d.max_poses) return fail(FUSION_EINVAL, "n_poses exceeds the model's max_poses");
+    if (!out_affinity || !poses->atom_off || !poses->n_lig || !poses->xyz || !poses->feat)
+        return fail(FUSION_EINVAL, "NULL pose array or output");
+    const fusion_model_desc &d = m->d;
+    const int B = n_poses;
+    CU(cudaSetDevice(m->device));
+    cudaStream_t st = m->stream;
+
+    const int32_t *off_d, *nlig_d;
+    const float *xyz_d, *feat_d;
+    std::vector<int32_t> off(B + 1), nlig(B);
+    if (!poses->on_device) {
+        std::memcpy(off.data(), poses->atom_off, sizeof(int32_t) * (B + 1));
+        std::memcpy(nlig.data(), poses->n_lig, sizeof(int32_t) * B);
+        if (off[0] != 0) return fail(FUSION_EINVAL, "atom_off[0] must be 0");
+        for (int p = 0; p < B; ++p) {
+            const int N = off[p + 1] - off[p];
+            if (N < 1 || N > d.max_atoms)
+                return fail(FUSION_EINVAL, "pose " + std::to_string(p) + " has " + std::to_string(N) +
+                                               " atoms (allowed 1.." + std::to_string(d.max_atoms) + ")");
+            if (nlig[p] < 1 || nlig[p] > N)
+                return fail(FUSION_EINVAL, "pose " + std::to_string(p) + ": n_lig outside [1, N]");
+        }
+        const size_t A = off[B];
+        for (size_t i = 0; i < A * 3; ++i)
+            if (!std::isfinite(poses->xyz[i]))
+                return fail(FUSION_EINVAL, "non-finite coordinate at atom " + std::to_string(i / 3));
+        CU(cudaMemcpyAsync(m->in_off, off.data(), sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(m->in_nlig, nlig.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(m->in_xyz, poses->xyz, sizeof(float) * A * 3, cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(m->in_feat, poses->feat, sizeof(float) * A * kFeat, cudaMemcpyHostToDevice, st));
+        off_d = m->in_off;
+        nlig_d = m->in_nlig;
+        xyz_d = m->in_xyz;
+        feat_d = m->in_feat;
+    } else {
+        CU(cudaMemcpyAsync(m->h_off, poses->atom_off, sizeof(int32_t) * (B + 1), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        std::memcpy(off.data(), m->h_off, sizeof(int32_t) * (B + 1));
+        if (off[0] != 0) return fail(FUSION_EINVAL, "atom_off[0] must be 0");
+        for (int p = 0; p < B; ++p) {
+            const int N = off[p + 1] - off[p];
+            if (N < 1 || N > d.max_atoms)
+                return fail(FUSION_EINVAL, "pose " + std::to_string(p) + " has " + std::to_string(N) +
+                                               " atoms (allowed 1.." + std::to_string(d.max_atoms) + ")");
+        }
+        off_d = poses->atom_off;
+        nlig_d = poses->n_lig;
+        xyz_d = poses->xyz;
+        feat_d = poses->feat;
+    }
+    const int A = off[B];
+    CU(cudaMemsetAsync(m->err, 0, 4 * sizeof(unsigned), st));
+
+    int ei = 0;
+    auto mark = [&]() { cudaEventRecord(m->ev[ei++], st); };
+    int map[16];
+    for (int i = 0; i < 16; ++i) map[i] = -1;
+    mark();
+
+    // pose prep + voxelize
+    PrepArgs pa{off_d, nlig_d, xyz_d, B, d.max_atoms, d.grid_n, d.grid_h, d.sigma, d.support,
+                m->origin, m->atom_vox, m->atom_w, m->err};
+    launch_prep(pa, st);
+    RC(check_launch("prep"));
+    map[0] = ei; mark();
+    VoxArgs va{off_d, feat_d, m->atom_vox, m->atom_w, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx, 0};
+    launch_voxelize(va, st);
+    RC(check_launch("voxelize"));
+    map[1] = ei; mark();
+
+    // 3D-CNN
+    const float *x = static_cast<const float *>(m->grid);
+    for (int i = 0; i < d.n_conv; ++i) {
+        const fusion_conv_desc &c = d.conv[i];
+        ConvArgs ca{x, m->conv[i].w, m->conv[i].b, m->act[i], B, m->conv[i].n_in, m->conv[i].n_out,
+                    m->conv[i].cx_in, c.c_out, c.k, c.stride, c.k / 2, c.residual};
+        launch_conv3d_f32(ca, st);
+        RC(check_launch("conv3d"));
+        m->last_conv_out[i] = m->act[i];
+        x = m->act[i];
+        map[2 + i] = ei; mark();
+    }
+    const float *flat_in = x;
+    if (d.pool > 1) {
+        const Shape s = conv_out(d, d.n_conv);
+        PoolArgs po{x, m->pool_out, B, s.n, m->pool_n, s.c, 0};
+        launch_maxpool(po, st);
+        RC(check_launch("maxpool"));
+        flat_in = m->pool_out;
+        map[10] = ei; mark();
+    }
+    DenseArgs da{flat_in, m->dense_w, m->dense_b, m->dense_part, m->cnn_lat, B, d.cnn_dense, m->flat, m->splits, 0, 1};
+    launch_dense(da, st);
+    RC(check_launch("dense"));
+    map[11] = ei; mark();
+
+    // radius graph
+    GraphArgs ga{off_d, xyz_d, B, d.max_atoms, d.max_degree, d.cut_cov, d.cut_nc,
+                 {m->e_beg[0], m->e_beg[1]}, {m->e_deg[0], m->e_deg[1]}, {m->e_col[0], m->e_col[1]}, m->err};
+    launch_radius_graph(ga, st);
+    RC(check_launch("radius_graph"));
+    map[12] = ei; mark();
+
+    // SG-CNN stages: each stage's input goes to xin (the gather reads the last
+    // one); GRU steps ping-pong between hbuf[0] and hbuf[1].
+    const int H = d.sg_hidden;
+    int tcur = 0;   // Tbuf ping-pong index holding the current transforms
+    const float *h = nullptr;
+    for (int s = 0; s < d.sg_n_stages; ++s) {
+        SgTransformArgs ta{};
+        ta.feat = feat_d;
+        ta.A = A;
+        ta.H = H;
+        ta.init = (s == 0);
+        ta.h_in = h;            // read row by row before the same row of xin is written
+        ta.h_out = m->xin;
+        if (s > 0 && d.sg_gate) {
+            ta.gi_t = m->gi_t; ta.gbi = m->gbi; ta.gj_t = m->gj_t; ta.gbj = m->gbj;
+        }
+        for (int e = 0; e < 2; ++e) {
+            const bool use = (d.sg_edges[s] & (1 << e)) && d.sg_steps[s] > 0;
+            ta.we_t[e] = use ? m->we_t[s][e] : nullptr;
+            ta.be[e] = use ? m->be[s][e] : nullptr;
+            ta.T[e] = m->Tbuf[e][tcur];
+        }
+        launch_sg_transform(ta, st);
+        RC(check_launch("sg_transform"));
+        h = m->xin;
+        for (int k = 0; k < d.sg_steps[s]; ++k) {
+            SgStepArgs sa{};
+            sa.h_in = h;
+            float *hout = (h == m->hbuf[0]) ? m->hbuf[1] : m->hbuf[0];
+            sa.h_out = hout;
+            const bool more = (k + 1 < d.sg_steps[s]);
+            for (int e = 0; e < 2; ++e) {
+                const bool use = (d.sg_edges[s] & (1 << e)) != 0;
+                sa.T_in[e] = use ? m->Tbuf[e][tcur] : nullptr;
+                sa.T_out[e] = (use && more) ? m->Tbuf[e][tcur ^ 1] : nullptr;
+                sa.beg[e] = m->e_beg[e];
+                sa.deg[e] = m->e_deg[e];
+                sa.col[e] = m->e_col[e];
+                sa.we_t[e] = use ? m->we_t[s][e] : nullptr;
+                sa.be[e] = use ? m->be[s][e] : nullptr;
+            }
+            sa.wih_t = m->wih_t[s]; sa.whh_t = m->whh_t[s]; sa.bih = m->bih[s]; sa.bhh = m->bhh[s];
+            sa.A = A;
+            sa.H = H;
+            launch_sg_step(sa, st);
+            RC(check_launch("sg_step"));
+            h = hout;
+            tcur ^= 1;
+        }
+    }
+    m->last_h = h;
+    const float *stage_in = m->xin;
+    map[13] = ei; mark();
+    SgGatherArgs gg{off_d, nlig_d, m->last_h, stage_in, m->gat_wg_t, m->gat_bg, m->gat_wo_t, m->gat_bo,
+                    m->sg_lat, B, H, d.sg_gather_width, d.sg_gather == FUSION_GATHER_GATED};
+    launch_sg_gather(gg, st);
+    RC(check_launch("sg_gather"));
+    map[14] = ei; mark();
+
+    HeadArgs ha{};
+    ha.cnn = m->cnn_lat;
+    ha.sg = m->sg_lat;
+    for (int l = 0; l < d.n_head; ++l) {
+        ha.wt[l] = m->head_wt[l];
+        ha.b[l] = m->head_b[l];
+        ha.width[l] = d.head[l];
+    }
+    ha.n_layers = d.n_head;
+    ha.B = B;
+    ha.Dc = d.cnn_dense;
+    ha.G = d.sg_gather_width;
+    ha.out = m->aff;
+    launch_head(ha, st);
+    RC(check_launch("head"));
+    map[15] = ei; mark();
+
+    CU(cudaMemcpyAsync(m->h_err, m->err, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(m->h_aff, m->aff, sizeof(float) * B, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+
+    // timings
+    for (int i = 0; i < 16; ++i) {
+        m->last_ms[i] = 0.f;
+        if (map[i] < 1) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, m->ev[map[i] - 1], m->ev[map[i]]);
+        m->last_ms[i] = ms;
+    }
+    m->last_B = B;
+    m->last_off = off;
+    if (!poses->on_device) m->last_nlig = nlig;
+    else m->last_nlig.clear();
+
+    const unsigned fl = m->h_err[0];
+    if (fl & FUSION_ERR_INPUT) return fail(FUSION_EINVAL, "invalid pose data (n_lig outside [1, N] or non-finite coordinate)");
+    if (fl & FUSION_ERR_EDGES) return fail(FUSION_ECAPACITY, "edge capacity exceeded (raise max_degree)");
+    if (fl & FUSION_ERR_TIMEOUT) return fail(FUSION_ETIMEOUT, "a bounded device wait ran out");
+    if (poses->on_device) {
+        CU(cudaMemcpyAsync(out_affinity, m->aff, sizeof(float) * B, cudaMemcpyDeviceToDevice, st));
+        CU(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(out_affinity, m->h_aff, sizeof(float) * B);
+    }
+    return FUSION_OK;
+}
+
+int fusion_last_timings(fusion_model *m, float *out, int32_t n) {
+    if (!m || !out || n < 0 || n > 16) return fail(FUSION_EINVAL, "bad arguments");
+    for (int i = 0; i < n; ++i) out[i] = m->last_ms[i];
+    return FUSION_OK;
+}
+
+int64_t fusion_stage_bytes(fusion_model *m, int32_t stage, int32_t index) {
+    if (!m || m->last_B == 0) return fail(FUSION_EINVAL, "no scoring call to fetch from");
+    const fusion_model_desc &d = m->d;
+    const int p = (stage == FUSION_STAGE_CONV) ? (index & 0xffff) : index;
+    if (stage != FUSION_STAGE_AFFINITY && (p < 0 || p >= m->last_B)) return fail(FUSION_EINVAL, "pose index out of range");
+    const int N = (stage == FUSION_STAGE_AFFINITY) ? 0 : m->last_off[p + 1] - m->last_off[p];
+    switch (stage) {
+    case FUSION_STAGE_ORIGIN: return 12;
+    case FUSION_STAGE_GRID: return (int64_t)d.grid_n * d.grid_n * d.grid_n * kFeat * 4;
+    case FUSION_STAGE_CONV: {
+        const int l = index >> 16;
+        if (l < 0 || l >= d.n_conv) return fail(FUSION_EINVAL, "conv layer out of range");
+        const Shape s = conv_out(d, l + 1);
+        return (int64_t)s.n * s.n * s.n * s.c * 4;
+    }
+    case FUSION_STAGE_POOL: return (int64_t)m->flat * 4;
+    case FUSION_STAGE_CNN_LATENT: return (int64_t)d.cnn_dense * 4;
+    case FUSION_STAGE_EDGES_COV:
+    case FUSION_STAGE_EDGES_NC: {
+        const int e = stage == FUSION_STAGE_EDGES_COV ? 0 : 1;
+        std::vector<int32_t> deg(N);
+        if (cudaMemcpy(deg.data(), m->e_deg[e] + m->last_off[p], N * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(FUSION_ECUDA, "copy of degrees failed");
+        int64_t E = 0;
+        for (int v : deg) E += v;
+        return (int64_t)(N + 1 + E) * 4;
+    }
+    case FUSION_STAGE_SG_STATE: return (int64_t)N * d.sg_hidden * 4;
+    case FUSION_STAGE_SG_LATENT: return (int64_t)d.sg_gather_width * 4;
+    case FUSION_STAGE_AFFINITY: return (int64_t)m->last_B * 4;
+    default: return fail(FUSION_EINVAL, "unknown stage");
+    }
+}
+
+int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst, size_t bytes) {
+    const int64_t need = fusion_stage_bytes(m, stage, index);
+    if (need < 0) return (int)need;
+    if (!dst || bytes < (size_t)need) return fail(FUSION_EINVAL, "destination too small");
+    CU(cudaSetDevice(m->device));
+    CU(cudaStreamSynchronize(m->stream));
+    const fusion_model_desc &d = m->d;
+    const int p = (stage == FUSION_STAGE_CONV) ? (index & 0xffff) : index;
+    switch (stage) {
+    case FUSION_STAGE_ORIGIN:
+        CU(cudaMemcpy(dst, m->origin + p * 3, 12, cudaMemcpyDeviceToHost));
+        return FUSION_OK;
+    case FUSION_STAGE_GRID: {
+        const size_t n3 = (size_t)d.grid_n * d.grid_n * d.grid_n;
+        std::vector<float> t(n3 * m->grid_cx);
+        CU(cudaMemcpy(t.data(), static_cast<const float *>(m->grid) + (size_t)p * n3 * m->grid_cx, t.size() * 4,
+                      cudaMemcpyDeviceToHost));
+        float *o = static_cast<float *>(dst);
+        for (size_t v = 0; v < n3; ++v)
+            for (int c = 0; c < kFeat; ++c) o[v * kFeat + c] = t[v * m->grid_cx + c];
+        return FUSION_OK;
+    }
+    case FUSION_STAGE_CONV: {
+        const int l = index >> 16;
+        if (!d.keep_stages && l != d.n_conv - 1) return fail(FUSION_EINVAL, "conv stages need keep_stages");
+        CU(cudaMemcpy(dst, m->last_conv_out[l] + (size_t)p * (need / 4), need, cudaMemcpyDeviceToHost));
+        return FUSION_OK;
+    }
+    case FUSION_STAGE_POOL:
+        if (d.pool <= 1) return fail(FUSION_EINVAL, "model has no pool");
+        CU(cudaMemcpy(dst, m->pool_out + (size_t)p * m->flat, need, cudaMemcpyDeviceToHost));
+        return FUSION_OK;
+    case FUSION_STAGE_CNN_LATENT:
+        CU(cudaMemcpy(dst, m->cnn_lat + (size_t)p * d.cnn_dense, need, cudaMemcpyDeviceToHost));
+        return FUSION_OK;
+    case FUSION_STAGE_EDGES_COV:
+    case FUSION_STAGE_EDGES_NC: {
+        const int e = stage == FUSION_STAGE_EDGES_COV ? 0 : 1;
+        const int a0 = m->last_off[p], N = m->last_off[p + 1] - a0;
+        std::vector<int32_t> beg(N), deg(N);
+        CU(cudaMemcpy(beg.data(), m->e_beg[e] + a0, N * 4, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(deg.data(), m->e_deg[e] + a0, N * 4, cudaMemcpyDeviceToHost));
+        int32_t *o = static_cast<int32_t *>(dst);
+        o[0] = 0;
+        for (int i = 0; i < N; ++i) o[i + 1] = o[i] + deg[i];
+        int32_t *col = o + N + 1;
+        for (int i = 0; i < N; ++i) {
+            if (deg[i] == 0) continue;
+            CU(cudaMemcpy(col + o[i], m->e_col[e] + beg[i], (size_t)deg[i] * 4, cudaMemcpyDeviceToHost));
+            for (int q = 0; q < deg[i]; ++q) col[o[i] + q] -= a0;
+        }
+        return FUSION_OK;
+    }
+    case FUSION_STAGE_SG_STATE:
+        CU(cudaMemcpy(dst, m->last_h + (size_t)m->last_off[p] * d.sg_hidden, need, cudaMemcpyDeviceToHost));
+        return FUSION_OK;
+    case FUSION_STAGE_SG_LATENT:
+        CU(cudaMemcpy(dst, m->sg_lat + (size_t)p * d.sg_gather_width, need, cudaMemcpyDeviceToHost));
+        return FUSION_OK;
+    case FUSION_STAGE_AFFINITY:
+        CU(cudaMemcpy(dst, m->aff, need, cudaMemcpyDeviceToHost));
+        return FUSION_OK;
+    default:
+        return fail(FUSION_EINVAL, "unknown stage");
+    }
+}
+
+}  // extern "C"

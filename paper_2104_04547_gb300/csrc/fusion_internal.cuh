@@ -1,0 +1,157 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Layouts in device memory (all row-major, batch outermost):
+//   grid / activations: NDHWC, [pose][z][y][x][channel], channels padded to `cx`
+//   conv weights (FP32 path): [k^3 offset][c_in padded][c_out]
+//   graph: per edge type, per atom i: beg[i], deg[i]; col[beg .. beg+deg) global atom indices, sorted
+//   node states: [atom][H]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/fusion.h"
+
+#define FUSION_ERR_INPUT     1u   // invalid pose data seen on the device
+#define FUSION_ERR_EDGES     2u   // edge capacity of a pose exceeded
+#define FUSION_ERR_TIMEOUT   4u   // a bounded wait ran out
+
+namespace fusion {
+
+constexpr int kFeat = 19;
+constexpr int kMaxSupportW = 11;     // 2k+1 for k <= 5
+constexpr int kGridCellsMax = 16;    // graph cell list: at most 16 cells per axis
+
+// ---- pose prep + voxelize -------------------------------------------------
+
+struct PrepArgs {
+    const int32_t *atom_off;
+    const int32_t *n_lig;
+    const float *xyz;
+    int n_poses;
+    int max_atoms;
+    int grid_n;
+    float h, sigma;
+    int k;
+    float *origin;        // [B][3]
+    int4 *atom_vox;       // [A]: (cz, cy, cx, pose)
+    float *atom_w;        // [A][3][2k+1]: z, y, x axis weights
+    unsigned *err;
+};
+void launch_prep(const PrepArgs &a, cudaStream_t s);
+
+struct VoxArgs {
+    const int32_t *atom_off;
+    const float *feat;
+    const int4 *atom_vox;
+    const float *atom_w;
+    int n_poses;
+    int grid_n;
+    int k;
+    int max_atoms;
+    void *out;            // [B][n][n][n][cx]
+    int cx;               // padded channel count of the output layout
+    int out_bf16;         // 0: float32, 1: bfloat16
+};
+void launch_voxelize(const VoxArgs &a, cudaStream_t s);
+
+// ---- 3D-CNN ----------------------------------------------------------------
+
+struct ConvArgs {
+    const float *x;       // [B][n_in]^3[cx_in]
+    const float *w;       // [k^3][cx_in][c_out]
+    const float *bias;    // [c_out]
+    float *y;             // [B][n_out]^3[c_out]
+    int B, n_in, n_out, cx_in, c_out, k, stride, pad, residual;
+};
+void launch_conv3d_f32(const ConvArgs &a, cudaStream_t s);
+
+struct PoolArgs {
+    const void *x; void *y;
+    int B, n_in, n_out, c;
+    int bf16;
+};
+void launch_maxpool(const PoolArgs &a, cudaStream_t s);
+
+struct DenseArgs {
+    const void *x;        // [B][K] (float or bf16)
+    const void *w;        // [N][K] (float or bf16)
+    const float *bias;    // [N]
+    float *part;          // [splits][B][N]
+    float *y;             // [B][N]
+    int B, N, K, splits;
+    int bf16;
+    int relu;
+};
+void launch_dense(const DenseArgs &a, cudaStream_t s);
+int dense_splits(int K);
+
+// ---- radius graph ----------------------------------------------------------
+
+struct GraphArgs {
+    const int32_t *atom_off;
+    const float *xyz;
+    int n_poses;
+    int max_atoms;
+    int max_degree;
+    float cut_cov, cut_nc;
+    int32_t *beg[2], *deg[2], *col[2];   // 0 covalent, 1 non-covalent
+    unsigned *err;
+};
+void launch_radius_graph(const GraphArgs &a, cudaStream_t s);
+size_t radius_graph_smem(int max_atoms);
+
+// ---- SG-CNN ----------------------------------------------------------------
+
+struct SgTransformArgs {
+    const float *feat;     // [A][19]
+    const float *h_in;     // [A][H] (unused in init mode)
+    float *h_out;          // [A][H]: the stage input written here
+    float *T[2];           // [A][H] per edge type slot
+    const float *we_t[2];  // [H][H] transposed edge transforms (nullptr: slot unused)
+    const float *be[2];
+    const float *gi_t, *gbi, *gj_t, *gbj;   // gate ([2H][H], [H], [H][H], [H]); nullptr: no gate
+    int A, H;
+    int init;              // 1: stage input = h0 (features zero-padded to H)
+};
+void launch_sg_transform(const SgTransformArgs &a, cudaStream_t s);
+
+struct SgStepArgs {
+    const float *h_in;     // [A][H]
+    float *h_out;          // [A][H]
+    const float *T_in[2];  // neighbour transforms of this step (nullptr: slot unused)
+    float *T_out[2];       // transforms of h_out for the next step (nullptr: not needed)
+    const int32_t *beg[2], *deg[2], *col[2];   // edges of each slot
+    const float *wih_t, *whh_t, *bih, *bhh;     // GRU: [H][3H], [H][3H], [3H], [3H]
+    const float *we_t[2], *be[2];               // for T_out
+    int A, H;
+};
+void launch_sg_step(const SgStepArgs &a, cudaStream_t s);
+
+struct SgGatherArgs {
+    const int32_t *atom_off;
+    const int32_t *n_lig;
+    const float *h;        // [A][H] final node states
+    const float *x;        // [A][H] input of the last stage
+    const float *wg_t, *bg;   // gated: [2H][G], [G]
+    const float *wo_t, *bo;   // [H][G], [G] (linear gather: the only matrix)
+    float *out;            // [B][G]
+    int B, H, G, gated;
+};
+void launch_sg_gather(const SgGatherArgs &a, cudaStream_t s);
+
+// ---- head ------------------------------------------------------------------
+
+struct HeadArgs {
+    const float *cnn;      // [B][Dc]
+    const float *sg;       // [B][G]
+    const float *wt[FUSION_MAX_HEAD];   // [in][out] transposed
+    const float *b[FUSION_MAX_HEAD];
+    int width[FUSION_MAX_HEAD];
+    int n_layers;
+    int B, Dc, G;
+    float *out;            // [B]
+};
+void launch_head(const HeadArgs &a, cudaStream_t s);
+
+}  // namespace fusion

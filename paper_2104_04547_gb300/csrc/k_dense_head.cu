@@ -1,0 +1,161 @@
+// CNN dense layer and fusion head.
+//
+// CNN dense (Section 3.3.1: flatten -> dense + ReLU): y[b][n] = ReLU(bias[n] +
+// sum_k x[b][k] W[n][k]) with K = pooled voxels x channels (221,184 for the
+// full-size model).  At small batch the weight stream dominates, so it is a
+// split-K product: CTA (n-tile, split s, b-tile) multiplies a 64 x 64 tile over
+// the K slice of split s from shared-memory tiles, and a second kernel adds the
+// split partials in a fixed order (split count depends on K only, so a pose's
+// result does not depend on its batch) and applies bias and ReLU.  The weight
+// rows were permuted at model creation so that the flatten of the NDHWC pooled
+// map is a plain row read.
+//
+// Fusion head (Section 3.3.3, Table V: fusion dense layers with SELU): one CTA
+// per pose runs Linear -> SELU -> ... -> Linear on [cnn latent, sg latent].
+#include "fusion_internal.cuh"
+
+namespace fusion {
+
+namespace {
+
+constexpr int DT = 64;     // tile edge (poses and outputs)
+constexpr int DBK = 32;    // K chunk
+
+template <bool BF16>
+__device__ __forceinline__ void load8(const void *base, size_t idx, bool ok, float *out) {
+    if (!ok) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[j] = 0.f;
+        return;
+    }
+    if constexpr (BF16) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(base) + idx);
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 f = __bfloat1622float2(h[j]);
+            out[2 * j] = f.x;
+            out[2 * j + 1] = f.y;
+        }
+    } else {
+        const float *p = reinterpret_cast<const float *>(base) + idx;
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        const float4 b = *reinterpret_cast<const float4 *>(p + 4);
+        out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+        out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+    }
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) dense_splitk_kernel(DenseArgs a) {
+    __shared__ __align__(16) float xs[DBK][DT + 4];
+    __shared__ __align__(16) float ws[DBK][DT + 4];
+    const int tid = threadIdx.x;
+    const int n0 = blockIdx.x * DT;
+    const int split = blockIdx.y;
+    const int b0 = blockIdx.z * DT;
+    const int kper = ((a.K + a.splits - 1) / a.splits + DBK - 1) / DBK * DBK;
+    const int kbeg = split * kper;
+    const int kend = min(a.K, kbeg + kper);
+
+    // load role: row r = tid / 4 (0..63), k offset (tid % 4) * 8
+    const int lr = tid >> 2, lk = (tid & 3) * 8;
+    const int tr = tid / 16, tc = tid % 16;    // compute role: rows tr*4.., cols tc*4..
+    float acc[4][4] = {};
+    for (int kc = kbeg; kc < kend; kc += DBK) {
+        float xv[8], wv[8];
+        const int kk = kc + lk;
+        const bool kin = kk < kend;      // K is a multiple of 8, so a chunk of 8 is all in or all out
+        load8<BF16>(a.x, (size_t)(b0 + lr) * a.K + kk, kin && (b0 + lr) < a.B, xv);
+        load8<BF16>(a.w, (size_t)(n0 + lr) * a.K + kk, kin && (n0 + lr) < a.N, wv);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            xs[lk + j][lr] = xv[j];
+            ws[lk + j][lr] = wv[j];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int q = 0; q < DBK; ++q) {
+            const float4 x4 = *reinterpret_cast<const float4 *>(&xs[q][tr * 4]);
+            const float4 w4 = *reinterpret_cast<const float4 *>(&ws[q][tc * 4]);
+            const float xr[4] = {x4.x, x4.y, x4.z, x4.w};
+            const float wr[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xr[i], wr[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int b = b0 + tr * 4 + i;
+        if (b >= a.B) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tc * 4 + j;
+            if (n < a.N) a.part[((size_t)split * a.B + b) * a.N + n] = acc[i][j];
+        }
+    }
+}
+
+__global__ void dense_reduce_kernel(DenseArgs a) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.B * a.N) return;
+    const int n = e % a.N;
+    float s = 0.f;
+    for (int q = 0; q < a.splits; ++q) s += a.part[(size_t)q * a.B * a.N + e];
+    s += a.bias[n];
+    a.y[e] = a.relu ? fmaxf(s, 0.f) : s;
+}
+
+__device__ __forceinline__ float selu(float x) {
+    const float alpha = 1.6732632423543772848f, scale = 1.0507009873554804934f;
+    return x > 0.f ? scale * x : scale * alpha * expm1f(x);
+}
+
+__global__ void __launch_bounds__(256) head_kernel(HeadArgs a) {
+    __shared__ float v[2][512];
+    const int p = blockIdx.x;
+    const int fin0 = a.Dc + a.G;
+    for (int i = threadIdx.x; i < fin0; i += blockDim.x)
+        v[0][i] = i < a.Dc ? a.cnn[(size_t)p * a.Dc + i] : a.sg[(size_t)p * a.G + (i - a.Dc)];
+    __syncthreads();
+    int fin = fin0, cur = 0;
+    for (int l = 0; l < a.n_layers; ++l) {
+        const int fout = a.width[l];
+        const float *wt = a.wt[l];
+        for (int o = threadIdx.x; o < fout; o += blockDim.x) {
+            float s = a.b[l][o];
+            for (int k = 0; k < fin; ++k) s = fmaf(wt[(size_t)k * fout + o], v[cur][k], s);
+            v[cur ^ 1][o] = (l + 1 < a.n_layers) ? selu(s) : s;
+        }
+        __syncthreads();
+        cur ^= 1;
+        fin = fout;
+    }
+    if (threadIdx.x == 0) a.out[p] = v[cur][0];
+}
+
+}  // namespace
+
+int dense_splits(int K) {
+    int s = K / 2048;
+    if (s < 1) s = 1;
+    if (s > 128) s = 128;
+    return s;
+}
+
+void launch_dense(const DenseArgs &a, cudaStream_t s) {
+    dim3 grid((a.N + DT - 1) / DT, a.splits, (a.B + DT - 1) / DT);
+    if (a.bf16) dense_splitk_kernel<true><<<grid, 256, 0, s>>>(a);
+    else dense_splitk_kernel<false><<<grid, 256, 0, s>>>(a);
+    const int tot = a.B * a.N;
+    dense_reduce_kernel<<<(tot + 255) / 256, 256, 0, s>>>(a);
+}
+
+void launch_head(const HeadArgs &a, cudaStream_t s) {
+    head_kernel<<<a.B, 256, 0, s>>>(a);
+}
+
+}  // namespace fusion

@@ -1,0 +1,225 @@
+// Spatial-graph CNN: PotentialNet-style gated graph convolution (Section
+// 3.3.1, Table II; Gated Graph Sequence Neural Networks and PotentialNet are
+// the architectures it cites).
+//
+//   h0 = atom features zero-padded to H
+//   per step of a stage: m_i = sum over the stage's edge types e, neighbours j of (W_e h_j + b_e)
+//                        h_i <- GRU(m_i, h_i)        (gate rows reset, update, new)
+//   between stages:      h_i <- sigmoid(W_i [h_i, h0_i] + b_i) * (W_j h_i + b_j)
+//   ligand gather:       sum over ligand atoms of sigmoid(W_g [h_i, x_i] + b_g) * (W_o h_i + b_o)
+//                        (x_i = input of the last stage), or sum of (W h_i + b)
+//
+// Node work is warp-per-node: lane l owns features l and l + 32.  The
+// per-edge-type transforms W_e h_j + b_e are computed once per node and step
+// (sg_transform_kernel at a stage start, then by the previous step), so a step
+// is a segment sum over the sorted CSR row in a fixed order followed by the
+// GRU matrix-vector products, all deterministic.  The gather is one CTA per
+// pose: warps take ligand atoms round robin and the warp partials are added in
+// warp order.
+#include "fusion_internal.cuh"
+
+namespace fusion {
+
+namespace {
+
+constexpr int kWarps = 8;
+
+__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+template <int H>
+__global__ void __launch_bounds__(kWarps * 32) sg_transform_kernel(SgTransformArgs a) {
+    constexpr int HJ = H / 32;
+    __shared__ float sv[kWarps][2 * H];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kWarps + warp;
+    if (i >= a.A) return;
+    float *v = sv[warp];
+#pragma unroll
+    for (int j = 0; j < HJ; ++j) {
+        const int o = lane + 32 * j;
+        v[H + o] = o < kFeat ? a.feat[(size_t)i * kFeat + o] : 0.f;
+        if (!a.init) v[o] = a.h_in[(size_t)i * H + o];
+    }
+    __syncwarp();
+    float x[HJ];
+#pragma unroll
+    for (int j = 0; j < HJ; ++j) {
+        const int o = lane + 32 * j;
+        if (a.init) {
+            x[j] = v[H + o];
+        } else if (a.gi_t) {
+            float u = a.gbi[o], w = a.gbj[o];
+            for (int k = 0; k < 2 * H; ++k) u = fmaf(a.gi_t[k * H + o], v[k], u);
+            for (int k = 0; k < H; ++k) w = fmaf(a.gj_t[k * H + o], v[k], w);
+            x[j] = sigm(u) * w;
+        } else {
+            x[j] = v[o];
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < HJ; ++j) {
+        const int o = lane + 32 * j;
+        v[o] = x[j];
+        a.h_out[(size_t)i * H + o] = x[j];
+    }
+    __syncwarp();
+    for (int e = 0; e < 2; ++e) {
+        if (!a.we_t[e]) continue;
+#pragma unroll
+        for (int j = 0; j < HJ; ++j) {
+            const int o = lane + 32 * j;
+            float t = a.be[e][o];
+            for (int k = 0; k < H; ++k) t = fmaf(a.we_t[e][k * H + o], v[k], t);
+            a.T[e][(size_t)i * H + o] = t;
+        }
+    }
+}
+
+template <int H>
+__global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
+    constexpr int HJ = H / 32;
+    __shared__ float sv[kWarps][2 * H];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kWarps + warp;
+    if (i >= a.A) return;
+    float *v = sv[warp];
+
+    // message: segment sum of the neighbours' transforms, edge type by edge type, row order
+    float m[HJ];
+#pragma unroll
+    for (int j = 0; j < HJ; ++j) m[j] = 0.f;
+    for (int e = 0; e < 2; ++e) {
+        if (!a.T_in[e]) continue;
+        const int beg = a.beg[e][i], d = a.deg[e][i];
+        const float *T = a.T_in[e];
+        for (int q0 = 0; q0 < d; q0 += 32) {
+            const int jl = (q0 + lane < d) ? a.col[e][beg + q0 + lane] : 0;
+            const int nq = min(32, d - q0);
+            for (int q = 0; q < nq; ++q) {
+                const int jn = __shfl_sync(0xffffffffu, jl, q);
+#pragma unroll
+                for (int j = 0; j < HJ; ++j) m[j] += T[(size_t)jn * H + lane + 32 * j];
+            }
+        }
+    }
+    float hv[HJ];
+#pragma unroll
+    for (int j = 0; j < HJ; ++j) {
+        const int o = lane + 32 * j;
+        hv[j] = a.h_in[(size_t)i * H + o];
+        v[o] = m[j];
+        v[H + o] = hv[j];
+    }
+    __syncwarp();
+    float hn[HJ];
+#pragma unroll
+    for (int j = 0; j < HJ; ++j) {
+        const int o = lane + 32 * j;
+        float ir = a.bih[o], iz = a.bih[H + o], in_ = a.bih[2 * H + o];
+        float hr = a.bhh[o], hz = a.bhh[H + o], hn_ = a.bhh[2 * H + o];
+        for (int k = 0; k < H; ++k) {
+            const float mk = v[k], hk = v[H + k];
+            const float *wi = a.wih_t + (size_t)k * 3 * H;
+            const float *wh = a.whh_t + (size_t)k * 3 * H;
+            ir = fmaf(wi[o], mk, ir);
+            iz = fmaf(wi[H + o], mk, iz);
+            in_ = fmaf(wi[2 * H + o], mk, in_);
+            hr = fmaf(wh[o], hk, hr);
+            hz = fmaf(wh[H + o], hk, hz);
+            hn_ = fmaf(wh[2 * H + o], hk, hn_);
+        }
+        const float r = sigm(ir + hr);
+        const float z = sigm(iz + hz);
+        const float nn = tanhf(in_ + r * hn_);
+        hn[j] = (1.f - z) * nn + z * hv[j];
+        a.h_out[(size_t)i * H + o] = hn[j];
+    }
+    if (!a.T_out[0] && !a.T_out[1]) return;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < HJ; ++j) v[lane + 32 * j] = hn[j];
+    __syncwarp();
+    for (int e = 0; e < 2; ++e) {
+        if (!a.T_out[e]) continue;
+#pragma unroll
+        for (int j = 0; j < HJ; ++j) {
+            const int o = lane + 32 * j;
+            float t = a.be[e][o];
+            for (int k = 0; k < H; ++k) t = fmaf(a.we_t[e][k * H + o], v[k], t);
+            a.T_out[e][(size_t)i * H + o] = t;
+        }
+    }
+}
+
+template <int H>
+__global__ void __launch_bounds__(kWarps * 32) sg_gather_kernel(SgGatherArgs a) {
+    __shared__ float sv[kWarps][2 * H];
+    __shared__ float part[kWarps][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x;
+    const int a0 = a.atom_off[p];
+    const int N = a.atom_off[p + 1] - a0;
+    int nl = a.n_lig[p];
+    if (nl > N || nl < 0) nl = 0;      // invalid pose: flagged by the prep kernel
+    const int G = a.G;
+    float acc[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) acc[g] = 0.f;
+    float *v = sv[warp];
+    for (int i = warp; i < nl; i += kWarps) {
+        const size_t ai = (size_t)a0 + i;
+        for (int o = lane; o < H; o += 32) {
+            v[o] = a.h[ai * H + o];
+            v[H + o] = a.x[ai * H + o];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int gj = 0; gj < 8; ++gj) {
+            const int g = lane + 32 * gj;
+            if (g >= G) break;
+            float w = a.bo[g];
+            for (int k = 0; k < H; ++k) w = fmaf(a.wo_t[k * G + g], v[k], w);
+            if (a.gated) {
+                float u = a.bg[g];
+                for (int k = 0; k < 2 * H; ++k) u = fmaf(a.wg_t[k * G + g], v[k], u);
+                acc[gj] += sigm(u) * w;
+            } else {
+                acc[gj] += w;
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int gj = 0; gj < 8; ++gj) {
+        const int g = lane + 32 * gj;
+        if (g < G) part[warp][g] = acc[gj];
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        float s = 0.f;
+        for (int w = 0; w < kWarps; ++w) s += part[w][g];
+        a.out[(size_t)p * G + g] = s;
+    }
+}
+
+}  // namespace
+
+void launch_sg_transform(const SgTransformArgs &a, cudaStream_t s) {
+    const int blocks = (a.A + kWarps - 1) / kWarps;
+    if (a.H == 64) sg_transform_kernel<64><<<blocks, kWarps * 32, 0, s>>>(a);
+    else sg_transform_kernel<32><<<blocks, kWarps * 32, 0, s>>>(a);
+}
+
+void launch_sg_step(const SgStepArgs &a, cudaStream_t s) {
+    const int blocks = (a.A + kWarps - 1) / kWarps;
+    if (a.H == 64) sg_step_kernel<64><<<blocks, kWarps * 32, 0, s>>>(a);
+    else sg_step_kernel<32><<<blocks, kWarps * 32, 0, s>>>(a);
+}
+
+void launch_sg_gather(const SgGatherArgs &a, cudaStream_t s) {
+    if (a.H == 64) sg_gather_kernel<64><<<a.B, kWarps * 32, 0, s>>>(a);
+    else sg_gather_kernel<32><<<a.B, kWarps * 32, 0, s>>>(a);
+}
+
+}  // namespace fusion

@@ -1,0 +1,232 @@
+// Pose preparation and gather-form voxelization (Section 1 and Section 3.3:
+// atoms become a multi-channel density grid; the paper keeps the FAST grid
+// sizing and atom propagation, read here as a voxel-integrated isotropic
+// Gaussian over the cube of voxels within +-k of the atom's own voxel).
+//
+// prep_kernel (one CTA per pose): validates the pose, computes the grid origin
+// (ligand centroid summed left to right in float32, minus half a grid edge)
+// and, per atom, its containing voxel and the 3 x (2k+1) per-axis weights
+//   w_d(i) = 1/2 [erf((u_i + h - x_d)/(sigma sqrt 2)) - erf((u_i - x_d)/(sigma sqrt 2))].
+//
+// voxelize_kernel (one CTA per 8^3 voxel tile of a pose): compacts, in atom
+// order, the atoms whose support cube meets the tile, stages them in shared
+// memory and accumulates all channels of each voxel in registers in atom-index
+// order (deterministic, no atomics), then stores the voxel's channels as one
+// contiguous vector (16-byte stores) in the NDHWC layout the first conv reads.
+#include "fusion_internal.cuh"
+
+#include <math.h>
+
+namespace fusion {
+
+namespace {
+
+// erf(b) - erf(a) for a < b, through erfc in the tails to keep relative accuracy.
+__device__ __forceinline__ float erf_diff(float a, float b) {
+    if (a >= 0.f) return erfcf(a) - erfcf(b);
+    if (b <= 0.f) return erfcf(-b) - erfcf(-a);
+    return erff(b) - erff(a);
+}
+
+__global__ void __launch_bounds__(256) prep_kernel(PrepArgs a) {
+    const int p = blockIdx.x;
+    const int a0 = a.atom_off[p];
+    const int N = a.atom_off[p + 1] - a0;
+    const int nl = a.n_lig[p];
+    __shared__ float s_org[3];
+    if (N < 1 || N > a.max_atoms || nl < 1 || nl > N || a0 < 0) {
+        if (threadIdx.x == 0) atomicOr(a.err, FUSION_ERR_INPUT);
+        return;
+    }
+    if (threadIdx.x < 3) {
+        const int d = threadIdx.x;
+        float s = 0.f;
+        for (int i = 0; i < nl; ++i) s = __fadd_rn(s, a.xyz[(size_t)(a0 + i) * 3 + d]);
+        const float c = __fdiv_rn(s, (float)nl);
+        const float half = __fmul_rn(__fmul_rn((float)a.grid_n, a.h), 0.5f);
+        const float o = __fsub_rn(c, half);
+        s_org[d] = o;
+        a.origin[p * 3 + d] = o;
+    }
+    __syncthreads();
+    const int K = a.k, KW = 2 * a.k + 1;
+    const float inv = 1.0f / (a.sigma * 1.41421356237309515f);
+    bool bad = false;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const size_t ai = (size_t)a0 + i;
+        int c3[3];
+        for (int d = 0; d < 3; ++d) {
+            const float x = a.xyz[ai * 3 + d];
+            if (!isfinite(x)) bad = true;
+            const float t = __fsub_rn(x, s_org[d]);
+            float q = floorf(__fdiv_rn(t, a.h));
+            q = fminf(fmaxf(q, -1.0e6f), 1.0e6f);      // far outside the grid: contributes nothing
+            if (!isfinite(t)) q = -1.0e6f;
+            const int ci = (int)q;
+            c3[d] = ci;
+            float *w = a.atom_w + (ai * 3 + (2 - d)) * KW;   // slots: 0 z, 1 y, 2 x
+            for (int m = 0; m < KW; ++m) {
+                const int idx = ci - K + m;
+                const float lo = __fsub_rn((float)idx * a.h, t);
+                const float hi = __fsub_rn((float)(idx + 1) * a.h, t);
+                w[m] = 0.5f * erf_diff(lo * inv, hi * inv);
+            }
+        }
+        a.atom_vox[ai] = make_int4(c3[2], c3[1], c3[0], p);
+    }
+    if (bad) atomicOr(a.err, FUSION_ERR_INPUT);
+}
+
+constexpr int kTile = 8;
+constexpr int kStage = 256;
+
+template <bool BF16, int CX>
+__global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = a.grid_n;
+    const int K = a.k, KW = 2 * a.k + 1;
+    const int tiles = (n + kTile - 1) / kTile;
+    const int t = blockIdx.x;
+    const int p = blockIdx.y;
+    const int t0x = (t % tiles) * kTile;
+    const int t0y = ((t / tiles) % tiles) * kTile;
+    const int t0z = (t / (tiles * tiles)) * kTile;
+    const int a0 = a.atom_off[p];
+    const int N = a.atom_off[p + 1] - a0;
+    if (N < 1 || N > a.max_atoms) return;
+
+    int4 *s_v = reinterpret_cast<int4 *>(smem);                  // [kStage]
+    float *s_w = reinterpret_cast<float *>(s_v + kStage);        // [kStage][3*KW]
+    float *s_f = s_w + kStage * 3 * KW;                          // [kStage][19]
+    int *s_list = reinterpret_cast<int *>(s_f + kStage * kFeat); // [max_atoms]
+    __shared__ int s_wsum[16];
+    __shared__ int s_total;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // 1. ordered compaction of the atoms whose support cube meets this tile
+    int count = 0;
+    for (int base = 0; base < N; base += 512) {
+        const int i = base + tid;
+        bool hit = false;
+        if (i < N) {
+            const int4 v = a.atom_vox[a0 + i];
+            hit = (v.x - K <= t0z + kTile - 1) && (v.x + K >= t0z) &&
+                  (v.y - K <= t0y + kTile - 1) && (v.y + K >= t0y) &&
+                  (v.z - K <= t0x + kTile - 1) && (v.z + K >= t0x);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        const int lp = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) s_wsum[warp] = __popc(bal);
+        __syncthreads();
+        if (warp == 0) {
+            int v = lane < 16 ? s_wsum[lane] : 0;
+            int incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (lane < 16) s_wsum[lane] = incl - v;
+            if (lane == 15) s_total = incl;
+        }
+        __syncthreads();
+        if (hit) s_list[count + s_wsum[warp] + lp] = i;
+        count += s_total;
+        __syncthreads();
+    }
+
+    // 2. accumulate the voxel's channels over the staged atoms, in atom order
+    const int vx = t0x + (tid & 7);
+    const int vy = t0y + ((tid >> 3) & 7);
+    const int vz = t0z + (tid >> 6);
+    float acc[kFeat];
+#pragma unroll
+    for (int c = 0; c < kFeat; ++c) acc[c] = 0.f;
+
+    for (int r = 0; r < count; r += kStage) {
+        const int nr = min(kStage, count - r);
+        for (int s = tid; s < nr; s += 512) s_v[s] = a.atom_vox[a0 + s_list[r + s]];
+        for (int e = tid; e < nr * 3 * KW; e += 512) {
+            const int s = e / (3 * KW), q = e - s * 3 * KW;
+            s_w[e] = a.atom_w[(size_t)(a0 + s_list[r + s]) * 3 * KW + q];
+        }
+        for (int e = tid; e < nr * kFeat; e += 512) {
+            const int s = e / kFeat, q = e - s * kFeat;
+            s_f[e] = a.feat[(size_t)(a0 + s_list[r + s]) * kFeat + q];
+        }
+        __syncthreads();
+        for (int s = 0; s < nr; ++s) {
+            const int4 v = s_v[s];
+            const unsigned dz = (unsigned)(vz - (v.x - K));
+            const unsigned dy = (unsigned)(vy - (v.y - K));
+            const unsigned dx = (unsigned)(vx - (v.z - K));
+            if (dz < (unsigned)KW && dy < (unsigned)KW && dx < (unsigned)KW) {
+                const float *w = s_w + s * 3 * KW;
+                const float wv = (w[dz] * w[KW + dy]) * w[2 * KW + dx];
+                const float *f = s_f + s * kFeat;
+#pragma unroll
+                for (int c = 0; c < kFeat; ++c) acc[c] = fmaf(wv, f[c], acc[c]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // 3. store the voxel's channel vector (channels >= 19 are zero padding)
+    if (vx < n && vy < n && vz < n) {
+        const size_t vox = (((size_t)p * n + vz) * n + vy) * n + vx;
+        if constexpr (BF16) {
+            __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(a.out) + vox * CX;
+#pragma unroll
+            for (int c0 = 0; c0 < CX; c0 += 8) {
+                __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v8[j] = __float2bfloat16_rn(c0 + j < kFeat ? acc[c0 + j] : 0.f);
+                *reinterpret_cast<uint4 *>(out + c0) = *reinterpret_cast<const uint4 *>(v8);
+            }
+        } else {
+            float *out = reinterpret_cast<float *>(a.out) + vox * CX;
+#pragma unroll
+            for (int c0 = 0; c0 < CX; c0 += 4) {
+                float4 v4;
+                v4.x = c0 + 0 < kFeat ? acc[c0 + 0] : 0.f;
+                v4.y = c0 + 1 < kFeat ? acc[c0 + 1] : 0.f;
+                v4.z = c0 + 2 < kFeat ? acc[c0 + 2] : 0.f;
+                v4.w = c0 + 3 < kFeat ? acc[c0 + 3] : 0.f;
+                *reinterpret_cast<float4 *>(out + c0) = v4;
+            }
+        }
+    }
+}
+
+size_t vox_smem(int k, int max_atoms) {
+    const int KW = 2 * k + 1;
+    return (size_t)kStage * sizeof(int4) + (size_t)kStage * 3 * KW * 4 + (size_t)kStage * kFeat * 4 +
+           (size_t)max_atoms * 4;
+}
+
+template <bool BF16, int CX>
+void launch_vox_t(const VoxArgs &a, cudaStream_t s) {
+    const int tiles = (a.grid_n + kTile - 1) / kTile;
+    const size_t sm = vox_smem(a.k, a.max_atoms);
+    cudaFuncSetAttribute(voxelize_kernel<BF16, CX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 grid(tiles * tiles * tiles, a.n_poses);
+    voxelize_kernel<BF16, CX><<<grid, 512, sm, s>>>(a);
+}
+
+}  // namespace
+
+void launch_prep(const PrepArgs &a, cudaStream_t s) {
+    prep_kernel<<<a.n_poses, 256, 0, s>>>(a);
+}
+
+void launch_voxelize(const VoxArgs &a, cudaStream_t s) {
+    if (a.out_bf16) {
+        launch_vox_t<true, 32>(a, s);
+    } else if (a.cx == 24) {
+        launch_vox_t<false, 24>(a, s);
+    } else {
+        launch_vox_t<false, 20>(a, s);
+    }
+}
+
+}  // namespace fusion
