@@ -172,6 +172,8 @@ def run_ours(args):
     W = weights.init_weights(desc, WEIGHTS_SEED)
     blob = weights.to_blob(desc, W)
     batch = poses.make_batch(configs.WORKLOADS[WORKLOAD])
+    if args.poses < len(batch["n_lig"]):
+        batch = poses.subset(batch, range(args.poses))     # profiling captures only
     B = len(batch["n_lig"])
 
     cpu = None
@@ -287,6 +289,7 @@ def main():
     ap.add_argument("--dtype", choices=["f32", "bf16"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--poses", type=int, default=64, help="first N poses of the batch (small profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -86,6 +86,28 @@ struct DenseArgs {
 void launch_dense(const DenseArgs &a, cudaStream_t s);
 int dense_splits(int K);
 
+// Tensor-core (tcgen05) BF16 conv: a plan per layer holds the TMA tensor map of
+// the layer's input buffer and the launch geometry.
+struct ConvTcPlan {
+    struct Impl;
+    Impl *impl;
+    ConvTcPlan();
+    ~ConvTcPlan();
+    ConvTcPlan(const ConvTcPlan &) = delete;
+    ConvTcPlan &operator=(const ConvTcPlan &) = delete;
+};
+// Output slices per CTA for a layer with c_out output channels.
+int conv_tc_tile_slices(int c_out);
+// bf16 elements of the arranged weights of one layer.
+size_t conv_tc_weight_elems(int cin_pad, int c_out, int k);
+// Blob conv weights [co][ci][k][k][k] -> bf16 [16-ch chunk][offset, phase order][8-ch half][co][8].
+void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, uint16_t *out_bf16);
+// Build the plan; returns 0, or nonzero with a reason in `why`.
+int conv_tc_plan(ConvTcPlan &plan, const void *x, int max_poses, int n_in, int cin_pad, const void *w,
+                 const float *bias, void *y, int n_out, int c_out, int k, int stride, int residual, unsigned *err,
+                 char *why, size_t why_len);
+void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s);
+
 // ---- radius graph ----------------------------------------------------------
 
 struct GraphArgs {

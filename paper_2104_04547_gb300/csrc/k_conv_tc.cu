@@ -1,0 +1,433 @@
+// BF16 3D convolution on the tcgen05 tensor cores (Section 3.3.1, Table III:
+// the convolutions of the 3D-CNN are the one dense contraction of the path).
+//
+// Implicit GEMM: M = output voxels, N = output channels, K = input channels x
+// kernel offsets.  A CTA owns T output slices of 16 x 8 voxels (T M-tiles of
+// 128 rows) and all N output channels; the T accumulators (128 lanes x N fp32
+// columns each) live in tensor memory.
+//
+// Operand A comes from an input halo in shared memory: for each 16-channel
+// chunk (and, for stride 2, each of the 8 input parity phases) one TMA load
+// per 8-channel plane brings the (T + k' - 1) x (16 + k' - 1) x (8 + k' - 1)
+// voxel neighbourhood of the tile (zero-filled outside the grid, which is the
+// convolution's zero padding; stride-2 phases use the TMA element stride).
+// Every kernel offset of the chunk then reads its A operand straight from that
+// halo through a shared-memory descriptor whose start address slides by the
+// offset (K-major, no swizzle: an 8-row core matrix is one 8-voxel W-line of
+// 8 channels, 16 bytes per row, W-lines at a stride of the halo width).  So
+// each input element is fetched once per chunk, not once per offset.
+// Operand B (the weights of a few offsets, pre-arranged on the host in the
+// same core-matrix layout) streams through a ring of shared-memory stages with
+// plain bulk copies.
+//
+// Roles: warp 0 lane 0 issues the TMA loads, warp 1 owns tensor memory and
+// lane 0 issues the MMAs, warps 2-5 run the epilogue (tensor memory ->
+// registers, bias, ReLU, residual add, bf16 NDHWC stores).  Every wait is
+// bounded; a wait that runs out sets FUSION_ERR_TIMEOUT and the CTA drains and
+// returns.
+#include "fusion_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstring>
+
+namespace fusion {
+
+namespace {
+
+constexpr int kThreads = 192;
+constexpr uint64_t kWaitNs = 1000000000ull;    // 1 s
+
+struct Geo {
+    int nbx, nby, nbz;     // blocks along x (8), y (16), z (T)
+    int nphase;            // 1 or 8
+    int ntap[2];           // taps per dim for parity 0 / 1 (stride 2), or k (stride 1)
+    int hd, hh, hw;        // halo extents
+    uint32_t plane_bytes;  // one 8-channel plane of the halo, 128-byte aligned
+    uint32_t stage_bytes;  // one B stage
+    int ops;               // offsets per B stage
+    int nbs;               // B stages
+    int na;                // A buffers
+    int chunks;            // 16-channel chunks of the input
+};
+
+struct Args {
+    const __nv_bfloat16 *x;     // input [B][n_in]^3[cin] (read by the epilogue for residual blocks)
+    const __nv_bfloat16 *w;     // [chunks][k^3 offsets, phase order][2][N][8]
+    const float *bias;          // [N]
+    __nv_bfloat16 *y;           // [B][n_out]^3[N]
+    int n_in, n_out, cin, k, stride, pad, residual;
+    Geo g;
+    unsigned *err;
+};
+
+__device__ __forceinline__ void phase_taps(const Args &a, int ph, int &pz, int &py, int &px, int &nz, int &ny,
+                                           int &nx) {
+    if (a.stride == 1) {
+        pz = py = px = 0;
+        nz = ny = nx = a.k;
+    } else {
+        pz = (ph >> 2) & 1;
+        py = (ph >> 1) & 1;
+        px = ph & 1;
+        nz = a.g.ntap[pz];
+        ny = a.g.ntap[py];
+        nx = a.g.ntap[px];
+    }
+}
+
+template <int N, int T>
+__global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_constant__ CUtensorMap tmap, Args a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr uint32_t TCOLS = (T * N <= 32) ? 32 : (T * N <= 64) ? 64 : (T * N <= 128) ? 128 : (T * N <= 256) ? 256 : 512;
+    constexpr uint32_t IDESC = tc::idesc_bf16(128, N);
+    const Geo &g = a.g;
+    const uint32_t a_bytes = 2 * g.plane_bytes;                     // buffer stride (128-byte aligned planes)
+    const uint32_t a_tx = 2u * (uint32_t)(g.hd * g.hh * g.hw) * 16u;  // bytes the two TMA loads deliver
+    unsigned char *sA = smem;
+    unsigned char *sB = smem + g.na * a_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + g.nbs * g.stage_bytes);
+    uint64_t *a_full = bars;            // [2]
+    uint64_t *a_empty = bars + 2;       // [2]
+    uint64_t *b_full = bars + 4;        // [nbs]
+    uint64_t *b_empty = b_full + g.nbs; // [nbs]
+    uint64_t *acc_full = b_empty + g.nbs;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_full + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int blk = blockIdx.x;
+    const int bx = blk % g.nbx; blk /= g.nbx;
+    const int by = blk % g.nby; blk /= g.nby;
+    const int bz = blk % g.nbz;
+    const int b = blk / g.nbz;
+    const int x0 = bx * 8, y0 = by * 16, z0 = bz * T;
+    const uint64_t deadline = tc::globaltimer() + kWaitNs;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) { tc::mbar_init(&a_full[i], 1); tc::mbar_init(&a_empty[i], 1); }
+        for (int i = 0; i < g.nbs; ++i) { tc::mbar_init(&b_full[i], 1); tc::mbar_init(&b_empty[i], 1); }
+        tc::mbar_init(acc_full, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tmem_slot, TCOLS);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(a.err, FUSION_ERR_TIMEOUT);
+    };
+
+    int prod_ai = 0, prod_bi = 0;
+    if (warp == 0 && lane == 0) {
+        // ---------------- producer ----------------
+        int &ai = prod_ai, &bi = prod_bi;
+        int off_base = 0;
+        for (int c = 0; c < g.chunks && !*abort_flag; ++c) {
+            off_base = c * a.k * a.k * a.k;
+            int ph_off = 0;
+            for (int ph = 0; ph < g.nphase && !*abort_flag; ++ph) {
+                int pz, py, px, nz, ny, nx;
+                phase_taps(a, ph, pz, py, px, nz, ny, nx);
+                const int noff = nz * ny * nx;
+                const int buf = ai % g.na;
+                if (!tc::mbar_wait(&a_empty[buf], ((ai / g.na) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
+                tc::mbar_expect_tx(&a_full[buf], a_tx);
+                const int S = a.stride;
+                for (int j = 0; j < 2; ++j)
+                    tc::tma_load_5d(sA + buf * a_bytes + j * g.plane_bytes, &tmap, &a_full[buf], c * 16 + j * 8,
+                                    x0 * S + px - a.pad, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
+                ++ai;
+                for (int o0 = 0; o0 < noff; o0 += g.ops) {
+                    const int cnt = min(g.ops, noff - o0);
+                    const int st = bi % g.nbs;
+                    if (!tc::mbar_wait(&b_empty[st], ((bi / g.nbs) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
+                    const uint32_t bytes = (uint32_t)cnt * N * 32;
+                    tc::mbar_expect_tx(&b_full[st], bytes);
+                    tc::bulk_load(sB + st * g.stage_bytes, a.w + (size_t)(off_base + ph_off + o0) * N * 16, bytes,
+                                  &b_full[st]);
+                    ++bi;
+                }
+                ph_off += noff;
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        int ai = 0, bi = 0;
+        bool first = true;
+        const uint32_t sbo_a = (uint32_t)g.hw * 16;
+        const uint32_t row_zy = (uint32_t)g.hh * g.hw;
+        for (int c = 0; c < g.chunks && !*abort_flag; ++c) {
+            for (int ph = 0; ph < g.nphase && !*abort_flag; ++ph) {
+                int pz, py, px, nz, ny, nx;
+                phase_taps(a, ph, pz, py, px, nz, ny, nx);
+                const int noff = nz * ny * nx;
+                const int buf = ai % g.na;
+                if (!tc::mbar_wait(&a_full[buf], (ai / g.na) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
+                const uint32_t abase = tc::smem_u32(sA + buf * a_bytes);
+                for (int o0 = 0; o0 < noff; o0 += g.ops) {
+                    const int cnt = min(g.ops, noff - o0);
+                    const int st = bi % g.nbs;
+                    if (!tc::mbar_wait(&b_full[st], (bi / g.nbs) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
+                    tc::tc_fence_after();
+                    const uint32_t bbase = tc::smem_u32(sB + st * g.stage_bytes);
+                    for (int q = 0; q < cnt; ++q) {
+                        const int o = o0 + q;
+                        const int tx = o % nx, ty = (o / nx) % ny, tz = o / (nx * ny);
+                        const uint64_t bd = tc::desc_kmajor(bbase + q * N * 32, N * 16, 128);
+#pragma unroll
+                        for (int d = 0; d < T; ++d) {
+                            const uint32_t row = (uint32_t)(d + tz) * row_zy + (uint32_t)ty * g.hw + tx;
+                            const uint64_t ad = tc::desc_kmajor(abase + row * 16, g.plane_bytes, sbo_a);
+                            tc::mma_bf16(tbase + d * N, ad, bd, IDESC, first ? 0u : 1u);
+                        }
+                        first = false;
+                    }
+                    tc::mma_commit(&b_empty[st]);
+                    ++bi;
+                }
+                tc::mma_commit(&a_empty[buf]);
+                ++ai;
+            }
+        }
+        tc::mma_commit(acc_full);
+    } else if (warp >= 2) {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3;                 // tensor-memory lane quarter of this warp
+        const int r = q * 32 + lane;            // M row = voxel of the slice
+        const int h = r >> 3, w = r & 7;
+        const bool ok = tc::mbar_wait(acc_full, 0, deadline, a.err, FUSION_ERR_TIMEOUT);
+        if (!ok) fail();
+        tc::tc_fence_after();
+        if (ok && !*abort_flag) {
+            const int yy = y0 + h, xx = x0 + w;
+            for (int d = 0; d < T; ++d) {
+                const int zz = z0 + d;
+                const bool valid = zz < a.n_out && yy < a.n_out && xx < a.n_out;
+                const size_t vox = (((size_t)b * a.n_out + zz) * a.n_out + yy) * a.n_out + xx;
+#pragma unroll 1
+                for (int cc = 0; cc < N / 32; ++cc) {
+                    uint32_t acc[32];
+                    tc::tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + d * N + cc * 32, acc);
+                    tc::tmem_ld_wait();
+                    if (!valid) continue;
+                    float v[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = fmaxf(__uint_as_float(acc[j]) + a.bias[cc * 32 + j], 0.f);
+                    if (a.residual) {
+                        const uint4 *src = reinterpret_cast<const uint4 *>(a.x + vox * a.cin + cc * 32);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const uint4 t4 = src[u];
+                            const __nv_bfloat162 *hp = reinterpret_cast<const __nv_bfloat162 *>(&t4);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float2 f = __bfloat1622float2(hp[e]);
+                                v[u * 8 + 2 * e] += f.x;
+                                v[u * 8 + 2 * e + 1] += f.y;
+                            }
+                        }
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(a.y + vox * N + cc * 32);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        uint4 t4;
+                        __nv_bfloat162 *hp = reinterpret_cast<__nv_bfloat162 *>(&t4);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) hp[e] = __floats2bfloat162_rn(v[u * 8 + 2 * e], v[u * 8 + 2 * e + 1]);
+                        dst[u] = t4;
+                    }
+                }
+            }
+        }
+    }
+    // the MMA issuer's final commit covers every MMA; wait for it before freeing tensor memory
+    if (warp == 1) {
+        if (lane == 0 && !tc::mbar_wait(acc_full, 0, deadline)) fail();
+        __syncwarp();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0 && lane == 0) {
+        // make sure no copy issued by this CTA is still landing in its shared memory
+        const uint64_t dl = tc::globaltimer() + 100000000ull;
+        for (int i = 0; i < g.na; ++i) {
+            const int n = prod_ai > i ? (prod_ai - i + g.na - 1) / g.na : 0;
+            if (n > 0 && !tc::mbar_wait(&a_full[i], (n - 1) & 1, dl)) atomicOr(a.err, FUSION_ERR_TIMEOUT);
+        }
+        for (int i = 0; i < g.nbs; ++i) {
+            const int n = prod_bi > i ? (prod_bi - i + g.nbs - 1) / g.nbs : 0;
+            if (n > 0 && !tc::mbar_wait(&b_full[i], (n - 1) & 1, dl)) atomicOr(a.err, FUSION_ERR_TIMEOUT);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tbase, TCOLS);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+struct ConvTcPlan::Impl {
+    CUtensorMap tmap;
+    Args args;
+    int N = 0, T = 0;
+    size_t smem = 0;
+    unsigned grid = 0;
+};
+
+ConvTcPlan::ConvTcPlan() : impl(new Impl()) {}
+ConvTcPlan::~ConvTcPlan() { delete impl; }
+
+int conv_tc_tile_slices(int c_out) { return c_out >= 256 ? 2 : 4; }
+
+size_t conv_tc_weight_elems(int cin_pad, int c_out, int k) { return (size_t)(cin_pad / 16) * k * k * k * 2 * c_out * 8; }
+
+void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, uint16_t *out_bf16) {
+    // blob layout w[co][ci][kd][kh][kw] -> [chunk][offset in phase order][half][co][8]
+    const int nph = stride == 1 ? 1 : 8;
+    size_t idx = 0;
+    for (int c = 0; c < cin_pad / 16; ++c) {
+        for (int ph = 0; ph < nph; ++ph) {
+            int pz = 0, py = 0, px = 0, nz = k, ny = k, nx = k;
+            if (stride == 2) {
+                pz = (ph >> 2) & 1; py = (ph >> 1) & 1; px = ph & 1;
+                nz = (k - pz + 1) / 2; ny = (k - py + 1) / 2; nx = (k - px + 1) / 2;
+            }
+            for (int tz = 0; tz < nz; ++tz)
+                for (int ty = 0; ty < ny; ++ty)
+                    for (int tx = 0; tx < nx; ++tx) {
+                        const int kd = pz + stride * tz, kh = py + stride * ty, kw = px + stride * tx;
+                        for (int half = 0; half < 2; ++half)
+                            for (int co = 0; co < c_out; ++co)
+                                for (int e = 0; e < 8; ++e) {
+                                    const int ci = c * 16 + half * 8 + e;
+                                    float v = 0.f;
+                                    if (ci < c_in) v = w[((((size_t)co * c_in + ci) * k + kd) * k + kh) * k + kw];
+                                    // round to nearest even bf16
+                                    uint32_t u;
+                                    memcpy(&u, &v, 4);
+                                    u += 0x7FFFu + ((u >> 16) & 1u);
+                                    out_bf16[idx++] = (uint16_t)(u >> 16);
+                                }
+                    }
+        }
+    }
+}
+
+int conv_tc_plan(ConvTcPlan &plan, const void *x, int max_poses, int n_in, int cin_pad, const void *w,
+                 const float *bias, void *y, int n_out, int c_out, int k, int stride, int residual, unsigned *err,
+                 char *why, size_t why_len) {
+    ConvTcPlan::Impl &P = *plan.impl;
+    const int T = conv_tc_tile_slices(c_out);
+    if (c_out != 32 && c_out != 64 && c_out != 128 && c_out != 256) {
+        snprintf(why, why_len, "tensor-core conv needs c_out in {32, 64, 128, 256}");
+        return -1;
+    }
+    if (cin_pad % 16 != 0 || (stride != 1 && stride != 2)) {
+        snprintf(why, why_len, "tensor-core conv needs input channels padded to 16 and stride 1 or 2");
+        return -1;
+    }
+    Geo g{};
+    g.nbx = (n_out + 7) / 8;
+    g.nby = (n_out + 15) / 16;
+    g.nbz = (n_out + T - 1) / T;
+    g.nphase = stride == 1 ? 1 : 8;
+    g.ntap[0] = stride == 1 ? k : (k + 1) / 2;
+    g.ntap[1] = stride == 1 ? k : k / 2;
+    const int ntmax = g.ntap[0];
+    g.hd = T + ntmax - 1;
+    g.hh = 16 + ntmax - 1;
+    g.hw = 8 + ntmax - 1;
+    g.plane_bytes = ((uint32_t)(g.hd * g.hh * g.hw) * 16 + 127) / 128 * 128;
+    g.ops = 16384 / (c_out * 32);
+    if (g.ops < 1) g.ops = 1;
+    g.stage_bytes = ((uint32_t)g.ops * c_out * 32 + 127) / 128 * 128;
+    g.nbs = 4;
+    g.chunks = cin_pad / 16;
+    const size_t bar_bytes = (size_t)(5 + 2 * g.nbs) * 8 + 16;
+    const size_t limit = 227 * 1024;
+    const size_t b_total = (size_t)g.nbs * g.stage_bytes;
+    const size_t a1 = 2 * (size_t)g.plane_bytes;
+    g.na = (2 * a1 + b_total + bar_bytes <= limit) ? 2 : 1;
+    P.smem = g.na * a1 + b_total + bar_bytes;
+    if (P.smem > limit) {
+        snprintf(why, why_len, "tensor-core conv tile needs %zu bytes of shared memory", P.smem);
+        return -1;
+    }
+    if (g.hw * stride > 256 || g.hh * stride > 256 || g.hd * stride > 256) {
+        snprintf(why, why_len, "halo box too large for a TMA load");
+        return -1;
+    }
+    auto enc = get_encode();
+    if (!enc) {
+        snprintf(why, why_len, "cuTensorMapEncodeTiled is not available");
+        return -2;
+    }
+    cuuint64_t dims[5] = {(cuuint64_t)cin_pad, (cuuint64_t)n_in, (cuuint64_t)n_in, (cuuint64_t)n_in, (cuuint64_t)max_poses};
+    cuuint64_t strides[4] = {(cuuint64_t)cin_pad * 2, (cuuint64_t)cin_pad * 2 * n_in,
+                             (cuuint64_t)cin_pad * 2 * n_in * n_in, (cuuint64_t)cin_pad * 2 * n_in * n_in * n_in};
+    cuuint32_t box[5] = {8, (cuuint32_t)(g.hw * stride), (cuuint32_t)(g.hh * stride), (cuuint32_t)(g.hd * stride), 1};
+    cuuint32_t estr[5] = {1, (cuuint32_t)stride, (cuuint32_t)stride, (cuuint32_t)stride, 1};
+    CUresult r = enc(&P.tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(why, why_len, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return -2;
+    }
+    Args &A = P.args;
+    A.x = static_cast<const __nv_bfloat16 *>(x);
+    A.w = static_cast<const __nv_bfloat16 *>(w);
+    A.bias = bias;
+    A.y = static_cast<__nv_bfloat16 *>(y);
+    A.n_in = n_in;
+    A.n_out = n_out;
+    A.cin = cin_pad;
+    A.k = k;
+    A.stride = stride;
+    A.pad = k / 2;
+    A.residual = residual;
+    A.g = g;
+    A.err = err;
+    P.N = c_out;
+    P.T = T;
+    P.grid = (unsigned)(g.nbx * g.nby * g.nbz);   // per pose; times B at launch
+    return 0;
+}
+
+template <int N, int T>
+static void launch_t(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
+    cudaFuncSetAttribute(conv3d_tc_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
+    conv3d_tc_kernel<N, T><<<P.grid * B, kThreads, P.smem, s>>>(P.tmap, P.args);
+}
+
+void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s) {
+    ConvTcPlan::Impl &P = *plan.impl;
+    switch (P.N) {
+    case 32: launch_t<32, 4>(P, B, s); break;
+    case 64: launch_t<64, 4>(P, B, s); break;
+    case 128: launch_t<128, 4>(P, B, s); break;
+    default: launch_t<256, 2>(P, B, s); break;
+    }
+}
+
+}  // namespace fusion
