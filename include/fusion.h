@@ -164,6 +164,36 @@ int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst,
  * Entries of absent layers are 0.  `n` entries are written (n <= 16). */
 int fusion_last_timings(fusion_model *m, float *out, int32_t n);
 
+/* ---- dense layer without any allocation ----
+ * The paper has no counterpart to this entry point; it serves deployment.
+ *
+ * y[b][n] = act(bias[n] + sum_k x[b][k] * w[n][k]) for b < B, n < N (act =
+ * ReLU when relu != 0, identity otherwise): the CNN dense layer of
+ * fusion_score, run as the same split-K kernels, for callers that cannot
+ * allocate device memory.  Such callers include a serving process that admits
+ * requests against a device-memory budget it does not own, a host application
+ * whose own allocator owns every byte of the device, and a latency-bound
+ * request loop that cannot take the implicit synchronisation and unbounded
+ * latency of cudaMalloc / cudaFree.  The call allocates nothing: the split-K
+ * partials go to a fixed 8 MiB array that the library keeps in every GPU
+ * that loads it until the process exits.
+ *
+ * x: device float32 [B][K]; w: device float32 [N][K]; bias: device float32 [N];
+ * y: device float32 [B][N]; all caller-owned.  K must be a positive multiple
+ * of 8, and splits(K) x B x N must fit FUSION_NOALLOC_MAX_PARTIALS floats,
+ * where splits(K) = clamp(K / 2048, 1, 128); larger sizes return FUSION_EINVAL
+ * with a message naming the limit.  The kernels are enqueued on `cuda_stream`
+ * (a cudaStream_t; NULL is the legacy default stream) and the call returns
+ * without waiting for them.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  Every call shares the one array:
+ * calls whose kernels overlap on the GPU race and must be serialised by the
+ * caller (for example by issuing them on one stream).  Nothing in the array
+ * needs clearing between calls. */
+#define FUSION_NOALLOC_MAX_PARTIALS (1 << 21)
+int fusion_cnn_dense_noalloc(const float *x, const float *w, const float *bias, int32_t B, int32_t N, int32_t K,
+                             int32_t relu, float *y, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -424,6 +424,8 @@ int alloc_workspace(fusion_model *m) {
 
 }  // namespace
 
+int fusion::set_last_error(int code, const char *msg) { return fail(code, msg ? msg : ""); }
+
 extern "C" {
 
 size_t fusion_weights_bytes(const fusion_model_desc *desc) {

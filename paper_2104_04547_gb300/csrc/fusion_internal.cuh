@@ -176,4 +176,7 @@ struct HeadArgs {
 };
 void launch_head(const HeadArgs &a, cudaStream_t s);
 
+// Record `msg` as the calling thread's fusion_last_error() message; returns `code`.
+int set_last_error(int code, const char *msg);
+
 }  // namespace fusion

@@ -36,7 +36,9 @@ TIMING_NAMES = ["prep", "voxelize"] + [f"conv{i}" for i in range(8)] + \
                ["maxpool", "cnn_dense", "radius_graph", "sg_steps", "sg_gather", "head"]
 
 EXPORTED = ["fusion_weights_bytes", "fusion_create", "fusion_score", "fusion_destroy", "fusion_last_error",
-            "fusion_stage_bytes", "fusion_fetch_stage", "fusion_last_timings"]
+            "fusion_stage_bytes", "fusion_fetch_stage", "fusion_last_timings", "fusion_cnn_dense_noalloc"]
+
+FUSION_NOALLOC_MAX_PARTIALS = 1 << 21
 
 
 class FusionError(RuntimeError):
@@ -88,6 +90,9 @@ def _load():
     lib.fusion_fetch_stage.restype = C.c_int
     lib.fusion_last_timings.argtypes = [C.c_void_p, P(C.c_float), C.c_int32]
     lib.fusion_last_timings.restype = C.c_int
+    lib.fusion_cnn_dense_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                             C.c_int32, C.c_void_p, C.c_void_p]
+    lib.fusion_cnn_dense_noalloc.restype = C.c_int
     return lib
 
 
@@ -215,6 +220,13 @@ def fusion_last_timings(model, n: int = 16) -> np.ndarray:
     out = (C.c_float * n)()
     _check(lib.fusion_last_timings(model, out, n))
     return np.array(out[:], dtype=np.float32)
+
+
+def fusion_cnn_dense_noalloc(x, w, bias, B: int, N: int, K: int, relu: bool, y, stream=None) -> None:
+    """Dense layer with the library's fixed scratch (no allocation); device buffers in and out."""
+    rc = lib.fusion_cnn_dense_noalloc(C.c_void_p(_ptr(x)), C.c_void_p(_ptr(w)), C.c_void_p(_ptr(bias)), B, N, K,
+                                      int(relu), C.c_void_p(_ptr(y)), C.c_void_p(stream) if stream else None)
+    _check(rc)
 
 
 class Model:
