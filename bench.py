@@ -236,6 +236,19 @@ def run_ours(args):
         e2e = {"value": world * B * args.steps / wall, "unit": "poses/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 4 * B}
 
+    # |affinity difference| against the FP32 path on the same batch (outside the timed region)
+    delta = None
+    if args.dtype != "f32" and not args.no_f32_compare:
+        got = out.float().cpu().numpy().copy()
+        d32 = configs.model(MODEL, dtype="f32")
+        m32 = F.Model(d32, weights.to_blob(d32, W), max_poses=B, max_atoms=1200, max_degree=64,
+                      stream=stream.cuda_stream)
+        ref = m32.score(batch)
+        m32.close()
+        dd = np.abs(got - ref)
+        delta = {"vs": "f32 path, same poses and weights", "mean": float(dd.mean()), "max": float(dd.max()),
+                 "tolerance": 0.05}
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -273,6 +286,8 @@ def run_ours(args):
         "clocks": clk,
         "affinity_std": float(out.float().std().item()),
     }
+    if delta is not None:
+        line["delta_affinity"] = delta
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -286,9 +301,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--dtype", choices=["f32", "bf16"], default="f32")
+    ap.add_argument("--dtype", choices=["f32", "bf16"], default="bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-f32-compare", action="store_true")
     ap.add_argument("--poses", type=int, default=64, help="first N poses of the batch (small profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -29,6 +29,12 @@ int fail(int code, const std::string &msg) {
                         std::string(#call) + ": " + cudaGetErrorString(e_));                       \
     } while (0)
 
+#define RC_INNER(x)           \
+    do {                      \
+        int rc_ = (x);        \
+        if (rc_) return rc_;  \
+    } while (0)
+
 struct Shape {
     int c, n;
 };
@@ -177,10 +183,15 @@ struct fusion_model {
 
     // weights (device)
     struct ConvW {
-        float *w = nullptr, *b = nullptr;
+        void *w = nullptr;        // f32 [k^3][cx][co], or bf16 in the tensor-core layout
+        float *b = nullptr;
         int cx_in = 0, n_in = 0, n_out = 0;
     } conv[FUSION_MAX_CONV];
-    float *dense_w = nullptr, *dense_b = nullptr;
+    void *dense_w = nullptr;      // f32 or bf16 [cnn_dense][flat], flat in (D, H, W, C) order
+    float *dense_b = nullptr;
+    bool bf16 = false;            // conv / pool / dense in bf16 (tensor cores)
+    size_t esz = 4;               // bytes per grid / activation element
+    ConvTcPlan tcplan[FUSION_MAX_CONV];
     int pool_n = 0, pool_c = 0, flat = 0, splits = 1;
     float *we_t[FUSION_MAX_STAGES][2] = {}, *be[FUSION_MAX_STAGES][2] = {};
     float *wih_t[FUSION_MAX_STAGES] = {}, *whh_t[FUSION_MAX_STAGES] = {}, *bih[FUSION_MAX_STAGES] = {}, *bhh[FUSION_MAX_STAGES] = {};
@@ -196,8 +207,9 @@ struct fusion_model {
     float *atom_w = nullptr;
     void *grid = nullptr;
     int grid_cx = kGridCxF32;
-    float *act[FUSION_MAX_CONV] = {};
-    float *pool_out = nullptr, *dense_part = nullptr, *cnn_lat = nullptr;
+    void *act[FUSION_MAX_CONV] = {};
+    void *pool_out = nullptr;
+    float *dense_part = nullptr, *cnn_lat = nullptr;
     int32_t *e_beg[2] = {}, *e_deg[2] = {}, *e_col[2] = {};
     float *hbuf[2] = {}, *Tbuf[2][2] = {}, *xin = nullptr, *sg_lat = nullptr, *aff = nullptr;
     unsigned *err = nullptr;
@@ -212,7 +224,7 @@ struct fusion_model {
     // last call
     int last_B = 0;
     std::vector<int32_t> last_off, last_nlig;
-    const float *last_conv_out[FUSION_MAX_CONV] = {};
+    const void *last_conv_out[FUSION_MAX_CONV] = {};
     const float *last_h = nullptr;
     float last_ms[16] = {};
     int ev_map[16] = {};
@@ -235,6 +247,13 @@ int dalloc(fusion_model *m, T **p, size_t count) {
     return FUSION_OK;
 }
 
+int dalloc_bytes(fusion_model *m, void **p, size_t bytes) {
+    unsigned char *q = nullptr;
+    int rc = dalloc(m, &q, bytes);
+    *p = q;
+    return rc;
+}
+
 template <typename T>
 int halloc(fusion_model *m, T **p, size_t count) {
     void *q = nullptr;
@@ -253,6 +272,26 @@ int upload(fusion_model *m, float **dst, const std::vector<float> &src) {
     if (rc) return rc;
     CU(cudaMemcpy(*dst, src.data(), src.size() * sizeof(float), cudaMemcpyHostToDevice));
     return FUSION_OK;
+}
+
+int upload_raw(fusion_model *m, void **dst, const void *src, size_t bytes) {
+    RC_INNER(dalloc_bytes(m, dst, bytes));
+    CU(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return FUSION_OK;
+}
+
+uint16_t bf16_rne(float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_to_f32(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
 }
 
 std::vector<float> transpose(const float *w, int rows, int cols) {   // [rows][cols] -> [cols][rows]
@@ -290,11 +329,18 @@ int load_weights(fusion_model *m, const float *blob) {
         const int cx = (i == 0) ? m->grid_cx : c.c_in;
         const float *w = take();
         const float *b = take();
-        std::vector<float> t((size_t)k3 * cx * c.c_out, 0.f);
-        for (int o = 0; o < c.c_out; ++o)
-            for (int ci = 0; ci < c.c_in; ++ci)
-                for (int q = 0; q < k3; ++q) t[((size_t)q * cx + ci) * c.c_out + o] = w[((size_t)o * c.c_in + ci) * k3 + q];
-        RC(upload(m, &m->conv[i].w, t));
+        if (m->bf16) {
+            std::vector<uint16_t> t(conv_tc_weight_elems(cx, c.c_out, c.k));
+            conv_tc_arrange_weights(w, c.c_out, c.c_in, cx, c.k, c.stride, t.data());
+            RC(upload_raw(m, &m->conv[i].w, t.data(), t.size() * 2));
+        } else {
+            std::vector<float> t((size_t)k3 * cx * c.c_out, 0.f);
+            for (int o = 0; o < c.c_out; ++o)
+                for (int ci = 0; ci < c.c_in; ++ci)
+                    for (int q = 0; q < k3; ++q)
+                        t[((size_t)q * cx + ci) * c.c_out + o] = w[((size_t)o * c.c_in + ci) * k3 + q];
+            RC(upload_raw(m, &m->conv[i].w, t.data(), t.size() * 4));
+        }
         RC(upload(m, &m->conv[i].b, std::vector<float>(b, b + c.c_out)));
         m->conv[i].cx_in = cx;
     }
@@ -309,7 +355,13 @@ int load_weights(fusion_model *m, const float *blob) {
             for (int c = 0; c < f.c; ++c)
                 for (size_t sp = 0; sp < S3; ++sp)
                     t[(size_t)o * m->flat + sp * f.c + c] = w[(size_t)o * m->flat + (size_t)c * S3 + sp];
-        RC(upload(m, &m->dense_w, t));
+        if (m->bf16) {
+            std::vector<uint16_t> h(t.size());
+            for (size_t q = 0; q < t.size(); ++q) h[q] = bf16_rne(t[q]);
+            RC(upload_raw(m, &m->dense_w, h.data(), h.size() * 2));
+        } else {
+            RC(upload_raw(m, &m->dense_w, t.data(), t.size() * 4));
+        }
         RC(upload(m, &m->dense_b, std::vector<float>(b, b + d.cnn_dense)));
     }
     const int H = d.sg_hidden;
@@ -381,24 +433,22 @@ int alloc_workspace(fusion_model *m) {
     RC(dalloc(m, &m->atom_vox, A));
     RC(dalloc(m, &m->atom_w, A * 3 * KW));
     const size_t n3 = (size_t)d.grid_n * d.grid_n * d.grid_n;
-    float *g = nullptr;
-    RC(dalloc(m, &g, B * n3 * m->grid_cx));
-    m->grid = g;
+    RC(dalloc_bytes(m, &m->grid, B * n3 * m->grid_cx * m->esz));
     size_t biggest = 0;
     for (int i = 0; i < d.n_conv; ++i) {
         const Shape s = conv_out(d, i + 1);
         const size_t sz = B * (size_t)s.n * s.n * s.n * s.c;
         m->conv[i].n_in = conv_out(d, i).n;
         m->conv[i].n_out = s.n;
-        if (d.keep_stages) RC(dalloc(m, &m->act[i], sz));
+        if (d.keep_stages) RC(dalloc_bytes(m, &m->act[i], sz * m->esz));
         if (sz > biggest) biggest = sz;
     }
     if (!d.keep_stages) {
-        RC(dalloc(m, &m->act[0], biggest));
-        if (d.n_conv > 1) RC(dalloc(m, &m->act[1], biggest));
+        RC(dalloc_bytes(m, &m->act[0], biggest * m->esz));
+        if (d.n_conv > 1) RC(dalloc_bytes(m, &m->act[1], biggest * m->esz));
         for (int i = 2; i < d.n_conv; ++i) m->act[i] = m->act[i % 2];
     }
-    if (d.pool > 1) RC(dalloc(m, &m->pool_out, B * m->flat));
+    if (d.pool > 1) RC(dalloc_bytes(m, &m->pool_out, B * m->flat * m->esz));
     RC(dalloc(m, &m->dense_part, (size_t)m->splits * B * d.cnn_dense));
     RC(dalloc(m, &m->cnn_lat, B * d.cnn_dense));
     for (int e = 0; e < 2; ++e) {
@@ -423,6 +473,21 @@ int alloc_workspace(fusion_model *m) {
 }
 
 }  // namespace
+
+static int plan_tensor_core_convs(fusion_model *m) {
+    const fusion_model_desc &d = m->d;
+    for (int i = 0; i < d.n_conv; ++i) {
+        const fusion_conv_desc &c = d.conv[i];
+        const void *x = (i == 0) ? m->grid : m->act[i - 1];
+        char why[256] = {0};
+        const int r = conv_tc_plan(m->tcplan[i], x, d.max_poses, m->conv[i].n_in, m->conv[i].cx_in, m->conv[i].w,
+                                   m->conv[i].b, m->act[i], m->conv[i].n_out, c.c_out, c.k, c.stride, c.residual,
+                                   m->err, why, sizeof(why));
+        if (r) return fail(r == -1 ? FUSION_EUNSUPPORTED : FUSION_ECUDA, std::string("conv layer ") +
+                                                                             std::to_string(i) + ": " + why);
+    }
+    return FUSION_OK;
+}
 
 int fusion::set_last_error(int code, const char *msg) { return fail(code, msg ? msg : ""); }
 
@@ -461,8 +526,8 @@ int fusion_create(const fusion_model_desc *desc, const void *weights, size_t wei
     if (!out) return fail(FUSION_EINVAL, "out is NULL");
     std::string why;
     if (!check_desc(desc, &why)) return fail(FUSION_EINVAL, why);
-    if (desc->dtype != FUSION_F32)
-        return fail(FUSION_EUNSUPPORTED, "this build computes the FP32 path only for this dtype");
+    if (desc->dtype == FUSION_FP8)
+        return fail(FUSION_EUNSUPPORTED, "this build computes the FP32 and BF16 paths; FP8 is not built yet");
     const size_t need = fusion_weights_bytes(desc);
     if (!weights || weights_bytes != need)
         return fail(FUSION_EWEIGHTS, "weights blob has " + std::to_string(weights_bytes) + " bytes, layout needs " +
@@ -491,8 +556,12 @@ int fusion_create(const fusion_model_desc *desc, const void *weights, size_t wei
     m->pool_c = f.c;
     m->flat = f.c * f.n * f.n * f.n;
     m->splits = dense_splits(m->flat);
+    m->bf16 = (m->d.dtype == FUSION_BF16);
+    m->esz = m->bf16 ? 2 : 4;
+    m->grid_cx = m->bf16 ? 32 : kGridCxF32;
     int rc = alloc_workspace(m);
     if (!rc) rc = load_weights(m, static_cast<const float *>(weights));
+    if (!rc && m->bf16) rc = plan_tensor_core_convs(m);
     if (rc) {
         std::string keep = g_err;
         fusion_destroy(m);
@@ -579,33 +648,40 @@ int fusion_score(fusion_model *m, const fusion_poses *poses, int32_t n_poses, fl
     launch_prep(pa, st);
     RC(check_launch("prep"));
     map[0] = ei; mark();
-    VoxArgs va{off_d, feat_d, m->atom_vox, m->atom_w, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx, 0};
+    VoxArgs va{off_d, feat_d, m->atom_vox, m->atom_w, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx,
+               m->bf16 ? 1 : 0};
     launch_voxelize(va, st);
     RC(check_launch("voxelize"));
     map[1] = ei; mark();
 
     // 3D-CNN
-    const float *x = static_cast<const float *>(m->grid);
+    const void *x = m->grid;
     for (int i = 0; i < d.n_conv; ++i) {
         const fusion_conv_desc &c = d.conv[i];
-        ConvArgs ca{x, m->conv[i].w, m->conv[i].b, m->act[i], B, m->conv[i].n_in, m->conv[i].n_out,
-                    m->conv[i].cx_in, c.c_out, c.k, c.stride, c.k / 2, c.residual};
-        launch_conv3d_f32(ca, st);
+        if (m->bf16) {
+            conv_tc_launch(m->tcplan[i], B, st);
+        } else {
+            ConvArgs ca{static_cast<const float *>(x), static_cast<const float *>(m->conv[i].w), m->conv[i].b,
+                        static_cast<float *>(m->act[i]), B, m->conv[i].n_in, m->conv[i].n_out,
+                        m->conv[i].cx_in, c.c_out, c.k, c.stride, c.k / 2, c.residual};
+            launch_conv3d_f32(ca, st);
+        }
         RC(check_launch("conv3d"));
         m->last_conv_out[i] = m->act[i];
         x = m->act[i];
         map[2 + i] = ei; mark();
     }
-    const float *flat_in = x;
+    const void *flat_in = x;
     if (d.pool > 1) {
         const Shape s = conv_out(d, d.n_conv);
-        PoolArgs po{x, m->pool_out, B, s.n, m->pool_n, s.c, 0};
+        PoolArgs po{x, m->pool_out, B, s.n, m->pool_n, s.c, m->bf16 ? 1 : 0};
         launch_maxpool(po, st);
         RC(check_launch("maxpool"));
         flat_in = m->pool_out;
         map[10] = ei; mark();
     }
-    DenseArgs da{flat_in, m->dense_w, m->dense_b, m->dense_part, m->cnn_lat, B, d.cnn_dense, m->flat, m->splits, 0, 1};
+    DenseArgs da{flat_in, m->dense_w, m->dense_b, m->dense_part, m->cnn_lat, B, d.cnn_dense, m->flat, m->splits,
+                 m->bf16 ? 1 : 0, 1};
     launch_dense(da, st);
     RC(check_launch("dense"));
     map[11] = ei; mark();
@@ -729,6 +805,18 @@ int fusion_last_timings(fusion_model *m, float *out, int32_t n) {
     return FUSION_OK;
 }
 
+static int copy_as_f32(fusion_model *m, const void *src, size_t elem_off, size_t n, std::vector<float> &out) {
+    out.resize(n);
+    if (m->esz == 4) {
+        CU(cudaMemcpy(out.data(), static_cast<const float *>(src) + elem_off, n * 4, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<uint16_t> h(n);
+        CU(cudaMemcpy(h.data(), static_cast<const uint16_t *>(src) + elem_off, n * 2, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) out[i] = bf16_to_f32(h[i]);
+    }
+    return FUSION_OK;
+}
+
 int64_t fusion_stage_bytes(fusion_model *m, int32_t stage, int32_t index) {
     if (!m || m->last_B == 0) return fail(FUSION_EINVAL, "no scoring call to fetch from");
     const fusion_model_desc &d = m->d;
@@ -777,9 +865,8 @@ int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst,
         return FUSION_OK;
     case FUSION_STAGE_GRID: {
         const size_t n3 = (size_t)d.grid_n * d.grid_n * d.grid_n;
-        std::vector<float> t(n3 * m->grid_cx);
-        CU(cudaMemcpy(t.data(), static_cast<const float *>(m->grid) + (size_t)p * n3 * m->grid_cx, t.size() * 4,
-                      cudaMemcpyDeviceToHost));
+        std::vector<float> t;
+        RC(copy_as_f32(m, m->grid, (size_t)p * n3 * m->grid_cx, n3 * m->grid_cx, t));
         float *o = static_cast<float *>(dst);
         for (size_t v = 0; v < n3; ++v)
             for (int c = 0; c < kFeat; ++c) o[v * kFeat + c] = t[v * m->grid_cx + c];
@@ -788,13 +875,18 @@ int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst,
     case FUSION_STAGE_CONV: {
         const int l = index >> 16;
         if (!d.keep_stages && l != d.n_conv - 1) return fail(FUSION_EINVAL, "conv stages need keep_stages");
-        CU(cudaMemcpy(dst, m->last_conv_out[l] + (size_t)p * (need / 4), need, cudaMemcpyDeviceToHost));
+        std::vector<float> t;
+        RC(copy_as_f32(m, m->last_conv_out[l], (size_t)p * (need / 4), need / 4, t));
+        std::memcpy(dst, t.data(), need);
         return FUSION_OK;
     }
-    case FUSION_STAGE_POOL:
+    case FUSION_STAGE_POOL: {
         if (d.pool <= 1) return fail(FUSION_EINVAL, "model has no pool");
-        CU(cudaMemcpy(dst, m->pool_out + (size_t)p * m->flat, need, cudaMemcpyDeviceToHost));
+        std::vector<float> t;
+        RC(copy_as_f32(m, m->pool_out, (size_t)p * m->flat, m->flat, t));
+        std::memcpy(dst, t.data(), need);
         return FUSION_OK;
+    }
     case FUSION_STAGE_CNN_LATENT:
         CU(cudaMemcpy(dst, m->cnn_lat + (size_t)p * d.cnn_dense, need, cudaMemcpyDeviceToHost));
         return FUSION_OK;
