@@ -48,7 +48,7 @@ struct Geo {
     int hd, hh, hw;        // halo extents
     uint32_t plane_bytes;  // one 8-channel plane of the halo, 128-byte aligned
     uint32_t stage_bytes;  // one B stage
-    int ops;               // offsets per B stage
+    int rows_per_stage;    // (tz, ty) rows of kernel offsets per B stage (each row = the x taps)
     int nbs;               // B stages
     int na;                // A buffers
     int chunks;            // 16-channel chunks of the input
@@ -145,14 +145,15 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                     tc::tma_load_5d(sA + buf * a_bytes + j * g.plane_bytes, &tmap, &a_full[buf], c * 16 + j * 8,
                                     x0 * S + px - a.pad, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
                 ++ai;
-                for (int o0 = 0; o0 < noff; o0 += g.ops) {
-                    const int cnt = min(g.ops, noff - o0);
+                const int nrows = nz * ny;
+                for (int r0 = 0; r0 < nrows; r0 += g.rows_per_stage) {
+                    const int cnt = min(g.rows_per_stage, nrows - r0) * nx;
                     const int st = bi % g.nbs;
                     if (!tc::mbar_wait(&b_empty[st], ((bi / g.nbs) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
                     const uint32_t bytes = (uint32_t)cnt * N * 32;
                     tc::mbar_expect_tx(&b_full[st], bytes);
-                    tc::bulk_load(sB + st * g.stage_bytes, a.w + (size_t)(off_base + ph_off + o0) * N * 16, bytes,
-                                  &b_full[st]);
+                    tc::bulk_load(sB + st * g.stage_bytes, a.w + (size_t)(off_base + ph_off + r0 * nx) * N * 16,
+                                  bytes, &b_full[st]);
                     ++bi;
                 }
                 ph_off += noff;
@@ -171,24 +172,26 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                 const int noff = nz * ny * nx;
                 const int buf = ai % g.na;
                 if (!tc::mbar_wait(&a_full[buf], (ai / g.na) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
-                const uint32_t abase = tc::smem_u32(sA + buf * a_bytes);
-                for (int o0 = 0; o0 < noff; o0 += g.ops) {
-                    const int cnt = min(g.ops, noff - o0);
+                // descriptors advance by plain integer adds: the start-address field counts 16-byte rows
+                const uint64_t adesc0 = tc::desc_kmajor(tc::smem_u32(sA + buf * a_bytes), g.plane_bytes, sbo_a);
+                const int nrows = nz * ny;
+                for (int r0 = 0; r0 < nrows; r0 += g.rows_per_stage) {
+                    const int rend = min(r0 + g.rows_per_stage, nrows);
                     const int st = bi % g.nbs;
                     if (!tc::mbar_wait(&b_full[st], (bi / g.nbs) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
                     tc::tc_fence_after();
-                    const uint32_t bbase = tc::smem_u32(sB + st * g.stage_bytes);
-                    for (int q = 0; q < cnt; ++q) {
-                        const int o = o0 + q;
-                        const int tx = o % nx, ty = (o / nx) % ny, tz = o / (nx * ny);
-                        const uint64_t bd = tc::desc_kmajor(bbase + q * N * 32, N * 16, 128);
+                    uint64_t bdesc = tc::desc_kmajor(tc::smem_u32(sB + st * g.stage_bytes), N * 16, 128);
+                    for (int r = r0; r < rend; ++r) {
+                        const int tz = r / ny, ty = r - (r / ny) * ny;
+                        const uint64_t arow = adesc0 + (uint64_t)(tz * row_zy + ty * g.hw);
+                        for (int tx = 0; tx < nx; ++tx) {
+                            const uint32_t acc = first ? 0u : 1u;
 #pragma unroll
-                        for (int d = 0; d < T; ++d) {
-                            const uint32_t row = (uint32_t)(d + tz) * row_zy + (uint32_t)ty * g.hw + tx;
-                            const uint64_t ad = tc::desc_kmajor(abase + row * 16, g.plane_bytes, sbo_a);
-                            tc::mma_bf16(tbase + d * N, ad, bd, IDESC, first ? 0u : 1u);
+                            for (int d = 0; d < T; ++d)
+                                tc::mma_bf16(tbase + d * N, arow + (uint64_t)(tx + d * row_zy), bdesc, IDESC, acc);
+                            first = false;
+                            bdesc += (uint64_t)(N * 32 / 16);
                         }
-                        first = false;
                     }
                     tc::mma_commit(&b_empty[st]);
                     ++bi;
@@ -297,7 +300,7 @@ struct ConvTcPlan::Impl {
 ConvTcPlan::ConvTcPlan() : impl(new Impl()) {}
 ConvTcPlan::~ConvTcPlan() { delete impl; }
 
-int conv_tc_tile_slices(int c_out) { return c_out >= 256 ? 2 : 4; }
+int conv_tc_tile_slices(int c_out) { return c_out >= 256 ? 2 : c_out >= 128 ? 4 : 8; }
 
 size_t conv_tc_weight_elems(int cin_pad, int c_out, int k) { return (size_t)(cin_pad / 16) * k * k * k * 2 * c_out * 8; }
 
@@ -358,9 +361,9 @@ int conv_tc_plan(ConvTcPlan &plan, const void *x, int max_poses, int n_in, int c
     g.hh = 16 + ntmax - 1;
     g.hw = 8 + ntmax - 1;
     g.plane_bytes = ((uint32_t)(g.hd * g.hh * g.hw) * 16 + 127) / 128 * 128;
-    g.ops = 16384 / (c_out * 32);
-    if (g.ops < 1) g.ops = 1;
-    g.stage_bytes = ((uint32_t)g.ops * c_out * 32 + 127) / 128 * 128;
+    g.rows_per_stage = 16384 / (ntmax * c_out * 32);
+    if (g.rows_per_stage < 1) g.rows_per_stage = 1;
+    g.stage_bytes = ((uint32_t)(g.rows_per_stage * ntmax) * c_out * 32 + 127) / 128 * 128;
     g.nbs = 4;
     g.chunks = cin_pad / 16;
     const size_t bar_bytes = (size_t)(5 + 2 * g.nbs) * 8 + 16;
@@ -423,8 +426,8 @@ static void launch_t(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s) {
     ConvTcPlan::Impl &P = *plan.impl;
     switch (P.N) {
-    case 32: launch_t<32, 4>(P, B, s); break;
-    case 64: launch_t<64, 4>(P, B, s); break;
+    case 32: launch_t<32, 8>(P, B, s); break;
+    case 64: launch_t<64, 8>(P, B, s); break;
     case 128: launch_t<128, 4>(P, B, s); break;
     default: launch_t<256, 2>(P, B, s); break;
     }
