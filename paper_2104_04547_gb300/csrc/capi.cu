@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -189,7 +190,8 @@ struct fusion_model {
     } conv[FUSION_MAX_CONV];
     void *dense_w = nullptr;      // f32 or bf16 [cnn_dense][flat], flat in (D, H, W, C) order
     float *dense_b = nullptr;
-    bool bf16 = false;            // conv / pool / dense in bf16 (tensor cores)
+    bool bf16 = false;            // bf16 activations, pool and dense (tensor-core conv)
+    bool fp8 = false;             // conv operands in FP8 E4M3 (per-channel weight, per-pose activation scales)
     size_t esz = 4;               // bytes per grid / activation element
     ConvTcPlan tcplan[FUSION_MAX_CONV];
     int pool_n = 0, pool_c = 0, flat = 0, splits = 1;
@@ -209,6 +211,9 @@ struct fusion_model {
     int grid_cx = kGridCxF32;
     void *act[FUSION_MAX_CONV] = {};
     void *pool_out = nullptr;
+    void *qbuf = nullptr;         // FP8 input of the conv layer being computed
+    float *amax = nullptr, *qscale = nullptr;   // FP8: per-pose max |activation| and scale [max_poses]
+    float *conv_sw[FUSION_MAX_CONV] = {};       // FP8: per-output-channel weight scales
     float *dense_part = nullptr, *cnn_lat = nullptr;
     int32_t *e_beg[2] = {}, *e_deg[2] = {}, *e_col[2] = {};
     float *hbuf[2] = {}, *Tbuf[2][2] = {}, *xin = nullptr, *sg_lat = nullptr, *aff = nullptr;
@@ -330,9 +335,12 @@ int load_weights(fusion_model *m, const float *blob) {
         const float *w = take();
         const float *b = take();
         if (m->bf16) {
-            std::vector<uint16_t> t(conv_tc_weight_elems(cx, c.c_out, c.k));
-            conv_tc_arrange_weights(w, c.c_out, c.c_in, cx, c.k, c.stride, t.data());
-            RC(upload_raw(m, &m->conv[i].w, t.data(), t.size() * 2));
+            const int elem = m->fp8 ? 1 : 2;
+            std::vector<uint8_t> t(conv_tc_weight_bytes(cx, c.c_out, c.k, elem));
+            std::vector<float> sw(c.c_out, 1.f);
+            conv_tc_arrange_weights(w, c.c_out, c.c_in, cx, c.k, c.stride, elem, t.data(), sw.data());
+            RC(upload_raw(m, &m->conv[i].w, t.data(), t.size()));
+            if (m->fp8) RC(upload(m, &m->conv_sw[i], sw));
         } else {
             std::vector<float> t((size_t)k3 * cx * c.c_out, 0.f);
             for (int o = 0; o < c.c_out; ++o)
@@ -449,6 +457,16 @@ int alloc_workspace(fusion_model *m) {
         for (int i = 2; i < d.n_conv; ++i) m->act[i] = m->act[i % 2];
     }
     if (d.pool > 1) RC(dalloc_bytes(m, &m->pool_out, B * m->flat * m->esz));
+    if (m->fp8) {
+        size_t qmax = B * n3 * m->grid_cx;
+        for (int i = 1; i < d.n_conv; ++i) {
+            const Shape s = conv_out(d, i);
+            qmax = std::max(qmax, B * (size_t)s.n * s.n * s.n * s.c);
+        }
+        RC(dalloc_bytes(m, &m->qbuf, qmax));
+        RC(dalloc(m, &m->amax, B));
+        RC(dalloc(m, &m->qscale, B));
+    }
     RC(dalloc(m, &m->dense_part, (size_t)m->splits * B * d.cnn_dense));
     RC(dalloc(m, &m->cnn_lat, B * d.cnn_dense));
     for (int e = 0; e < 2; ++e) {
@@ -478,11 +496,29 @@ static int plan_tensor_core_convs(fusion_model *m) {
     const fusion_model_desc &d = m->d;
     for (int i = 0; i < d.n_conv; ++i) {
         const fusion_conv_desc &c = d.conv[i];
-        const void *x = (i == 0) ? m->grid : m->act[i - 1];
+        const void *xb = (i == 0) ? m->grid : m->act[i - 1];   // bf16 input (and residual source)
+        ConvTcSpec sp{};
+        sp.x = m->fp8 ? m->qbuf : xb;
+        sp.elem = m->fp8 ? 1 : 2;
+        sp.max_poses = d.max_poses;
+        sp.n_in = m->conv[i].n_in;
+        sp.cin_pad = m->conv[i].cx_in;
+        sp.w = m->conv[i].w;
+        sp.bias = m->conv[i].b;
+        sp.s_w = m->conv_sw[i];
+        sp.s_in = m->qscale;
+        sp.amax = (m->fp8 && i + 1 < d.n_conv) ? m->amax : nullptr;
+        sp.xres = xb;
+        sp.cres = m->conv[i].cx_in;
+        sp.y = m->act[i];
+        sp.n_out = m->conv[i].n_out;
+        sp.c_out = c.c_out;
+        sp.k = c.k;
+        sp.stride = c.stride;
+        sp.residual = c.residual;
+        sp.err = m->err;
         char why[256] = {0};
-        const int r = conv_tc_plan(m->tcplan[i], x, d.max_poses, m->conv[i].n_in, m->conv[i].cx_in, m->conv[i].w,
-                                   m->conv[i].b, m->act[i], m->conv[i].n_out, c.c_out, c.k, c.stride, c.residual,
-                                   m->err, why, sizeof(why));
+        const int r = conv_tc_plan(m->tcplan[i], sp, why, sizeof(why));
         if (r) return fail(r == -1 ? FUSION_EUNSUPPORTED : FUSION_ECUDA, std::string("conv layer ") +
                                                                              std::to_string(i) + ": " + why);
     }
@@ -526,8 +562,7 @@ int fusion_create(const fusion_model_desc *desc, const void *weights, size_t wei
     if (!out) return fail(FUSION_EINVAL, "out is NULL");
     std::string why;
     if (!check_desc(desc, &why)) return fail(FUSION_EINVAL, why);
-    if (desc->dtype == FUSION_FP8)
-        return fail(FUSION_EUNSUPPORTED, "this build computes the FP32 and BF16 paths; FP8 is not built yet");
+
     const size_t need = fusion_weights_bytes(desc);
     if (!weights || weights_bytes != need)
         return fail(FUSION_EWEIGHTS, "weights blob has " + std::to_string(weights_bytes) + " bytes, layout needs " +
@@ -556,7 +591,8 @@ int fusion_create(const fusion_model_desc *desc, const void *weights, size_t wei
     m->pool_c = f.c;
     m->flat = f.c * f.n * f.n * f.n;
     m->splits = dense_splits(m->flat);
-    m->bf16 = (m->d.dtype == FUSION_BF16);
+    m->bf16 = (m->d.dtype == FUSION_BF16 || m->d.dtype == FUSION_FP8);
+    m->fp8 = (m->d.dtype == FUSION_FP8);
     m->esz = m->bf16 ? 2 : 4;
     m->grid_cx = m->bf16 ? 32 : kGridCxF32;
     int rc = alloc_workspace(m);
@@ -658,7 +694,18 @@ int fusion_score(fusion_model *m, const fusion_poses *poses, int32_t n_poses, fl
     const void *x = m->grid;
     for (int i = 0; i < d.n_conv; ++i) {
         const fusion_conv_desc &c = d.conv[i];
-        if (m->bf16) {
+        if (m->fp8) {
+            // quantize this layer's bf16 input per pose, then run the FP8 conv
+            const Shape si = conv_out(d, i);
+            const size_t per_pose = (size_t)si.n * si.n * si.n * m->conv[i].cx_in;
+            if (i == 0) {
+                CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
+                launch_amax_per_pose(m->grid, B, per_pose, m->amax, st);
+            }
+            launch_quantize_per_pose(x, m->qbuf, B, per_pose, m->amax, m->qscale, st);
+            CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
+            conv_tc_launch(m->tcplan[i], B, st);
+        } else if (m->bf16) {
             conv_tc_launch(m->tcplan[i], B, st);
         } else {
             ConvArgs ca{static_cast<const float *>(x), static_cast<const float *>(m->conv[i].w), m->conv[i].b,

@@ -98,15 +98,35 @@ struct ConvTcPlan {
 };
 // Output slices per CTA for a layer with c_out output channels.
 int conv_tc_tile_slices(int c_out);
-// bf16 elements of the arranged weights of one layer.
-size_t conv_tc_weight_elems(int cin_pad, int c_out, int k);
-// Blob conv weights [co][ci][k][k][k] -> bf16 [16-ch chunk][offset, phase order][8-ch half][co][8].
-void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, uint16_t *out_bf16);
+// Bytes of the arranged weights of one layer (elem = 2 for bf16, 1 for FP8 E4M3).
+size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int elem);
+// Blob conv weights [co][ci][k][k][k] -> [channel chunk][offset, phase order][16-byte plane][co][16 bytes];
+// FP8 also returns the per-output-channel scales s_w[c_out] (weights = stored code * s_w).
+void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, int elem,
+                             uint8_t *out, float *s_w);
+struct ConvTcSpec {
+    const void *x;          // input (bf16 or FP8) [max_poses][n_in]^3[cin_pad], read by TMA
+    int elem;               // 2 = bf16, 1 = FP8 E4M3
+    int max_poses, n_in, cin_pad;
+    const void *w;          // arranged weights
+    const float *bias;      // [c_out]
+    const float *s_w;       // FP8: weight scales [c_out]
+    const float *s_in;      // FP8: per-pose input scales [max_poses]
+    float *amax;            // FP8: per-pose max |output| (atomic max), or null
+    const void *xres;       // bf16 residual source [max_poses][n_in]^3[cres]
+    int cres;
+    void *y;                // bf16 output [max_poses][n_out]^3[c_out]
+    int n_out, c_out, k, stride, residual;
+    unsigned *err;
+};
 // Build the plan; returns 0, or nonzero with a reason in `why`.
-int conv_tc_plan(ConvTcPlan &plan, const void *x, int max_poses, int n_in, int cin_pad, const void *w,
-                 const float *bias, void *y, int n_out, int c_out, int k, int stride, int residual, unsigned *err,
-                 char *why, size_t why_len);
+int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &spec, char *why, size_t why_len);
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s);
+
+// Per-pose FP8 quantization of bf16 NDHWC activations (per_pose elements per pose, a multiple of 8).
+void launch_amax_per_pose(const void *x_bf16, int B, size_t per_pose, float *amax, cudaStream_t s);
+void launch_quantize_per_pose(const void *x_bf16, void *q_fp8, int B, size_t per_pose, const float *amax, float *scale,
+                              cudaStream_t s);
 
 // ---- radius graph ----------------------------------------------------------
 

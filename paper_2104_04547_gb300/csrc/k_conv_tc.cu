@@ -20,6 +20,11 @@
 // same core-matrix layout) streams through a ring of shared-memory stages with
 // plain bulk copies.
 //
+// FP8 variant (E4M3 inputs, kind::f8f6f4, 32 channels per MMA): weights carry a
+// per-output-channel scale and activations a per-pose scale; the epilogue
+// multiplies the FP32 accumulator by both, and records the per-pose maximum
+// |output| so the next layer's input can be quantized with its own scale.
+//
 // Roles: warp 0 lane 0 issues the TMA loads, warp 1 owns tensor memory and
 // lane 0 issues the MMAs, warps 2-5 run the epilogue (tensor memory ->
 // registers, bias, ReLU, residual add, bf16 NDHWC stores).  Every wait is
@@ -31,6 +36,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 
@@ -55,8 +61,12 @@ struct Geo {
 };
 
 struct Args {
-    const __nv_bfloat16 *x;     // input [B][n_in]^3[cin] (read by the epilogue for residual blocks)
-    const __nv_bfloat16 *w;     // [chunks][k^3 offsets, phase order][2][N][8]
+    const __nv_bfloat16 *xres;  // bf16 copy of the input [B][n_in]^3[cres] (residual blocks)
+    int cres;                   // channels of xres
+    const uint8_t *w;           // [chunks][k^3 offsets, phase order][2 planes][N][16 bytes]
+    const float *s_in;          // FP8: per-pose input scale [B]
+    const float *s_w;           // FP8: per-output-channel weight scale [N]
+    float *amax;                // FP8: per-pose max |output| [B] (atomic max; may be null)
     const float *bias;          // [N]
     __nv_bfloat16 *y;           // [B][n_out]^3[N]
     int n_in, n_out, cin, k, stride, pad, residual;
@@ -79,11 +89,12 @@ __device__ __forceinline__ void phase_taps(const Args &a, int ph, int &pz, int &
     }
 }
 
-template <int N, int T>
+template <int N, int T, bool F8>
 __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_constant__ CUtensorMap tmap, Args a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr uint32_t TCOLS = (T * N <= 32) ? 32 : (T * N <= 64) ? 64 : (T * N <= 128) ? 128 : (T * N <= 256) ? 256 : 512;
-    constexpr uint32_t IDESC = tc::idesc_bf16(128, N);
+    constexpr uint32_t IDESC = F8 ? tc::idesc_e4m3(128, N) : tc::idesc_bf16(128, N);
+    constexpr int CPR = F8 ? 16 : 8;      // channels per 16-byte row (one core-matrix column)
     const Geo &g = a.g;
     const uint32_t a_bytes = 2 * g.plane_bytes;                     // buffer stride (128-byte aligned planes)
     const uint32_t a_tx = 2u * (uint32_t)(g.hd * g.hh * g.hw) * 16u;  // bytes the two TMA loads deliver
@@ -142,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                 tc::mbar_expect_tx(&a_full[buf], a_tx);
                 const int S = a.stride;
                 for (int j = 0; j < 2; ++j)
-                    tc::tma_load_5d(sA + buf * a_bytes + j * g.plane_bytes, &tmap, &a_full[buf], c * 16 + j * 8,
+                    tc::tma_load_5d(sA + buf * a_bytes + j * g.plane_bytes, &tmap, &a_full[buf], c * 2 * CPR + j * CPR,
                                     x0 * S + px - a.pad, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
                 ++ai;
                 const int nrows = nz * ny;
@@ -152,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                     if (!tc::mbar_wait(&b_empty[st], ((bi / g.nbs) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
                     const uint32_t bytes = (uint32_t)cnt * N * 32;
                     tc::mbar_expect_tx(&b_full[st], bytes);
-                    tc::bulk_load(sB + st * g.stage_bytes, a.w + (size_t)(off_base + ph_off + r0 * nx) * N * 16,
+                    tc::bulk_load(sB + st * g.stage_bytes, a.w + (size_t)(off_base + ph_off + r0 * nx) * N * 32,
                                   bytes, &b_full[st]);
                     ++bi;
                 }
@@ -188,7 +199,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                             const uint32_t acc = first ? 0u : 1u;
 #pragma unroll
                             for (int d = 0; d < T; ++d)
-                                tc::mma_bf16(tbase + d * N, arow + (uint64_t)(tx + d * row_zy), bdesc, IDESC, acc);
+                                if constexpr (F8)
+                                    tc::mma_e4m3(tbase + d * N, arow + (uint64_t)(tx + d * row_zy), bdesc, IDESC, acc);
+                                else
+                                    tc::mma_bf16(tbase + d * N, arow + (uint64_t)(tx + d * row_zy), bdesc, IDESC, acc);
                             first = false;
                             bdesc += (uint64_t)(N * 32 / 16);
                         }
@@ -211,6 +225,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
         tc::tc_fence_after();
         if (ok && !*abort_flag) {
             const int yy = y0 + h, xx = x0 + w;
+            const float sx = F8 ? a.s_in[b] : 1.f;
+            float vmax = 0.f;
             for (int d = 0; d < T; ++d) {
                 const int zz = z0 + d;
                 const bool valid = zz < a.n_out && yy < a.n_out && xx < a.n_out;
@@ -223,9 +239,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                     if (!valid) continue;
                     float v[32];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = fmaxf(__uint_as_float(acc[j]) + a.bias[cc * 32 + j], 0.f);
+                    for (int j = 0; j < 32; ++j) {
+                        float t = __uint_as_float(acc[j]);
+                        if constexpr (F8) t *= sx * a.s_w[cc * 32 + j];
+                        v[j] = fmaxf(t + a.bias[cc * 32 + j], 0.f);
+                    }
                     if (a.residual) {
-                        const uint4 *src = reinterpret_cast<const uint4 *>(a.x + vox * a.cin + cc * 32);
+                        const uint4 *src = reinterpret_cast<const uint4 *>(a.xres + vox * a.cres + cc * 32);
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const uint4 t4 = src[u];
@@ -244,10 +264,21 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                         uint4 t4;
                         __nv_bfloat162 *hp = reinterpret_cast<__nv_bfloat162 *>(&t4);
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) hp[e] = __floats2bfloat162_rn(v[u * 8 + 2 * e], v[u * 8 + 2 * e + 1]);
+                        for (int e = 0; e < 4; ++e) {
+                            hp[e] = __floats2bfloat162_rn(v[u * 8 + 2 * e], v[u * 8 + 2 * e + 1]);
+                            if constexpr (F8) {
+                                const float2 r = __bfloat1622float2(hp[e]);
+                                vmax = fmaxf(vmax, fmaxf(fabsf(r.x), fabsf(r.y)));
+                            }
+                        }
                         dst[u] = t4;
                     }
                 }
+            }
+            if constexpr (F8) {
+                for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+                if (lane == 0 && a.amax && vmax > 0.f)
+                    atomicMax(reinterpret_cast<unsigned *>(a.amax + b), __float_as_uint(vmax));
             }
         }
     }
@@ -293,6 +324,7 @@ struct ConvTcPlan::Impl {
     CUtensorMap tmap;
     Args args;
     int N = 0, T = 0;
+    bool f8 = false;
     size_t smem = 0;
     unsigned grid = 0;
 };
@@ -302,13 +334,58 @@ ConvTcPlan::~ConvTcPlan() { delete impl; }
 
 int conv_tc_tile_slices(int c_out) { return c_out >= 256 ? 2 : c_out >= 128 ? 4 : 8; }
 
-size_t conv_tc_weight_elems(int cin_pad, int c_out, int k) { return (size_t)(cin_pad / 16) * k * k * k * 2 * c_out * 8; }
+size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int elem) {
+    return (size_t)cin_pad * elem * k * k * k * c_out;
+}
 
-void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, uint16_t *out_bf16) {
-    // blob layout w[co][ci][kd][kh][kw] -> [chunk][offset in phase order][half][co][8]
+// float -> E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; largest finite 448, no
+// infinities), round to nearest even, saturating to +-448.
+static uint8_t e4m3_from_float(float x) {
+    const uint8_t sign = (x < 0.f) ? 0x80 : 0x00;
+    double a = std::fabs((double)x);
+    if (!(a > 0.0)) return sign;
+    if (a >= 448.0) return sign | 0x7E;
+    int e;
+    std::frexp(a, &e);                     // a = f * 2^e, f in [0.5, 1)
+    int E = e - 1;                         // a in [2^E, 2^(E+1))
+    if (E < -6) E = -6;                    // subnormal range shares the 2^-9 quantum
+    const double quantum = std::ldexp(1.0, E - 3);
+    double r = std::nearbyint(a / quantum) * quantum;   // default rounding mode: ties to even
+    if (r > 448.0) r = 448.0;
+    if (r == 0.0) return sign;
+    if (r < std::ldexp(1.0, -6)) {         // subnormal: mantissa m in 1..7, value m * 2^-9
+        const int m = (int)std::lround(r / std::ldexp(1.0, -9));
+        return sign | (uint8_t)m;
+    }
+    int er;
+    std::frexp(r, &er);
+    const int Er = er - 1;
+    const int m = (int)std::lround((r / std::ldexp(1.0, Er) - 1.0) * 8.0);
+    return sign | (uint8_t)(((Er + 7) << 3) | m);
+}
+
+static uint16_t bf16_from_float(float v) {
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);       // round to nearest even
+    return (uint16_t)(u >> 16);
+}
+
+void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, int elem,
+                             uint8_t *out, float *s_w) {
+    // blob layout w[co][ci][kd][kh][kw] -> [chunk][offset in phase order][16-byte plane][co][16 bytes]
+    const int cpr = elem == 2 ? 8 : 16;                // channels per 16-byte row
     const int nph = stride == 1 ? 1 : 8;
+    const int k3 = k * k * k;
+    if (elem == 1) {
+        for (int co = 0; co < c_out; ++co) {
+            float mx = 0.f;
+            for (int q = 0; q < c_in * k3; ++q) mx = std::fmax(mx, std::fabs(w[(size_t)co * c_in * k3 + q]));
+            s_w[co] = mx > 0.f ? mx / 448.f : 1.f;
+        }
+    }
     size_t idx = 0;
-    for (int c = 0; c < cin_pad / 16; ++c) {
+    for (int c = 0; c < cin_pad / (2 * cpr); ++c) {
         for (int ph = 0; ph < nph; ++ph) {
             int pz = 0, py = 0, px = 0, nz = k, ny = k, nx = k;
             if (stride == 2) {
@@ -321,38 +398,40 @@ void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, i
                         const int kd = pz + stride * tz, kh = py + stride * ty, kw = px + stride * tx;
                         for (int half = 0; half < 2; ++half)
                             for (int co = 0; co < c_out; ++co)
-                                for (int e = 0; e < 8; ++e) {
-                                    const int ci = c * 16 + half * 8 + e;
+                                for (int e = 0; e < cpr; ++e) {
+                                    const int ci = c * 2 * cpr + half * cpr + e;
                                     float v = 0.f;
                                     if (ci < c_in) v = w[((((size_t)co * c_in + ci) * k + kd) * k + kh) * k + kw];
-                                    // round to nearest even bf16
-                                    uint32_t u;
-                                    memcpy(&u, &v, 4);
-                                    u += 0x7FFFu + ((u >> 16) & 1u);
-                                    out_bf16[idx++] = (uint16_t)(u >> 16);
+                                    if (elem == 2) {
+                                        const uint16_t h = bf16_from_float(v);
+                                        memcpy(out + idx, &h, 2);
+                                        idx += 2;
+                                    } else {
+                                        out[idx++] = e4m3_from_float(v / s_w[co]);
+                                    }
                                 }
                     }
         }
     }
 }
 
-int conv_tc_plan(ConvTcPlan &plan, const void *x, int max_poses, int n_in, int cin_pad, const void *w,
-                 const float *bias, void *y, int n_out, int c_out, int k, int stride, int residual, unsigned *err,
-                 char *why, size_t why_len) {
+int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_len) {
     ConvTcPlan::Impl &P = *plan.impl;
+    const int c_out = sp.c_out, k = sp.k, stride = sp.stride;
     const int T = conv_tc_tile_slices(c_out);
+    const int chunk_ch = sp.elem == 2 ? 16 : 32;
     if (c_out != 32 && c_out != 64 && c_out != 128 && c_out != 256) {
         snprintf(why, why_len, "tensor-core conv needs c_out in {32, 64, 128, 256}");
         return -1;
     }
-    if (cin_pad % 16 != 0 || (stride != 1 && stride != 2)) {
-        snprintf(why, why_len, "tensor-core conv needs input channels padded to 16 and stride 1 or 2");
+    if (sp.cin_pad % chunk_ch != 0 || (stride != 1 && stride != 2) || (sp.elem != 1 && sp.elem != 2)) {
+        snprintf(why, why_len, "tensor-core conv needs input channels padded to %d and stride 1 or 2", chunk_ch);
         return -1;
     }
     Geo g{};
-    g.nbx = (n_out + 7) / 8;
-    g.nby = (n_out + 15) / 16;
-    g.nbz = (n_out + T - 1) / T;
+    g.nbx = (sp.n_out + 7) / 8;
+    g.nby = (sp.n_out + 15) / 16;
+    g.nbz = (sp.n_out + T - 1) / T;
     g.nphase = stride == 1 ? 1 : 8;
     g.ntap[0] = stride == 1 ? k : (k + 1) / 2;
     g.ntap[1] = stride == 1 ? k : k / 2;
@@ -361,11 +440,13 @@ int conv_tc_plan(ConvTcPlan &plan, const void *x, int max_poses, int n_in, int c
     g.hh = 16 + ntmax - 1;
     g.hw = 8 + ntmax - 1;
     g.plane_bytes = ((uint32_t)(g.hd * g.hh * g.hw) * 16 + 127) / 128 * 128;
-    g.rows_per_stage = 16384 / (ntmax * c_out * 32);
+    // about 32 KB of weights per stage: fewer stage hand-offs per MMA measured faster than
+    // deeper rings of smaller stages
+    g.rows_per_stage = 32768 / (ntmax * c_out * 32);
     if (g.rows_per_stage < 1) g.rows_per_stage = 1;
     g.stage_bytes = ((uint32_t)(g.rows_per_stage * ntmax) * c_out * 32 + 127) / 128 * 128;
-    g.nbs = 4;
-    g.chunks = cin_pad / 16;
+    g.nbs = 3;
+    g.chunks = sp.cin_pad / chunk_ch;
     const size_t bar_bytes = (size_t)(5 + 2 * g.nbs) * 8 + 16;
     const size_t limit = 227 * 1024;
     const size_t b_total = (size_t)g.nbs * g.stage_bytes;
@@ -385,52 +466,65 @@ int conv_tc_plan(ConvTcPlan &plan, const void *x, int max_poses, int n_in, int c
         snprintf(why, why_len, "cuTensorMapEncodeTiled is not available");
         return -2;
     }
-    cuuint64_t dims[5] = {(cuuint64_t)cin_pad, (cuuint64_t)n_in, (cuuint64_t)n_in, (cuuint64_t)n_in, (cuuint64_t)max_poses};
-    cuuint64_t strides[4] = {(cuuint64_t)cin_pad * 2, (cuuint64_t)cin_pad * 2 * n_in,
-                             (cuuint64_t)cin_pad * 2 * n_in * n_in, (cuuint64_t)cin_pad * 2 * n_in * n_in * n_in};
-    cuuint32_t box[5] = {8, (cuuint32_t)(g.hw * stride), (cuuint32_t)(g.hh * stride), (cuuint32_t)(g.hd * stride), 1};
+    const cuuint64_t rowb = (cuuint64_t)sp.cin_pad * sp.elem;   // bytes per voxel
+    const cuuint64_t n = (cuuint64_t)sp.n_in;
+    cuuint64_t dims[5] = {(cuuint64_t)sp.cin_pad, n, n, n, (cuuint64_t)sp.max_poses};
+    cuuint64_t strides[4] = {rowb, rowb * n, rowb * n * n, rowb * n * n * n};
+    cuuint32_t box[5] = {(cuuint32_t)(16 / sp.elem), (cuuint32_t)(g.hw * stride), (cuuint32_t)(g.hh * stride),
+                         (cuuint32_t)(g.hd * stride), 1};
     cuuint32_t estr[5] = {1, (cuuint32_t)stride, (cuuint32_t)stride, (cuuint32_t)stride, 1};
-    CUresult r = enc(&P.tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(&P.tmap, sp.elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 5,
+                     const_cast<void *>(sp.x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         snprintf(why, why_len, "cuTensorMapEncodeTiled failed (%d)", (int)r);
         return -2;
     }
     Args &A = P.args;
-    A.x = static_cast<const __nv_bfloat16 *>(x);
-    A.w = static_cast<const __nv_bfloat16 *>(w);
-    A.bias = bias;
-    A.y = static_cast<__nv_bfloat16 *>(y);
-    A.n_in = n_in;
-    A.n_out = n_out;
-    A.cin = cin_pad;
+    A.xres = static_cast<const __nv_bfloat16 *>(sp.xres);
+    A.cres = sp.cres;
+    A.w = static_cast<const uint8_t *>(sp.w);
+    A.s_in = sp.s_in;
+    A.s_w = sp.s_w;
+    A.amax = sp.amax;
+    A.bias = sp.bias;
+    A.y = static_cast<__nv_bfloat16 *>(sp.y);
+    A.n_in = sp.n_in;
+    A.n_out = sp.n_out;
+    A.cin = sp.cin_pad;
     A.k = k;
     A.stride = stride;
     A.pad = k / 2;
-    A.residual = residual;
+    A.residual = sp.residual;
     A.g = g;
-    A.err = err;
+    A.err = sp.err;
     P.N = c_out;
     P.T = T;
+    P.f8 = sp.elem == 1;
     P.grid = (unsigned)(g.nbx * g.nby * g.nbz);   // per pose; times B at launch
     return 0;
 }
 
-template <int N, int T>
+template <int N, int T, bool F8>
 static void launch_t(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
-    cudaFuncSetAttribute(conv3d_tc_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
-    conv3d_tc_kernel<N, T><<<P.grid * B, kThreads, P.smem, s>>>(P.tmap, P.args);
+    cudaFuncSetAttribute(conv3d_tc_kernel<N, T, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
+    conv3d_tc_kernel<N, T, F8><<<P.grid * B, kThreads, P.smem, s>>>(P.tmap, P.args);
+}
+
+template <bool F8>
+static void launch_n(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
+    switch (P.N) {
+    case 32: launch_t<32, 8, F8>(P, B, s); break;
+    case 64: launch_t<64, 8, F8>(P, B, s); break;
+    case 128: launch_t<128, 4, F8>(P, B, s); break;
+    default: launch_t<256, 2, F8>(P, B, s); break;
+    }
 }
 
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s) {
     ConvTcPlan::Impl &P = *plan.impl;
-    switch (P.N) {
-    case 32: launch_t<32, 8>(P, B, s); break;
-    case 64: launch_t<64, 8>(P, B, s); break;
-    case 128: launch_t<128, 4>(P, B, s); break;
-    default: launch_t<256, 2>(P, B, s); break;
-    }
+    if (P.f8) launch_n<true>(P, B, s);
+    else launch_n<false>(P, B, s);
 }
 
 }  // namespace fusion
