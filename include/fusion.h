@@ -34,6 +34,7 @@ extern "C" {
 #define FUSION_ECUDA        -5  /* a CUDA runtime call failed */
 #define FUSION_ETIMEOUT     -6  /* a bounded device wait ran out */
 #define FUSION_EUNSUPPORTED -7  /* descriptor valid but not supported by this build (dtype or shape) */
+#define FUSION_EAGAIN       -8  /* server: queue full, or the result is not ready yet */
 
 /* Compute dtypes of the CNN contractions (density, distances, pooling and head stay FP32). */
 #define FUSION_F32  0
@@ -157,12 +158,88 @@ int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst,
 /* Device time in milliseconds of each kernel group of the last fusion_score
  * call, measured with CUDA events on the model's stream.  Index:
  *   0 pose prep (validation, grid origin, per-atom weights)   1 voxelize
- *   2..9 conv layer 0..7                                      10 max-pool
+ *   2..9 conv layer 0..7 (FP8: with the layer's input quantization)   10 max-pool
  *   11 CNN dense                                              12 radius graph
  *   13 graph-convolution steps                                14 ligand gather
- *   15 fusion head
- * Entries of absent layers are 0.  `n` entries are written (n <= 16). */
+ *   15 fusion head                                            16 whole forward pass
+ * Entries 12-14 are elapsed times on the model's second stream, where the
+ * graph branch runs concurrently with the grid branch (so they overlap the
+ * conv entries).  Entries of absent layers are 0; with CUDA graphs only
+ * entry 16 is measured.
+ * `n` entries are written (n <= 17). */
 int fusion_last_timings(fusion_model *m, float *out, int32_t n);
+
+/* ---- batching: options and tile autotuning ---- */
+
+#define FUSION_OPT_CUDA_GRAPH 1   /* value 1: fusion_score replays a CUDA graph of the whole device-side
+                                     forward pass, captured on first use for each batch size (inputs are
+                                     copied into the model's own buffers first); 0: plain launches */
+
+/* Set a runtime option of a model (FUSION_OPT_*). */
+int fusion_set_option(fusion_model *m, int32_t option, int64_t value);
+
+/* Pick, for every conv layer of a tensor-core model (bf16 / fp8), the
+ * fastest tile configuration (output slices per CTA, kernel-offset rows per
+ * weight stage, weight stages) by timing every configuration that fits shared
+ * memory on the given batch (scored once first).  Replaces the layer plans;
+ * captured graphs are dropped.  FUSION_EUNSUPPORTED on the FP32 path. */
+int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses);
+
+/* Tile configuration of conv `layer`: out4 = {slices per CTA, rows per weight
+ * stage, weight stages, shared-memory bytes}. */
+int fusion_describe_conv(fusion_model *m, int32_t layer, int32_t *out4);
+
+/* ---- serving: continuous batching request loop ----
+ * The paper scores a job's poses in fixed batches and writes every result at
+ * job end, noting that results should be written as they are computed
+ * (Section 4.3).  A server scores poses one by one as they arrive: requests are
+ * queued, and each of its slots (a model replica with its own workspace and
+ * stream) repeatedly takes the queued poses (waiting at most batch_window_us
+ * for max_batch of them) and scores them as one batch.  While one slot's batch
+ * runs on the GPU, the other slots take the requests that arrived meanwhile,
+ * so batches overlap on the device.  A pose's result does not depend on the
+ * poses it was batched with. */
+typedef struct {
+    int32_t slots;             /* slots (batches in flight); 0 = up to 4, as the HBM budget admits */
+    int32_t max_batch;         /* poses per batch, 1 .. desc->max_poses */
+    double  batch_window_us;   /* longest wait for a batch to fill once a request is queued */
+    size_t  hbm_budget_bytes;  /* device memory the slots may use; 0 = no limit */
+    int32_t queue_capacity;    /* poses that may wait in the queue; beyond it submit returns FUSION_EAGAIN */
+} fusion_server_config;
+
+typedef struct {
+    int32_t slots;             /* slots admitted */
+    size_t  slot_bytes;        /* measured device footprint of one slot */
+    int64_t submitted, completed, rejected, failed, batches, queued, inflight;
+    double  gpu_busy_s;        /* summed wall time of the slots' scoring calls */
+} fusion_server_stats;
+
+typedef struct fusion_server fusion_server;
+
+/* Start a server on the current device: creates the slots (model replicas from
+ * desc and the weights blob, desc->max_poses >= cfg->max_batch) and one worker
+ * thread per slot. */
+int fusion_server_create(const fusion_model_desc *desc, const void *weights, size_t weights_bytes,
+                         const fusion_server_config *cfg, fusion_server **out);
+
+/* Queue one pose (host arrays xyz[n_atoms][3], feat[n_atoms][19], ligand atoms
+ * first; copied before return).  *ticket identifies its result.  Invalid poses
+ * return FUSION_EINVAL; a full queue returns FUSION_EAGAIN. */
+int fusion_server_submit(fusion_server *s, const float *xyz, const float *feat, int32_t n_atoms, int32_t n_lig,
+                         uint64_t *ticket);
+
+/* Non-blocking: FUSION_OK with the affinity and the latency from submission
+ * to completion (seconds) once the pose is scored (each result is returned
+ * once), FUSION_EAGAIN while it is pending. */
+int fusion_server_poll(fusion_server *s, uint64_t ticket, float *affinity, double *latency_s);
+
+/* Wait until every submitted pose is scored (FUSION_ETIMEOUT after timeout_s). */
+int fusion_server_drain(fusion_server *s, double timeout_s);
+
+int fusion_server_get_stats(fusion_server *s, fusion_server_stats *out);
+
+/* Stop: finishes queued work, joins the workers, frees the slots.  NULL-safe. */
+void fusion_server_destroy(fusion_server *s);
 
 /* ---- dense layer without any allocation ----
  * The paper has no counterpart to this entry point; it serves deployment.

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -225,13 +226,18 @@ struct fusion_model {
     float *h_aff = nullptr;
 
     cudaEvent_t ev[18] = {};
+    cudaStream_t sg_stream = nullptr;             // graph branch
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr, ev_sg[4] = {};
+    bool use_graph = false;                       // replay captured CUDA graphs, one per batch size
+    std::map<int, cudaGraphExec_t> graph_exec;
+    std::map<int, cudaGraph_t> graph;
 
     // last call
     int last_B = 0;
     std::vector<int32_t> last_off, last_nlig;
     const void *last_conv_out[FUSION_MAX_CONV] = {};
     const float *last_h = nullptr;
-    float last_ms[16] = {};
+    float last_ms[17] = {};
     int ev_map[16] = {};
 };
 
@@ -487,36 +493,45 @@ int alloc_workspace(fusion_model *m) {
     RC(halloc(m, &m->h_err, 4));
     RC(halloc(m, &m->h_aff, B));
     for (auto &e : m->ev) CU(cudaEventCreate(&e));
+    for (auto &e : m->ev_sg) CU(cudaEventCreate(&e));
+    CU(cudaEventCreateWithFlags(&m->fork_ev, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&m->join_ev, cudaEventDisableTiming));
+    CU(cudaStreamCreateWithFlags(&m->sg_stream, cudaStreamNonBlocking));
     return FUSION_OK;
 }
 
 }  // namespace
 
-static int plan_tensor_core_convs(fusion_model *m) {
+static ConvTcSpec conv_spec(fusion_model *m, int i) {
     const fusion_model_desc &d = m->d;
-    for (int i = 0; i < d.n_conv; ++i) {
-        const fusion_conv_desc &c = d.conv[i];
-        const void *xb = (i == 0) ? m->grid : m->act[i - 1];   // bf16 input (and residual source)
-        ConvTcSpec sp{};
-        sp.x = m->fp8 ? m->qbuf : xb;
-        sp.elem = m->fp8 ? 1 : 2;
-        sp.max_poses = d.max_poses;
-        sp.n_in = m->conv[i].n_in;
-        sp.cin_pad = m->conv[i].cx_in;
-        sp.w = m->conv[i].w;
-        sp.bias = m->conv[i].b;
-        sp.s_w = m->conv_sw[i];
-        sp.s_in = m->qscale;
-        sp.amax = (m->fp8 && i + 1 < d.n_conv) ? m->amax : nullptr;
-        sp.xres = xb;
-        sp.cres = m->conv[i].cx_in;
-        sp.y = m->act[i];
-        sp.n_out = m->conv[i].n_out;
-        sp.c_out = c.c_out;
-        sp.k = c.k;
-        sp.stride = c.stride;
-        sp.residual = c.residual;
-        sp.err = m->err;
+    const fusion_conv_desc &c = d.conv[i];
+    const void *xb = (i == 0) ? m->grid : m->act[i - 1];   // bf16 input (and residual source)
+    ConvTcSpec sp{};
+    sp.x = m->fp8 ? m->qbuf : xb;
+    sp.elem = m->fp8 ? 1 : 2;
+    sp.max_poses = d.max_poses;
+    sp.n_in = m->conv[i].n_in;
+    sp.cin_pad = m->conv[i].cx_in;
+    sp.w = m->conv[i].w;
+    sp.bias = m->conv[i].b;
+    sp.s_w = m->conv_sw[i];
+    sp.s_in = m->qscale;
+    sp.amax = (m->fp8 && i + 1 < d.n_conv) ? m->amax : nullptr;
+    sp.xres = xb;
+    sp.cres = m->conv[i].cx_in;
+    sp.y = m->act[i];
+    sp.n_out = m->conv[i].n_out;
+    sp.c_out = c.c_out;
+    sp.k = c.k;
+    sp.stride = c.stride;
+    sp.residual = c.residual;
+    sp.err = m->err;
+    return sp;
+}
+
+static int plan_tensor_core_convs(fusion_model *m) {
+    for (int i = 0; i < m->d.n_conv; ++i) {
+        ConvTcSpec sp = conv_spec(m, i);
         char why[256] = {0};
         const int r = conv_tc_plan(m->tcplan[i], sp, why, sizeof(why));
         if (r) return fail(r == -1 ? FUSION_EUNSUPPORTED : FUSION_ECUDA, std::string("conv layer ") +
@@ -548,8 +563,18 @@ void fusion_destroy(fusion_model *m) {
     cudaGetDevice(&prev);
     cudaSetDevice(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);
+    for (auto &g : m->graph_exec) cudaGraphExecDestroy(g.second);
+    for (auto &g : m->graph) cudaGraphDestroy(g.second);
     for (auto &e : m->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : m->ev_sg)
+        if (e) cudaEventDestroy(e);
+    if (m->fork_ev) cudaEventDestroy(m->fork_ev);
+    if (m->join_ev) cudaEventDestroy(m->join_ev);
+    if (m->sg_stream) {
+        cudaStreamSynchronize(m->sg_stream);
+        cudaStreamDestroy(m->sg_stream);
+    }
     for (void *p : m->allocs) cudaFree(p);
     for (void *p : m->host_allocs) cudaFreeHost(p);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -614,6 +639,176 @@ static int check_launch(const char *what) {
     return FUSION_OK;
 }
 
+static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, const int32_t *off_d,
+                           const int32_t *nlig_d, const float *xyz_d, const float *feat_d, bool timed, int *map) {
+    const fusion_model_desc &d = m->d;
+    cudaStream_t st = m->stream;
+    CU(cudaMemsetAsync(m->err, 0, 4 * sizeof(unsigned), st));
+
+    int ei = 0;
+    auto mark = [&]() {
+        if (timed) cudaEventRecord(m->ev[ei], st);
+        ++ei;
+    };
+    mark();
+
+    // pose prep + voxelize
+    PrepArgs pa{off_d, nlig_d, xyz_d, B, d.max_atoms, d.grid_n, d.grid_h, d.sigma, d.support,
+                m->origin, m->atom_vox, m->atom_w, m->err};
+    launch_prep(pa, st);
+    RC(check_launch("prep"));
+    map[0] = ei; mark();
+
+    // The graph branch (radius graph, gated graph convolution, ligand gather)
+    // is independent of the grid branch until the head: it runs on a second
+    // stream, forked here and joined before the head.
+    cudaStream_t sgs = m->sg_stream;
+    CU(cudaEventRecord(m->fork_ev, st));
+    CU(cudaStreamWaitEvent(sgs, m->fork_ev, 0));
+    auto sg_mark = [&](int k) {
+        if (timed) cudaEventRecord(m->ev_sg[k], sgs);
+    };
+    sg_mark(0);
+    // radius graph
+    GraphArgs ga{off_d, xyz_d, B, d.max_atoms, d.max_degree, d.cut_cov, d.cut_nc,
+                 {m->e_beg[0], m->e_beg[1]}, {m->e_deg[0], m->e_deg[1]}, {m->e_col[0], m->e_col[1]}, m->err};
+    launch_radius_graph(ga, sgs);
+    RC(check_launch("radius_graph"));
+    sg_mark(1);
+
+    // SG-CNN stages: each stage's input goes to xin (the gather reads the last
+    // one); GRU steps ping-pong between hbuf[0] and hbuf[1].
+    const int H = d.sg_hidden;
+    int tcur = 0;   // Tbuf ping-pong index holding the current transforms
+    const float *h = nullptr;
+    for (int s = 0; s < d.sg_n_stages; ++s) {
+        SgTransformArgs ta{};
+        ta.feat = feat_d;
+        ta.A = A;
+        ta.H = H;
+        ta.init = (s == 0);
+        ta.A_dev = A_dev;
+        ta.h_in = h;            // read row by row before the same row of xin is written
+        ta.h_out = m->xin;
+        if (s > 0 && d.sg_gate) {
+            ta.gi_t = m->gi_t; ta.gbi = m->gbi; ta.gj_t = m->gj_t; ta.gbj = m->gbj;
+        }
+        for (int e = 0; e < 2; ++e) {
+            const bool use = (d.sg_edges[s] & (1 << e)) && d.sg_steps[s] > 0;
+            ta.we_t[e] = use ? m->we_t[s][e] : nullptr;
+            ta.be[e] = use ? m->be[s][e] : nullptr;
+            ta.T[e] = m->Tbuf[e][tcur];
+        }
+        launch_sg_transform(ta, sgs);
+        RC(check_launch("sg_transform"));
+        h = m->xin;
+        for (int k = 0; k < d.sg_steps[s]; ++k) {
+            SgStepArgs sa{};
+            sa.h_in = h;
+            float *hout = (h == m->hbuf[0]) ? m->hbuf[1] : m->hbuf[0];
+            sa.h_out = hout;
+            const bool more = (k + 1 < d.sg_steps[s]);
+            for (int e = 0; e < 2; ++e) {
+                const bool use = (d.sg_edges[s] & (1 << e)) != 0;
+                sa.T_in[e] = use ? m->Tbuf[e][tcur] : nullptr;
+                sa.T_out[e] = (use && more) ? m->Tbuf[e][tcur ^ 1] : nullptr;
+                sa.beg[e] = m->e_beg[e];
+                sa.deg[e] = m->e_deg[e];
+                sa.col[e] = m->e_col[e];
+                sa.we_t[e] = use ? m->we_t[s][e] : nullptr;
+                sa.be[e] = use ? m->be[s][e] : nullptr;
+            }
+            sa.wih_t = m->wih_t[s]; sa.whh_t = m->whh_t[s]; sa.bih = m->bih[s]; sa.bhh = m->bhh[s];
+            sa.A = A;
+            sa.H = H;
+            sa.A_dev = A_dev;
+            launch_sg_step(sa, sgs);
+            RC(check_launch("sg_step"));
+            h = hout;
+            tcur ^= 1;
+        }
+    }
+    m->last_h = h;
+    const float *stage_in = m->xin;
+    sg_mark(2);
+    SgGatherArgs gg{off_d, nlig_d, m->last_h, stage_in, m->gat_wg_t, m->gat_bg, m->gat_wo_t, m->gat_bo,
+                    m->sg_lat, B, H, d.sg_gather_width, d.sg_gather == FUSION_GATHER_GATED};
+    launch_sg_gather(gg, sgs);
+    RC(check_launch("sg_gather"));
+    sg_mark(3);
+    VoxArgs va{off_d, feat_d, m->atom_vox, m->atom_w, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx,
+               m->bf16 ? 1 : 0};
+    launch_voxelize(va, st);
+    RC(check_launch("voxelize"));
+    map[1] = ei; mark();
+
+    // 3D-CNN
+    const void *x = m->grid;
+    for (int i = 0; i < d.n_conv; ++i) {
+        const fusion_conv_desc &c = d.conv[i];
+        if (m->fp8) {
+            // quantize this layer's bf16 input per pose, then run the FP8 conv
+            const Shape si = conv_out(d, i);
+            const size_t per_pose = (size_t)si.n * si.n * si.n * m->conv[i].cx_in;
+            if (i == 0) {
+                CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
+                launch_amax_per_pose(m->grid, B, per_pose, m->amax, st);
+            }
+            launch_quantize_per_pose(x, m->qbuf, B, per_pose, m->amax, m->qscale, st);
+            CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
+            conv_tc_launch(m->tcplan[i], B, st);
+        } else if (m->bf16) {
+            conv_tc_launch(m->tcplan[i], B, st);
+        } else {
+            ConvArgs ca{static_cast<const float *>(x), static_cast<const float *>(m->conv[i].w), m->conv[i].b,
+                        static_cast<float *>(m->act[i]), B, m->conv[i].n_in, m->conv[i].n_out,
+                        m->conv[i].cx_in, c.c_out, c.k, c.stride, c.k / 2, c.residual};
+            launch_conv3d_f32(ca, st);
+        }
+        RC(check_launch("conv3d"));
+        m->last_conv_out[i] = m->act[i];
+        x = m->act[i];
+        map[2 + i] = ei; mark();
+    }
+    const void *flat_in = x;
+    if (d.pool > 1) {
+        const Shape s = conv_out(d, d.n_conv);
+        PoolArgs po{x, m->pool_out, B, s.n, m->pool_n, s.c, m->bf16 ? 1 : 0};
+        launch_maxpool(po, st);
+        RC(check_launch("maxpool"));
+        flat_in = m->pool_out;
+        map[10] = ei; mark();
+    }
+    DenseArgs da{flat_in, m->dense_w, m->dense_b, m->dense_part, m->cnn_lat, B, d.cnn_dense, m->flat, m->splits,
+                 m->bf16 ? 1 : 0, 1};
+    launch_dense(da, st);
+    RC(check_launch("dense"));
+    map[11] = ei; mark();
+
+    // join the graph branch
+    CU(cudaEventRecord(m->join_ev, m->sg_stream));
+    CU(cudaStreamWaitEvent(st, m->join_ev, 0));
+    mark();
+
+    HeadArgs ha{};
+    ha.cnn = m->cnn_lat;
+    ha.sg = m->sg_lat;
+    for (int l = 0; l < d.n_head; ++l) {
+        ha.wt[l] = m->head_wt[l];
+        ha.b[l] = m->head_b[l];
+        ha.width[l] = d.head[l];
+    }
+    ha.n_layers = d.n_head;
+    ha.B = B;
+    ha.Dc = d.cnn_dense;
+    ha.G = d.sg_gather_width;
+    ha.out = m->aff;
+    launch_head(ha, st);
+    RC(check_launch("head"));
+    map[15] = ei; mark();
+    return FUSION_OK;
+}
+
 int fusion_score(fusion_model *m, const fusion_poses *poses, int32_t n_poses, float *out_affinity) {
     if (!m || !poses) return fail(FUSION_EINVAL, "model or poses is NULL");
     if (n_poses == 0) return FUSION_OK;
@@ -670,163 +865,63 @@ int fusion_score(fusion_model *m, const fusion_poses *poses, int32_t n_poses, fl
         feat_d = poses->feat;
     }
     const int A = off[B];
-    CU(cudaMemsetAsync(m->err, 0, 4 * sizeof(unsigned), st));
-
-    int ei = 0;
-    auto mark = [&]() { cudaEventRecord(m->ev[ei++], st); };
     int map[16];
     for (int i = 0; i < 16; ++i) map[i] = -1;
-    mark();
-
-    // pose prep + voxelize
-    PrepArgs pa{off_d, nlig_d, xyz_d, B, d.max_atoms, d.grid_n, d.grid_h, d.sigma, d.support,
-                m->origin, m->atom_vox, m->atom_w, m->err};
-    launch_prep(pa, st);
-    RC(check_launch("prep"));
-    map[0] = ei; mark();
-    VoxArgs va{off_d, feat_d, m->atom_vox, m->atom_w, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx,
-               m->bf16 ? 1 : 0};
-    launch_voxelize(va, st);
-    RC(check_launch("voxelize"));
-    map[1] = ei; mark();
-
-    // 3D-CNN
-    const void *x = m->grid;
-    for (int i = 0; i < d.n_conv; ++i) {
-        const fusion_conv_desc &c = d.conv[i];
-        if (m->fp8) {
-            // quantize this layer's bf16 input per pose, then run the FP8 conv
-            const Shape si = conv_out(d, i);
-            const size_t per_pose = (size_t)si.n * si.n * si.n * m->conv[i].cx_in;
-            if (i == 0) {
-                CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
-                launch_amax_per_pose(m->grid, B, per_pose, m->amax, st);
+    if (m->use_graph) {
+        // the graph reads the model's own input buffers: device inputs are copied there first
+        if (poses->on_device) {
+            CU(cudaMemcpyAsync(m->in_off, off_d, sizeof(int32_t) * (B + 1), cudaMemcpyDeviceToDevice, st));
+            CU(cudaMemcpyAsync(m->in_nlig, nlig_d, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, st));
+            CU(cudaMemcpyAsync(m->in_xyz, xyz_d, sizeof(float) * (size_t)A * 3, cudaMemcpyDeviceToDevice, st));
+            CU(cudaMemcpyAsync(m->in_feat, feat_d, sizeof(float) * (size_t)A * kFeat, cudaMemcpyDeviceToDevice, st));
+        }
+        auto it = m->graph_exec.find(B);
+        if (it == m->graph_exec.end()) {
+            CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+            const int rc = enqueue_forward(m, B, B * d.max_atoms, m->in_off + B, m->in_off, m->in_nlig, m->in_xyz,
+                                           m->in_feat, false, map);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(st, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
             }
-            launch_quantize_per_pose(x, m->qbuf, B, per_pose, m->amax, m->qscale, st);
-            CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
-            conv_tc_launch(m->tcplan[i], B, st);
-        } else if (m->bf16) {
-            conv_tc_launch(m->tcplan[i], B, st);
-        } else {
-            ConvArgs ca{static_cast<const float *>(x), static_cast<const float *>(m->conv[i].w), m->conv[i].b,
-                        static_cast<float *>(m->act[i]), B, m->conv[i].n_in, m->conv[i].n_out,
-                        m->conv[i].cx_in, c.c_out, c.k, c.stride, c.k / 2, c.residual};
-            launch_conv3d_f32(ca, st);
-        }
-        RC(check_launch("conv3d"));
-        m->last_conv_out[i] = m->act[i];
-        x = m->act[i];
-        map[2 + i] = ei; mark();
-    }
-    const void *flat_in = x;
-    if (d.pool > 1) {
-        const Shape s = conv_out(d, d.n_conv);
-        PoolArgs po{x, m->pool_out, B, s.n, m->pool_n, s.c, m->bf16 ? 1 : 0};
-        launch_maxpool(po, st);
-        RC(check_launch("maxpool"));
-        flat_in = m->pool_out;
-        map[10] = ei; mark();
-    }
-    DenseArgs da{flat_in, m->dense_w, m->dense_b, m->dense_part, m->cnn_lat, B, d.cnn_dense, m->flat, m->splits,
-                 m->bf16 ? 1 : 0, 1};
-    launch_dense(da, st);
-    RC(check_launch("dense"));
-    map[11] = ei; mark();
-
-    // radius graph
-    GraphArgs ga{off_d, xyz_d, B, d.max_atoms, d.max_degree, d.cut_cov, d.cut_nc,
-                 {m->e_beg[0], m->e_beg[1]}, {m->e_deg[0], m->e_deg[1]}, {m->e_col[0], m->e_col[1]}, m->err};
-    launch_radius_graph(ga, st);
-    RC(check_launch("radius_graph"));
-    map[12] = ei; mark();
-
-    // SG-CNN stages: each stage's input goes to xin (the gather reads the last
-    // one); GRU steps ping-pong between hbuf[0] and hbuf[1].
-    const int H = d.sg_hidden;
-    int tcur = 0;   // Tbuf ping-pong index holding the current transforms
-    const float *h = nullptr;
-    for (int s = 0; s < d.sg_n_stages; ++s) {
-        SgTransformArgs ta{};
-        ta.feat = feat_d;
-        ta.A = A;
-        ta.H = H;
-        ta.init = (s == 0);
-        ta.h_in = h;            // read row by row before the same row of xin is written
-        ta.h_out = m->xin;
-        if (s > 0 && d.sg_gate) {
-            ta.gi_t = m->gi_t; ta.gbi = m->gbi; ta.gj_t = m->gj_t; ta.gbj = m->gbj;
-        }
-        for (int e = 0; e < 2; ++e) {
-            const bool use = (d.sg_edges[s] & (1 << e)) && d.sg_steps[s] > 0;
-            ta.we_t[e] = use ? m->we_t[s][e] : nullptr;
-            ta.be[e] = use ? m->be[s][e] : nullptr;
-            ta.T[e] = m->Tbuf[e][tcur];
-        }
-        launch_sg_transform(ta, st);
-        RC(check_launch("sg_transform"));
-        h = m->xin;
-        for (int k = 0; k < d.sg_steps[s]; ++k) {
-            SgStepArgs sa{};
-            sa.h_in = h;
-            float *hout = (h == m->hbuf[0]) ? m->hbuf[1] : m->hbuf[0];
-            sa.h_out = hout;
-            const bool more = (k + 1 < d.sg_steps[s]);
-            for (int e = 0; e < 2; ++e) {
-                const bool use = (d.sg_edges[s] & (1 << e)) != 0;
-                sa.T_in[e] = use ? m->Tbuf[e][tcur] : nullptr;
-                sa.T_out[e] = (use && more) ? m->Tbuf[e][tcur ^ 1] : nullptr;
-                sa.beg[e] = m->e_beg[e];
-                sa.deg[e] = m->e_deg[e];
-                sa.col[e] = m->e_col[e];
-                sa.we_t[e] = use ? m->we_t[s][e] : nullptr;
-                sa.be[e] = use ? m->be[s][e] : nullptr;
+            if (e != cudaSuccess) return fail(FUSION_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t e2 = cudaGraphInstantiate(&ex, g, 0);
+            if (e2 != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return fail(FUSION_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
             }
-            sa.wih_t = m->wih_t[s]; sa.whh_t = m->whh_t[s]; sa.bih = m->bih[s]; sa.bhh = m->bhh[s];
-            sa.A = A;
-            sa.H = H;
-            launch_sg_step(sa, st);
-            RC(check_launch("sg_step"));
-            h = hout;
-            tcur ^= 1;
+            m->graph[B] = g;
+            it = m->graph_exec.emplace(B, ex).first;
         }
+        cudaEventRecord(m->ev[0], st);
+        CU(cudaGraphLaunch(it->second, st));
+        cudaEventRecord(m->ev[1], st);
+    } else {
+        RC(enqueue_forward(m, B, A, nullptr, off_d, nlig_d, xyz_d, feat_d, true, map));
     }
-    m->last_h = h;
-    const float *stage_in = m->xin;
-    map[13] = ei; mark();
-    SgGatherArgs gg{off_d, nlig_d, m->last_h, stage_in, m->gat_wg_t, m->gat_bg, m->gat_wo_t, m->gat_bo,
-                    m->sg_lat, B, H, d.sg_gather_width, d.sg_gather == FUSION_GATHER_GATED};
-    launch_sg_gather(gg, st);
-    RC(check_launch("sg_gather"));
-    map[14] = ei; mark();
-
-    HeadArgs ha{};
-    ha.cnn = m->cnn_lat;
-    ha.sg = m->sg_lat;
-    for (int l = 0; l < d.n_head; ++l) {
-        ha.wt[l] = m->head_wt[l];
-        ha.b[l] = m->head_b[l];
-        ha.width[l] = d.head[l];
-    }
-    ha.n_layers = d.n_head;
-    ha.B = B;
-    ha.Dc = d.cnn_dense;
-    ha.G = d.sg_gather_width;
-    ha.out = m->aff;
-    launch_head(ha, st);
-    RC(check_launch("head"));
-    map[15] = ei; mark();
 
     CU(cudaMemcpyAsync(m->h_err, m->err, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     CU(cudaMemcpyAsync(m->h_aff, m->aff, sizeof(float) * B, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
 
     // timings
-    for (int i = 0; i < 16; ++i) {
-        m->last_ms[i] = 0.f;
-        if (map[i] < 1) continue;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, m->ev[map[i] - 1], m->ev[map[i]]);
-        m->last_ms[i] = ms;
+    for (int i = 0; i < 17; ++i) m->last_ms[i] = 0.f;
+    if (m->use_graph) {
+        cudaEventElapsedTime(&m->last_ms[16], m->ev[0], m->ev[1]);
+    } else {
+        int last = 0;
+        for (int i = 0; i < 16; ++i) {
+            if (map[i] < 1) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, m->ev[map[i] - 1], m->ev[map[i]]);
+            m->last_ms[i] = ms;
+            last = std::max(last, map[i]);
+        }
+        cudaEventElapsedTime(&m->last_ms[16], m->ev[0], m->ev[last]);
+        for (int k = 0; k < 3; ++k) cudaEventElapsedTime(&m->last_ms[12 + k], m->ev_sg[k], m->ev_sg[k + 1]);
     }
     m->last_B = B;
     m->last_off = off;
@@ -847,7 +942,7 @@ int fusion_score(fusion_model *m, const fusion_poses *poses, int32_t n_poses, fl
 }
 
 int fusion_last_timings(fusion_model *m, float *out, int32_t n) {
-    if (!m || !out || n < 0 || n > 16) return fail(FUSION_EINVAL, "bad arguments");
+    if (!m || !out || n < 0 || n > 17) return fail(FUSION_EINVAL, "bad arguments");
     for (int i = 0; i < n; ++i) out[i] = m->last_ms[i];
     return FUSION_OK;
 }
@@ -967,6 +1062,102 @@ int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst,
     default:
         return fail(FUSION_EINVAL, "unknown stage");
     }
+}
+
+int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
+    if (!m) return fail(FUSION_EINVAL, "NULL model");
+    switch (option) {
+    case FUSION_OPT_CUDA_GRAPH:
+        m->use_graph = value != 0;
+        return FUSION_OK;
+    default:
+        return fail(FUSION_EINVAL, "unknown option");
+    }
+}
+
+int fusion_describe_conv(fusion_model *m, int32_t layer, int32_t *out4) {
+    if (!m || !out4 || layer < 0 || layer >= m->d.n_conv) return fail(FUSION_EINVAL, "bad arguments");
+    if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "the FP32 path has no tensor-core tiles");
+    int T, rows, nbs;
+    size_t smem;
+    conv_tc_describe(m->tcplan[layer], &T, &rows, &nbs, &smem);
+    out4[0] = T;
+    out4[1] = rows;
+    out4[2] = nbs;
+    out4[3] = (int32_t)smem;
+    return FUSION_OK;
+}
+
+int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses) {
+    if (!m || !poses) return fail(FUSION_EINVAL, "NULL argument");
+    if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "autotuning applies to the tensor-core (bf16 / fp8) paths");
+    std::vector<float> out(std::max(1, n_poses));
+    float *dout = nullptr;
+    if (poses->on_device) {
+        CU(cudaMalloc(&dout, sizeof(float) * std::max(1, n_poses)));
+    }
+    const int rc = fusion_score(m, poses, n_poses, poses->on_device ? dout : out.data());
+    if (dout) cudaFree(dout);
+    if (rc) return rc;
+    const fusion_model_desc &d = m->d;
+    const int B = n_poses;
+    cudaStream_t st = m->stream;
+    cudaEvent_t e0 = m->ev[16], e1 = m->ev[17];
+    for (int i = 0; i < d.n_conv; ++i) {
+        const int co = d.conv[i].c_out;
+        std::vector<int> Ts = co <= 64 ? std::vector<int>{8, 4} : co == 128 ? std::vector<int>{4, 2} : std::vector<int>{2};
+        float best_ms = 1e30f;
+        int best[3] = {0, 0, 0};
+        auto prepare_input = [&]() {
+            if (!m->fp8) return;
+            // the FP8 input of layer i is re-derived from its bf16 input (the buffer holds another layer's)
+            const Shape si = conv_out(d, i);
+            const size_t per_pose = (size_t)si.n * si.n * si.n * m->conv[i].cx_in;
+            const void *xb = (i == 0) ? m->grid : m->act[i - 1];
+            cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st);
+            launch_amax_per_pose(xb, B, per_pose, m->amax, st);
+            launch_quantize_per_pose(xb, m->qbuf, B, per_pose, m->amax, m->qscale, st);
+        };
+        for (int T : Ts)
+            for (int rows : {1, 2, 3, 4, 6})
+                for (int nbs : {2, 3, 4}) {
+                    ConvTcPlan trial;
+                    ConvTcSpec sp = conv_spec(m, i);
+                    sp.T = T;
+                    sp.rows_per_stage = rows;
+                    sp.nbs = nbs;
+                    char why[256] = {0};
+                    if (conv_tc_plan(trial, sp, why, sizeof(why))) continue;   // does not fit: skip
+                    prepare_input();
+                    conv_tc_launch(trial, B, st);
+                    CU(cudaEventRecord(e0, st));
+                    for (int r = 0; r < 3; ++r) conv_tc_launch(trial, B, st);
+                    CU(cudaEventRecord(e1, st));
+                    CU(cudaStreamSynchronize(st));
+                    RC(check_launch("autotune conv"));
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best[0] = T;
+                        best[1] = rows;
+                        best[2] = nbs;
+                    }
+                }
+        if (best[0] == 0) return fail(FUSION_EUNSUPPORTED, "no tile configuration fits layer " + std::to_string(i));
+        ConvTcSpec sp = conv_spec(m, i);
+        sp.T = best[0];
+        sp.rows_per_stage = best[1];
+        sp.nbs = best[2];
+        char why[256] = {0};
+        if (conv_tc_plan(m->tcplan[i], sp, why, sizeof(why))) return fail(FUSION_ECUDA, why);
+    }
+    // captured graphs hold the old launch parameters
+    for (auto &g : m->graph_exec) cudaGraphExecDestroy(g.second);
+    for (auto &g : m->graph) cudaGraphDestroy(g.second);
+    m->graph_exec.clear();
+    m->graph.clear();
+    return FUSION_OK;
 }
 
 }  // extern "C"

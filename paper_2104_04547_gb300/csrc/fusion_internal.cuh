@@ -118,10 +118,14 @@ struct ConvTcSpec {
     void *y;                // bf16 output [max_poses][n_out]^3[c_out]
     int n_out, c_out, k, stride, residual;
     unsigned *err;
+    int T;                  // output slices per CTA (0: default for c_out)
+    int rows_per_stage;     // kernel-offset rows per weight stage (0: about 48 KB per stage)
+    int nbs;                // weight stages in the ring (0: 2)
 };
 // Build the plan; returns 0, or nonzero with a reason in `why`.
 int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &spec, char *why, size_t why_len);
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s);
+void conv_tc_describe(const ConvTcPlan &plan, int *T, int *rows_per_stage, int *nbs, size_t *smem);
 
 // Per-pose FP8 quantization of bf16 NDHWC activations (per_pose elements per pose, a multiple of 8).
 void launch_amax_per_pose(const void *x_bf16, int B, size_t per_pose, float *amax, cudaStream_t s);
@@ -155,6 +159,7 @@ struct SgTransformArgs {
     const float *gi_t, *gbi, *gj_t, *gbj;   // gate ([2H][H], [H], [H][H], [H]); nullptr: no gate
     int A, H;
     int init;              // 1: stage input = h0 (features zero-padded to H)
+    const int32_t *A_dev;  // non-null: the atom count is *A_dev (A is then the launch capacity)
 };
 void launch_sg_transform(const SgTransformArgs &a, cudaStream_t s);
 
@@ -167,6 +172,7 @@ struct SgStepArgs {
     const float *wih_t, *whh_t, *bih, *bhh;     // GRU: [H][3H], [H][3H], [3H], [3H]
     const float *we_t[2], *be[2];               // for T_out
     int A, H;
+    const int32_t *A_dev;  // non-null: the atom count is *A_dev (A is then the launch capacity)
 };
 void launch_sg_step(const SgStepArgs &a, cudaStream_t s);
 

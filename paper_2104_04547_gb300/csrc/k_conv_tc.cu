@@ -418,8 +418,14 @@ void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, i
 int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_len) {
     ConvTcPlan::Impl &P = *plan.impl;
     const int c_out = sp.c_out, k = sp.k, stride = sp.stride;
-    const int T = conv_tc_tile_slices(c_out);
+    const int T = sp.T > 0 ? sp.T : conv_tc_tile_slices(c_out);
     const int chunk_ch = sp.elem == 2 ? 16 : 32;
+    const bool t_ok = (c_out <= 64 && (T == 4 || T == 8)) || (c_out == 128 && (T == 2 || T == 4)) ||
+                      (c_out == 256 && T == 2);
+    if (!t_ok) {
+        snprintf(why, why_len, "unsupported output slices per CTA (%d) for %d output channels", T, c_out);
+        return -1;
+    }
     if (c_out != 32 && c_out != 64 && c_out != 128 && c_out != 256) {
         snprintf(why, why_len, "tensor-core conv needs c_out in {32, 64, 128, 256}");
         return -1;
@@ -440,12 +446,16 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     g.hh = 16 + ntmax - 1;
     g.hw = 8 + ntmax - 1;
     g.plane_bytes = ((uint32_t)(g.hd * g.hh * g.hw) * 16 + 127) / 128 * 128;
-    // about 32 KB of weights per stage: fewer stage hand-offs per MMA measured faster than
-    // deeper rings of smaller stages
-    g.rows_per_stage = 32768 / (ntmax * c_out * 32);
+    // about 48 KB of weights per stage in a ring of two: each stage hand-off costs a fixed few
+    // hundred cycles, and fewer, larger stages measured faster than deeper rings of smaller ones
+    g.rows_per_stage = sp.rows_per_stage > 0 ? sp.rows_per_stage : 49152 / (ntmax * c_out * 32);
     if (g.rows_per_stage < 1) g.rows_per_stage = 1;
     g.stage_bytes = ((uint32_t)(g.rows_per_stage * ntmax) * c_out * 32 + 127) / 128 * 128;
-    g.nbs = 3;
+    g.nbs = sp.nbs > 0 ? sp.nbs : 2;
+    if (g.nbs < 2 || g.nbs > 8) {
+        snprintf(why, why_len, "weight stages must be in [2, 8]");
+        return -1;
+    }
     g.chunks = sp.cin_pad / chunk_ch;
     const size_t bar_bytes = (size_t)(5 + 2 * g.nbs) * 8 + 16;
     const size_t limit = 227 * 1024;
@@ -513,12 +523,22 @@ static void launch_t(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
 
 template <bool F8>
 static void launch_n(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
-    switch (P.N) {
-    case 32: launch_t<32, 8, F8>(P, B, s); break;
-    case 64: launch_t<64, 8, F8>(P, B, s); break;
-    case 128: launch_t<128, 4, F8>(P, B, s); break;
+    switch (P.N * 16 + P.T) {
+    case 32 * 16 + 4: launch_t<32, 4, F8>(P, B, s); break;
+    case 32 * 16 + 8: launch_t<32, 8, F8>(P, B, s); break;
+    case 64 * 16 + 4: launch_t<64, 4, F8>(P, B, s); break;
+    case 64 * 16 + 8: launch_t<64, 8, F8>(P, B, s); break;
+    case 128 * 16 + 2: launch_t<128, 2, F8>(P, B, s); break;
+    case 128 * 16 + 4: launch_t<128, 4, F8>(P, B, s); break;
     default: launch_t<256, 2, F8>(P, B, s); break;
     }
+}
+
+void conv_tc_describe(const ConvTcPlan &plan, int *T, int *rows_per_stage, int *nbs, size_t *smem) {
+    *T = plan.impl->T;
+    *rows_per_stage = plan.impl->args.g.rows_per_stage;
+    *nbs = plan.impl->args.g.nbs;
+    *smem = plan.impl->smem;
 }
 
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s) {

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kWarps * 32) sg_transform_kernel(SgTransformAr
     __shared__ float sv[kWarps][2 * H];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kWarps + warp;
-    if (i >= a.A) return;
+    if (i >= (a.A_dev ? *a.A_dev : a.A)) return;
     float *v = sv[warp];
 #pragma unroll
     for (int j = 0; j < HJ; ++j) {
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
     __shared__ float sv[kWarps][2 * H];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kWarps + warp;
-    if (i >= a.A) return;
+    if (i >= (a.A_dev ? *a.A_dev : a.A)) return;
     float *v = sv[warp];
 
     // message: segment sum of the neighbours' transforms, edge type by edge type, row order

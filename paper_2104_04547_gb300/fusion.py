@@ -23,6 +23,7 @@ FUSION_ECAPACITY = -4
 FUSION_ECUDA = -5
 FUSION_ETIMEOUT = -6
 FUSION_EUNSUPPORTED = -7
+FUSION_EAGAIN = -8
 
 FUSION_F32, FUSION_BF16, FUSION_FP8 = 0, 1, 2
 DTYPES = {"f32": FUSION_F32, "bf16": FUSION_BF16, "fp8": FUSION_FP8}
@@ -33,10 +34,15 @@ STAGE_ORIGIN, STAGE_GRID, STAGE_CONV, STAGE_POOL, STAGE_CNN_LATENT = 1, 2, 3, 4,
 STAGE_EDGES_COV, STAGE_EDGES_NC, STAGE_SG_STATE, STAGE_SG_LATENT, STAGE_AFFINITY = 6, 7, 8, 9, 10
 
 TIMING_NAMES = ["prep", "voxelize"] + [f"conv{i}" for i in range(8)] + \
-               ["maxpool", "cnn_dense", "radius_graph", "sg_steps", "sg_gather", "head"]
+               ["maxpool", "cnn_dense", "radius_graph", "sg_steps", "sg_gather", "head", "total"]
+
+FUSION_OPT_CUDA_GRAPH = 1
 
 EXPORTED = ["fusion_weights_bytes", "fusion_create", "fusion_score", "fusion_destroy", "fusion_last_error",
-            "fusion_stage_bytes", "fusion_fetch_stage", "fusion_last_timings", "fusion_cnn_dense_noalloc"]
+            "fusion_stage_bytes", "fusion_fetch_stage", "fusion_last_timings", "fusion_cnn_dense_noalloc",
+            "fusion_server_create", "fusion_server_submit", "fusion_server_poll", "fusion_server_drain",
+            "fusion_server_get_stats", "fusion_server_destroy", "fusion_set_option", "fusion_autotune",
+            "fusion_describe_conv"]
 
 FUSION_NOALLOC_MAX_PARTIALS = 1 << 21
 
@@ -69,6 +75,17 @@ class fusion_poses(C.Structure):
                 ("feat", C.c_void_p), ("on_device", C.c_int32)]
 
 
+class fusion_server_config(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("batch_window_us", C.c_double),
+                ("hbm_budget_bytes", C.c_size_t), ("queue_capacity", C.c_int32)]
+
+
+class fusion_server_stats(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("slot_bytes", C.c_size_t), ("submitted", C.c_int64), ("completed", C.c_int64),
+                ("rejected", C.c_int64), ("failed", C.c_int64), ("batches", C.c_int64), ("queued", C.c_int64),
+                ("inflight", C.c_int64), ("gpu_busy_s", C.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"CUDA library not built ({LIB_PATH}); run paper_2104_04547_gb300.build.build()")
@@ -93,6 +110,25 @@ def _load():
     lib.fusion_cnn_dense_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                              C.c_int32, C.c_void_p, C.c_void_p]
     lib.fusion_cnn_dense_noalloc.restype = C.c_int
+    lib.fusion_server_create.argtypes = [P(fusion_model_desc), C.c_void_p, C.c_size_t, P(fusion_server_config),
+                                         P(C.c_void_p)]
+    lib.fusion_server_create.restype = C.c_int
+    lib.fusion_server_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, P(C.c_uint64)]
+    lib.fusion_server_submit.restype = C.c_int
+    lib.fusion_server_poll.argtypes = [C.c_void_p, C.c_uint64, P(C.c_float), P(C.c_double)]
+    lib.fusion_server_poll.restype = C.c_int
+    lib.fusion_server_drain.argtypes = [C.c_void_p, C.c_double]
+    lib.fusion_server_drain.restype = C.c_int
+    lib.fusion_server_get_stats.argtypes = [C.c_void_p, P(fusion_server_stats)]
+    lib.fusion_server_get_stats.restype = C.c_int
+    lib.fusion_server_destroy.argtypes = [C.c_void_p]
+    lib.fusion_server_destroy.restype = None
+    lib.fusion_set_option.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
+    lib.fusion_set_option.restype = C.c_int
+    lib.fusion_autotune.argtypes = [C.c_void_p, P(fusion_poses), C.c_int32]
+    lib.fusion_autotune.restype = C.c_int
+    lib.fusion_describe_conv.argtypes = [C.c_void_p, C.c_int32, P(C.c_int32)]
+    lib.fusion_describe_conv.restype = C.c_int
     return lib
 
 
@@ -173,6 +209,38 @@ def _ptr(x):
     raise TypeError(f"cannot take a pointer of {type(x)}")
 
 
+def _poses_struct(poses, n_poses, on_device, keep):
+    if not on_device:
+        arrs = {
+            "atom_off": np.ascontiguousarray(poses["atom_off"], dtype=np.int32),
+            "n_lig": np.ascontiguousarray(poses["n_lig"], dtype=np.int32),
+            "xyz": np.ascontiguousarray(poses["xyz"], dtype=np.float32),
+            "feat": np.ascontiguousarray(poses["feat"], dtype=np.float32),
+        }
+        keep.append(arrs)
+        src = arrs
+    else:
+        src = poses
+    return fusion_poses(n_poses, _ptr(src["atom_off"]), _ptr(src["n_lig"]), _ptr(src["xyz"]), _ptr(src["feat"]),
+                        int(on_device))
+
+
+def fusion_set_option(model, option: int, value: int) -> None:
+    _check(lib.fusion_set_option(model, option, value))
+
+
+def fusion_autotune(model, poses: dict, n_poses: int, on_device: bool = False) -> None:
+    keep = []
+    P = _poses_struct(poses, n_poses, on_device, keep)
+    _check(lib.fusion_autotune(model, C.byref(P), n_poses))
+
+
+def fusion_describe_conv(model, layer: int) -> dict:
+    out = (C.c_int32 * 4)()
+    _check(lib.fusion_describe_conv(model, layer, out))
+    return {"slices_per_cta": out[0], "rows_per_stage": out[1], "stages": out[2], "smem_bytes": out[3]}
+
+
 def fusion_score(model, poses: dict, n_poses: int, out, on_device: bool = False) -> None:
     """Score a packed batch.
 
@@ -216,7 +284,7 @@ def fusion_fetch_stage(model, stage: int, index: int = 0) -> np.ndarray:
     return out
 
 
-def fusion_last_timings(model, n: int = 16) -> np.ndarray:
+def fusion_last_timings(model, n: int = 17) -> np.ndarray:
     out = (C.c_float * n)()
     _check(lib.fusion_last_timings(model, out, n))
     return np.array(out[:], dtype=np.float32)
@@ -252,9 +320,98 @@ class Model:
     def timings(self):
         return dict(zip(TIMING_NAMES, fusion_last_timings(self.handle).tolist()))
 
+    def use_cuda_graphs(self, on=True):
+        fusion_set_option(self.handle, FUSION_OPT_CUDA_GRAPH, int(on))
+
+    def autotune(self, poses, n_poses=None, on_device=False):
+        if n_poses is None:
+            n_poses = len(poses["n_lig"])
+        fusion_autotune(self.handle, poses, n_poses, on_device)
+
+    def conv_tiles(self):
+        return [fusion_describe_conv(self.handle, i) for i in range(self.desc.n_conv)]
+
     def close(self):
         if self.handle:
             fusion_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fusion_server_create(desc: fusion_model_desc, weights, cfg: fusion_server_config) -> C.c_void_p:
+    buf = weights if isinstance(weights, (bytes, bytearray)) else np.ascontiguousarray(weights).tobytes()
+    h = C.c_void_p()
+    cbuf = C.create_string_buffer(bytes(buf), len(buf))
+    _check(lib.fusion_server_create(C.byref(desc), cbuf, len(buf), C.byref(cfg), C.byref(h)))
+    return h
+
+
+def fusion_server_submit(server, xyz, feat, n_lig: int) -> int | None:
+    """Ticket of the queued pose, or None when the queue is full (FUSION_EAGAIN)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    feat = np.ascontiguousarray(feat, dtype=np.float32)
+    t = C.c_uint64()
+    rc = lib.fusion_server_submit(server, xyz.ctypes.data, feat.ctypes.data, len(xyz), int(n_lig), C.byref(t))
+    if rc == FUSION_EAGAIN:
+        return None
+    _check(rc)
+    return t.value
+
+
+def fusion_server_poll(server, ticket: int):
+    """(affinity, latency_s) once scored, else None."""
+    a = C.c_float()
+    lat = C.c_double()
+    rc = lib.fusion_server_poll(server, ticket, C.byref(a), C.byref(lat))
+    if rc == FUSION_EAGAIN:
+        return None
+    _check(rc)
+    return a.value, lat.value
+
+
+def fusion_server_drain(server, timeout_s: float = 600.0) -> None:
+    _check(lib.fusion_server_drain(server, timeout_s))
+
+
+def fusion_server_get_stats(server) -> dict:
+    st = fusion_server_stats()
+    _check(lib.fusion_server_get_stats(server, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in fusion_server_stats._fields_}
+
+
+def fusion_server_destroy(server) -> None:
+    lib.fusion_server_destroy(server)
+
+
+class Server:
+    """Continuous-batching server: ``Server(model_dict, weights_blob, max_batch=64, ...)``."""
+
+    def __init__(self, model: dict, weights, max_batch=64, slots=0, batch_window_us=2000.0,
+                 hbm_budget_bytes=0, queue_capacity=1 << 20, max_atoms=1200, max_degree=64, dtype=None):
+        self.desc = make_desc(model, max_batch, max_atoms, max_degree, False, dtype)
+        cfg = fusion_server_config(slots, max_batch, batch_window_us, hbm_budget_bytes, queue_capacity)
+        self.handle = fusion_server_create(self.desc, weights, cfg)
+
+    def submit(self, xyz, feat, n_lig):
+        return fusion_server_submit(self.handle, xyz, feat, n_lig)
+
+    def poll(self, ticket):
+        return fusion_server_poll(self.handle, ticket)
+
+    def drain(self, timeout_s=600.0):
+        fusion_server_drain(self.handle, timeout_s)
+
+    def stats(self):
+        return fusion_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            fusion_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -319,3 +319,60 @@ def pose_slice(batch, p):
 def subset(batch, idx):
     """A new packed batch holding the poses idx (in that order)."""
     return pack([pose_slice(batch, int(p)) for p in idx])
+
+
+def _rotation(rng):
+    """Uniform random rotation from a unit quaternion drawn by rejection in the 4-ball."""
+    while True:
+        q = rng.random(4) * 2.0 - 1.0
+        n2 = float(q @ q)
+        if 1e-4 < n2 <= 1.0:
+            break
+    w, x, y, z = q / np.sqrt(n2)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+def make_pose_group(seed: int, n_rot: int = 10):
+    """Docked-pose stand-ins for one ligand: n_rot poses of the same ligand in the same pocket.
+
+    Ligand heavy-atom count log-normal with median 32 (clipped to 8..90); pocket
+    U[150, 1000] atoms.  Pose r rotates the ligand rigidly about its centroid by
+    a uniform random rotation and jitters each ligand atom by approximately
+    N(0, 0.5^2) A per axis.  Returns [(xyz, feat, n_lig)] * n_rot.
+    """
+    rng = np.random.default_rng(seed)
+    z = _approx_normal(rng)
+    n_lig = int(np.clip(np.rint(32.0 * np.exp(0.45 * z)), 8, 90))
+    n_pocket = int(rng.integers(150, 1001))
+    rings = max(1, min(4, n_lig // 12))
+    lig, nb, ring = _ligand(rng, n_lig, rings)
+    pocket = _pocket(rng, lig, n_pocket, n_lig)
+    shift = (rng.random(3) * 2.0 - 1.0) * 40.0
+    nb_all = nb + [[] for _ in range(n_pocket)]
+    ring_all = np.concatenate([ring, np.zeros(n_pocket, dtype=bool)])
+    feat = _features(rng, n_lig, n_pocket, nb_all, ring_all)
+    cen = lig.mean(axis=0)
+    out = []
+    for _ in range(n_rot):
+        R = _rotation(rng)
+        jit = np.array([[_approx_normal(rng) for _ in range(3)] for _ in range(n_lig)]) * 0.5
+        posed = (lig - cen) @ R.T + cen + jit
+        pos = np.concatenate([posed, pocket]) + shift
+        for _it in range(1000):
+            bad = _near_cutoff_pairs(pos.astype(np.float32))
+            if not bad:
+                break
+            for i, j in bad:
+                pos[j] += 0.01 * _unit(rng)
+        out.append((pos.astype(np.float32), feat, n_lig))
+    return out
+
+
+def make_uneven_pool(n_groups: int, n_rot: int = 10, seed0: int = 500000):
+    """Poses of n_groups ligands x n_rot rotations, in generation order."""
+    poses = []
+    for g in range(n_groups):
+        poses.extend(make_pose_group(seed0 + g, n_rot))
+    return poses

@@ -26,6 +26,7 @@ CASES = [
     # (file, model, weights seed, workload, sampled pose indices)
     ("full64_w0.json", "fusion-48grid-c64", 0, "batch64-lig20to50-pocket300to600", [0, 21, 42, 63]),
     ("tiny1_w0.json", "fusion-24grid-c32", 0, "pose1-lig24-pocket200", [0]),
+    ("batch256_w0.json", "fusion-48grid-c64", 0, "batch256-lig15to60-pocket250to800", [0, 85, 170, 255]),
 ]
 
 
