@@ -25,11 +25,14 @@
 // multiplies the FP32 accumulator by both, and records the per-pose maximum
 // |output| so the next layer's input can be quantized with its own scale.
 //
-// Roles: warp 0 lane 0 issues the TMA loads, warp 1 owns tensor memory and
-// lane 0 issues the MMAs, warps 2-5 run the epilogue (tensor memory ->
-// registers, bias, ReLU, residual add, bf16 NDHWC stores).  Every wait is
-// bounded; a wait that runs out sets FUSION_ERR_TIMEOUT and the CTA drains and
-// returns.
+// Roles: warp 0 lane 0 issues the TMA loads; warp 1 owns tensor memory; lane 0
+// of warps 1..NI issues the MMAs of T/NI slices each (one issuing thread was
+// measured to limit the MMA rate, so several warps issue; each commits its own
+// MMAs and the empty barriers count NI arrivals); then every warp but the
+// producer runs the epilogue (tensor memory -> registers, bias, ReLU, residual
+// add, bf16 NDHWC stores), two warps per tensor-memory lane quarter.  Every
+// wait is bounded; a wait that runs out sets FUSION_ERR_TIMEOUT and the CTA
+// drains and returns.
 #include "fusion_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -44,7 +47,8 @@ namespace fusion {
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kIssReq = 4;
+constexpr int kThreads = 32 * (1 + kIssReq + 4);
 constexpr uint64_t kWaitNs = 1000000000ull;    // 1 s
 
 struct Geo {
@@ -94,6 +98,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr uint32_t TCOLS = (T * N <= 32) ? 32 : (T * N <= 64) ? 64 : (T * N <= 128) ? 128 : (T * N <= 256) ? 256 : 512;
     constexpr uint32_t IDESC = F8 ? tc::idesc_e4m3(128, N) : tc::idesc_bf16(128, N);
+    constexpr int NI = kIssReq < T ? kIssReq : T;     // MMA-issuing warps, each owns T / NI slices
+    constexpr int DPI = T / NI;
     constexpr int CPR = F8 ? 16 : 8;      // channels per 16-byte row (one core-matrix column)
     const Geo &g = a.g;
     const uint32_t a_bytes = 2 * g.plane_bytes;                     // buffer stride (128-byte aligned planes)
@@ -119,9 +125,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     const uint64_t deadline = tc::globaltimer() + kWaitNs;
 
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) { tc::mbar_init(&a_full[i], 1); tc::mbar_init(&a_empty[i], 1); }
-        for (int i = 0; i < g.nbs; ++i) { tc::mbar_init(&b_full[i], 1); tc::mbar_init(&b_empty[i], 1); }
-        tc::mbar_init(acc_full, 1);
+        for (int i = 0; i < 2; ++i) { tc::mbar_init(&a_full[i], 1); tc::mbar_init(&a_empty[i], NI); }
+        for (int i = 0; i < g.nbs; ++i) { tc::mbar_init(&b_full[i], 1); tc::mbar_init(&b_empty[i], NI); }
+        tc::mbar_init(acc_full, NI);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -170,7 +176,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                 ph_off += noff;
             }
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp >= 1 && warp <= NI && lane == 0) {
+        const int d0 = (warp - 1) * DPI;
         // ---------------- MMA issuer ----------------
         int ai = 0, bi = 0;
         bool first = true;
@@ -198,11 +205,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                         for (int tx = 0; tx < nx; ++tx) {
                             const uint32_t acc = first ? 0u : 1u;
 #pragma unroll
-                            for (int d = 0; d < T; ++d)
+                            for (int dd = 0; dd < DPI; ++dd) {
+                                const int d = d0 + dd;
                                 if constexpr (F8)
                                     tc::mma_e4m3(tbase + d * N, arow + (uint64_t)(tx + d * row_zy), bdesc, IDESC, acc);
                                 else
                                     tc::mma_bf16(tbase + d * N, arow + (uint64_t)(tx + d * row_zy), bdesc, IDESC, acc);
+                            }
                             first = false;
                             bdesc += (uint64_t)(N * 32 / 16);
                         }
@@ -215,10 +224,19 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
             }
         }
         tc::mma_commit(acc_full);
-    } else if (warp >= 2) {
-        // ---------------- epilogue ----------------
+    }
+    if (warp >= 1) {
+        // ---------------- epilogue (the MMA warps join once they have issued everything) ----------------
+        __syncwarp();
         const int q = warp & 3;                 // tensor-memory lane quarter of this warp
         const int r = q * 32 + lane;            // M row = voxel of the slice
+        // warps 1 .. NI+4 share the slices of their lane quarter round robin
+        int cq = 0, rq = 0;
+        for (int w2 = 1; w2 <= NI + 4; ++w2)
+            if ((w2 & 3) == q) {
+                if (w2 < warp) ++rq;
+                ++cq;
+            }
         const int h = r >> 3, w = r & 7;
         const bool ok = tc::mbar_wait(acc_full, 0, deadline, a.err, FUSION_ERR_TIMEOUT);
         if (!ok) fail();
@@ -227,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
             const int yy = y0 + h, xx = x0 + w;
             const float sx = F8 ? a.s_in[b] : 1.f;
             float vmax = 0.f;
-            for (int d = 0; d < T; ++d) {
+            for (int d = rq; d < T; d += cq) {
                 const int zz = z0 + d;
                 const bool valid = zz < a.n_out && yy < a.n_out && xx < a.n_out;
                 const size_t vox = (((size_t)b * a.n_out + zz) * a.n_out + yy) * a.n_out + xx;
