@@ -229,6 +229,7 @@ struct fusion_model {
     cudaStream_t sg_stream = nullptr;             // graph branch
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr, ev_sg[4] = {};
     bool use_graph = false;                       // replay captured CUDA graphs, one per batch size
+    int pair_mode = -1;                           // conv slice pairs: -1 default per layer, 0 off, 1 on
     std::map<int, cudaGraphExec_t> graph_exec;
     std::map<int, cudaGraph_t> graph;
 
@@ -342,7 +343,7 @@ int load_weights(fusion_model *m, const float *blob) {
         const float *b = take();
         if (m->bf16) {
             const int elem = m->fp8 ? 1 : 2;
-            std::vector<uint8_t> t(conv_tc_weight_bytes(cx, c.c_out, c.k, elem));
+            std::vector<uint8_t> t(conv_tc_weight_bytes(cx, c.c_out, c.k, c.stride, elem));
             std::vector<float> sw(c.c_out, 1.f);
             conv_tc_arrange_weights(w, c.c_out, c.c_in, cx, c.k, c.stride, elem, t.data(), sw.data());
             RC(upload_raw(m, &m->conv[i].w, t.data(), t.size()));
@@ -526,6 +527,7 @@ static ConvTcSpec conv_spec(fusion_model *m, int i) {
     sp.stride = c.stride;
     sp.residual = c.residual;
     sp.err = m->err;
+    sp.pair = m->pair_mode;
     return sp;
 }
 
@@ -538,6 +540,14 @@ static int plan_tensor_core_convs(fusion_model *m) {
                                                                              std::to_string(i) + ": " + why);
     }
     return FUSION_OK;
+}
+
+// Captured graphs hold the launch parameters of the plans they were captured with.
+static void drop_graphs(fusion_model *m) {
+    for (auto &g : m->graph_exec) cudaGraphExecDestroy(g.second);
+    for (auto &g : m->graph) cudaGraphDestroy(g.second);
+    m->graph_exec.clear();
+    m->graph.clear();
 }
 
 int fusion::set_last_error(int code, const char *msg) { return fail(code, msg ? msg : ""); }
@@ -1070,21 +1080,36 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
     case FUSION_OPT_CUDA_GRAPH:
         m->use_graph = value != 0;
         return FUSION_OK;
+    case FUSION_OPT_CONV_SLICE_PAIRS: {
+        if (value < -1 || value > 1) return fail(FUSION_EINVAL, "slice-pair mode must be -1, 0 or 1");
+        if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "the FP32 path has no tensor-core tiles");
+        const int old = m->pair_mode;
+        m->pair_mode = (int)value;
+        const int rc = plan_tensor_core_convs(m);
+        if (rc) {
+            m->pair_mode = old;
+            plan_tensor_core_convs(m);
+            return rc;
+        }
+        drop_graphs(m);
+        return FUSION_OK;
+    }
     default:
         return fail(FUSION_EINVAL, "unknown option");
     }
 }
 
-int fusion_describe_conv(fusion_model *m, int32_t layer, int32_t *out4) {
-    if (!m || !out4 || layer < 0 || layer >= m->d.n_conv) return fail(FUSION_EINVAL, "bad arguments");
+int fusion_describe_conv(fusion_model *m, int32_t layer, int32_t *out5) {
+    if (!m || !out5 || layer < 0 || layer >= m->d.n_conv) return fail(FUSION_EINVAL, "bad arguments");
     if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "the FP32 path has no tensor-core tiles");
-    int T, rows, nbs;
+    int T, groups, nbs, pair;
     size_t smem;
-    conv_tc_describe(m->tcplan[layer], &T, &rows, &nbs, &smem);
-    out4[0] = T;
-    out4[1] = rows;
-    out4[2] = nbs;
-    out4[3] = (int32_t)smem;
+    conv_tc_describe(m->tcplan[layer], &T, &groups, &nbs, &smem, &pair);
+    out5[0] = T;
+    out5[1] = groups;
+    out5[2] = nbs;
+    out5[3] = (int32_t)smem;
+    out5[4] = pair;
     return FUSION_OK;
 }
 
@@ -1107,7 +1132,7 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
         const int co = d.conv[i].c_out;
         std::vector<int> Ts = co <= 64 ? std::vector<int>{8, 4} : co == 128 ? std::vector<int>{4, 2} : std::vector<int>{2};
         float best_ms = 1e30f;
-        int best[3] = {0, 0, 0};
+        int best[4] = {0, 0, 0, 0};
         auto prepare_input = [&]() {
             if (!m->fp8) return;
             // the FP8 input of layer i is re-derived from its bf16 input (the buffer holds another layer's)
@@ -1119,12 +1144,14 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
             launch_quantize_per_pose(xb, m->qbuf, B, per_pose, m->amax, m->qscale, st);
         };
         for (int T : Ts)
-            for (int rows : {1, 2, 3, 4, 6})
+            for (int pair : {1, 0})
+            for (int groups : {1, 2, 3, 4, 6})
                 for (int nbs : {2, 3, 4}) {
                     ConvTcPlan trial;
                     ConvTcSpec sp = conv_spec(m, i);
                     sp.T = T;
-                    sp.rows_per_stage = rows;
+                    sp.pair = pair;
+                    sp.groups_per_stage = groups;
                     sp.nbs = nbs;
                     char why[256] = {0};
                     if (conv_tc_plan(trial, sp, why, sizeof(why))) continue;   // does not fit: skip
@@ -1140,23 +1167,21 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
                     if (ms < best_ms) {
                         best_ms = ms;
                         best[0] = T;
-                        best[1] = rows;
+                        best[1] = groups;
                         best[2] = nbs;
+                        best[3] = pair;
                     }
                 }
         if (best[0] == 0) return fail(FUSION_EUNSUPPORTED, "no tile configuration fits layer " + std::to_string(i));
         ConvTcSpec sp = conv_spec(m, i);
         sp.T = best[0];
-        sp.rows_per_stage = best[1];
+        sp.groups_per_stage = best[1];
         sp.nbs = best[2];
+        sp.pair = best[3];
         char why[256] = {0};
         if (conv_tc_plan(m->tcplan[i], sp, why, sizeof(why))) return fail(FUSION_ECUDA, why);
     }
-    // captured graphs hold the old launch parameters
-    for (auto &g : m->graph_exec) cudaGraphExecDestroy(g.second);
-    for (auto &g : m->graph) cudaGraphDestroy(g.second);
-    m->graph_exec.clear();
-    m->graph.clear();
+    drop_graphs(m);
     return FUSION_OK;
 }
 

@@ -99,8 +99,9 @@ struct ConvTcPlan {
 // Output slices per CTA for a layer with c_out output channels.
 int conv_tc_tile_slices(int c_out);
 // Bytes of the arranged weights of one layer (elem = 2 for bf16, 1 for FP8 E4M3).
-size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int elem);
-// Blob conv weights [co][ci][k][k][k] -> [channel chunk][offset, phase order][16-byte plane][co][16 bytes];
+size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem);
+// Blob conv weights [co][ci][k][k][k] -> [channel chunk][phase][ty][tx][16-byte half][tz = nz..-1, the two ends
+// zero][co][16 bytes];
 // FP8 also returns the per-output-channel scales s_w[c_out] (weights = stored code * s_w).
 void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, int elem,
                              uint8_t *out, float *s_w);
@@ -119,13 +120,14 @@ struct ConvTcSpec {
     int n_out, c_out, k, stride, residual;
     unsigned *err;
     int T;                  // output slices per CTA (0: default for c_out)
-    int rows_per_stage;     // kernel-offset rows per weight stage (0: about 48 KB per stage)
+    int groups_per_stage;   // (ty, tx) kernel-offset groups per weight stage (0: about 48 KB per stage)
     int nbs;                // weight stages in the ring (0: 2)
+    int pair;               // 1: two output slices per MMA (N = 2 c_out); 0: one; -1: default for the layer
 };
 // Build the plan; returns 0, or nonzero with a reason in `why`.
 int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &spec, char *why, size_t why_len);
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s);
-void conv_tc_describe(const ConvTcPlan &plan, int *T, int *rows_per_stage, int *nbs, size_t *smem);
+void conv_tc_describe(const ConvTcPlan &plan, int *T, int *groups_per_stage, int *nbs, size_t *smem, int *pair);
 
 // Per-pose FP8 quantization of bf16 NDHWC activations (per_pose elements per pose, a multiple of 8).
 void launch_amax_per_pose(const void *x_bf16, int B, size_t per_pose, float *amax, cudaStream_t s);

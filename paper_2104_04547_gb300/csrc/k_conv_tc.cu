@@ -16,9 +16,22 @@
 // offset (K-major, no swizzle: an 8-row core matrix is one 8-voxel W-line of
 // 8 channels, 16 bytes per row, W-lines at a stride of the halo width).  So
 // each input element is fetched once per chunk, not once per offset.
-// Operand B (the weights of a few offsets, pre-arranged on the host in the
-// same core-matrix layout) streams through a ring of shared-memory stages with
-// plain bulk copies.
+//
+// Operand B (the weights) streams through a ring of shared-memory stages with
+// plain bulk copies.  The host arranges them per in-plane offset (ty, tx) as a
+// group [8-channel half][tz = nz, nz-1, .., 0, -1][co][16 bytes], the two end
+// entries zero.  Two uses of that order:
+//   - one slice, offset tz: B = the N rows of entry nz - tz;
+//   - a pair of adjacent output slices (z, z+1) and input plane z + u: the 2N
+//     rows from entry nz - u are W(tz = u) then W(tz = u - 1), which are the
+//     offsets that plane contributes to z and to z+1.  One M=128, N=2C MMA then
+//     serves both slices: the A tile is read from shared memory once for two
+//     slices, so the operand bytes per MMA clock drop from 6 KB / 32 to 8 KB /
+//     64 (at N = 64), for (nz + 1) / nz times the MMA work (the zero entries).
+// The accumulator of pair j spans columns [2jN, 2jN + 2N), so slice d sits at
+// column dN either way and the epilogue does not depend on the pairing.  The
+// summation order per output element is the same in both forms (offset groups
+// in (ty, tx) order, tz ascending, the paired form adding exact zeros).
 //
 // FP8 variant (E4M3 inputs, kind::f8f6f4, 32 channels per MMA): weights carry a
 // per-output-channel scale and activations a per-pose scale; the epilogue
@@ -26,13 +39,13 @@
 // |output| so the next layer's input can be quantized with its own scale.
 //
 // Roles: warp 0 lane 0 issues the TMA loads; warp 1 owns tensor memory; lane 0
-// of warps 1..NI issues the MMAs of T/NI slices each (one issuing thread was
-// measured to limit the MMA rate, so several warps issue; each commits its own
-// MMAs and the empty barriers count NI arrivals); then every warp but the
-// producer runs the epilogue (tensor memory -> registers, bias, ReLU, residual
-// add, bf16 NDHWC stores), two warps per tensor-memory lane quarter.  Every
-// wait is bounded; a wait that runs out sets FUSION_ERR_TIMEOUT and the CTA
-// drains and returns.
+// of warps 1..NI issues the MMAs of its share of the slices (or slice pairs):
+// one issuing thread was measured to limit the MMA rate, so several warps
+// issue; each commits its own MMAs and the empty barriers count NI arrivals.
+// Then every warp but the producer runs the epilogue (tensor memory ->
+// registers, bias, ReLU, residual add, bf16 NDHWC stores), two warps per
+// tensor-memory lane quarter.  Every wait is bounded; a wait that runs out sets
+// FUSION_ERR_TIMEOUT and the CTA drains and returns.
 #include "fusion_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -48,7 +61,8 @@ namespace fusion {
 namespace {
 
 constexpr int kIssReq = 4;
-constexpr int kThreads = 32 * (1 + kIssReq + 4);
+constexpr int kWarps = 1 + kIssReq + 4;
+constexpr int kThreads = 32 * kWarps;
 constexpr uint64_t kWaitNs = 1000000000ull;    // 1 s
 
 struct Geo {
@@ -58,16 +72,17 @@ struct Geo {
     int hd, hh, hw;        // halo extents
     uint32_t plane_bytes;  // one 8-channel plane of the halo, 128-byte aligned
     uint32_t stage_bytes;  // one B stage
-    int rows_per_stage;    // (tz, ty) rows of kernel offsets per B stage (each row = the x taps)
+    int groups_per_stage;  // (ty, tx) offset groups per B stage
     int nbs;               // B stages
     int na;                // A buffers
-    int chunks;            // 16-channel chunks of the input
+    int chunks;            // 16-channel (FP8: 32-channel) chunks of the input
+    uint32_t chunk_wbytes; // arranged weight bytes of one chunk (all phases)
 };
 
 struct Args {
     const __nv_bfloat16 *xres;  // bf16 copy of the input [B][n_in]^3[cres] (residual blocks)
     int cres;                   // channels of xres
-    const uint8_t *w;           // [chunks][k^3 offsets, phase order][2 planes][N][16 bytes]
+    const uint8_t *w;           // [chunk][phase][ty][tx][2 halves][tz = nz..-1][N][16 bytes]
     const float *s_in;          // FP8: per-pose input scale [B]
     const float *s_w;           // FP8: per-output-channel weight scale [N]
     float *amax;                // FP8: per-pose max |output| [B] (atomic max; may be null)
@@ -93,13 +108,16 @@ __device__ __forceinline__ void phase_taps(const Args &a, int ph, int &pz, int &
     }
 }
 
-template <int N, int T, bool F8>
+template <int N, int T, bool F8, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_constant__ CUtensorMap tmap, Args a) {
     extern __shared__ __align__(1024) unsigned char smem[];
+    static_assert(!PAIR || (T % 2 == 0 && 2 * N <= 256), "slice pairs need an even T and 2N <= 256");
     constexpr uint32_t TCOLS = (T * N <= 32) ? 32 : (T * N <= 64) ? 64 : (T * N <= 128) ? 128 : (T * N <= 256) ? 256 : 512;
-    constexpr uint32_t IDESC = F8 ? tc::idesc_e4m3(128, N) : tc::idesc_bf16(128, N);
-    constexpr int NI = kIssReq < T ? kIssReq : T;     // MMA-issuing warps, each owns T / NI slices
-    constexpr int DPI = T / NI;
+    constexpr int NM = PAIR ? 2 * N : N;  // MMA N
+    constexpr uint32_t IDESC = F8 ? tc::idesc_e4m3(128, NM) : tc::idesc_bf16(128, NM);
+    constexpr int UNITS = PAIR ? T / 2 : T;            // accumulators (slices or slice pairs)
+    constexpr int NI = kIssReq < UNITS ? kIssReq : UNITS;   // MMA-issuing warps, each owns UNITS / NI
+    constexpr int DPI = UNITS / NI;
     constexpr int CPR = F8 ? 16 : 8;      // channels per 16-byte row (one core-matrix column)
     const Geo &g = a.g;
     const uint32_t a_bytes = 2 * g.plane_bytes;                     // buffer stride (128-byte aligned planes)
@@ -146,14 +164,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     if (warp == 0 && lane == 0) {
         // ---------------- producer ----------------
         int &ai = prod_ai, &bi = prod_bi;
-        int off_base = 0;
         for (int c = 0; c < g.chunks && !*abort_flag; ++c) {
-            off_base = c * a.k * a.k * a.k;
-            int ph_off = 0;
+            const uint8_t *wc = a.w + (size_t)c * g.chunk_wbytes;
             for (int ph = 0; ph < g.nphase && !*abort_flag; ++ph) {
                 int pz, py, px, nz, ny, nx;
                 phase_taps(a, ph, pz, py, px, nz, ny, nx);
-                const int noff = nz * ny * nx;
                 const int buf = ai % g.na;
                 if (!tc::mbar_wait(&a_empty[buf], ((ai / g.na) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
                 tc::mbar_expect_tx(&a_full[buf], a_tx);
@@ -162,18 +177,18 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                     tc::tma_load_5d(sA + buf * a_bytes + j * g.plane_bytes, &tmap, &a_full[buf], c * 2 * CPR + j * CPR,
                                     x0 * S + px - a.pad, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
                 ++ai;
-                const int nrows = nz * ny;
-                for (int r0 = 0; r0 < nrows; r0 += g.rows_per_stage) {
-                    const int cnt = min(g.rows_per_stage, nrows - r0) * nx;
+                const int ngr = ny * nx;
+                const uint32_t gbytes = (uint32_t)(nz + 2) * N * 32;
+                for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
+                    const int cnt = min(g.groups_per_stage, ngr - g0);
                     const int st = bi % g.nbs;
                     if (!tc::mbar_wait(&b_empty[st], ((bi / g.nbs) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
-                    const uint32_t bytes = (uint32_t)cnt * N * 32;
+                    const uint32_t bytes = (uint32_t)cnt * gbytes;
                     tc::mbar_expect_tx(&b_full[st], bytes);
-                    tc::bulk_load(sB + st * g.stage_bytes, a.w + (size_t)(off_base + ph_off + r0 * nx) * N * 32,
-                                  bytes, &b_full[st]);
+                    tc::bulk_load(sB + st * g.stage_bytes, wc + (size_t)g0 * gbytes, bytes, &b_full[st]);
                     ++bi;
                 }
-                ph_off += noff;
+                wc += (size_t)ngr * gbytes;
             }
         }
     } else if (warp >= 1 && warp <= NI && lane == 0) {
@@ -187,34 +202,50 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
             for (int ph = 0; ph < g.nphase && !*abort_flag; ++ph) {
                 int pz, py, px, nz, ny, nx;
                 phase_taps(a, ph, pz, py, px, nz, ny, nx);
-                const int noff = nz * ny * nx;
                 const int buf = ai % g.na;
                 if (!tc::mbar_wait(&a_full[buf], (ai / g.na) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
                 // descriptors advance by plain integer adds: the start-address field counts 16-byte rows
                 const uint64_t adesc0 = tc::desc_kmajor(tc::smem_u32(sA + buf * a_bytes), g.plane_bytes, sbo_a);
-                const int nrows = nz * ny;
-                for (int r0 = 0; r0 < nrows; r0 += g.rows_per_stage) {
-                    const int rend = min(r0 + g.rows_per_stage, nrows);
+                const uint32_t lbo_b = (uint32_t)(nz + 2) * N * 16;    // between the two 8-channel halves
+                const int ngr = ny * nx;
+                for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
+                    const int gend = min(g0 + g.groups_per_stage, ngr);
                     const int st = bi % g.nbs;
                     if (!tc::mbar_wait(&b_full[st], (bi / g.nbs) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
                     tc::tc_fence_after();
-                    uint64_t bdesc = tc::desc_kmajor(tc::smem_u32(sB + st * g.stage_bytes), N * 16, 128);
-                    for (int r = r0; r < rend; ++r) {
-                        const int tz = r / ny, ty = r - (r / ny) * ny;
-                        const uint64_t arow = adesc0 + (uint64_t)(tz * row_zy + ty * g.hw);
-                        for (int tx = 0; tx < nx; ++tx) {
-                            const uint32_t acc = first ? 0u : 1u;
+                    uint64_t bgrp = tc::desc_kmajor(tc::smem_u32(sB + st * g.stage_bytes), lbo_b, 128);
+                    for (int gi = g0; gi < gend; ++gi) {
+                        const int ty = gi / nx, tx = gi - (gi / nx) * nx;
+                        const uint64_t arow = adesc0 + (uint64_t)(ty * g.hw + tx);
+                        if constexpr (PAIR) {
+                            // plane u of pair j (slices 2j, 2j+1): rows W(tz = u) | W(tz = u - 1) from entry nz - u
+                            for (int u = 0; u <= nz; ++u) {
+                                const uint32_t acc = first ? 0u : 1u;
+                                const uint64_t bdesc = bgrp + (uint64_t)((nz - u) * N);
 #pragma unroll
-                            for (int dd = 0; dd < DPI; ++dd) {
-                                const int d = d0 + dd;
-                                if constexpr (F8)
-                                    tc::mma_e4m3(tbase + d * N, arow + (uint64_t)(tx + d * row_zy), bdesc, IDESC, acc);
-                                else
-                                    tc::mma_bf16(tbase + d * N, arow + (uint64_t)(tx + d * row_zy), bdesc, IDESC, acc);
+                                for (int dd = 0; dd < DPI; ++dd) {
+                                    const int j = d0 + dd;
+                                    const uint64_t ad = arow + (uint64_t)((2 * j + u) * row_zy);
+                                    if constexpr (F8) tc::mma_e4m3(tbase + 2 * j * N, ad, bdesc, IDESC, acc);
+                                    else tc::mma_bf16(tbase + 2 * j * N, ad, bdesc, IDESC, acc);
+                                }
+                                first = false;
                             }
-                            first = false;
-                            bdesc += (uint64_t)(N * 32 / 16);
+                        } else {
+                            for (int tz = 0; tz < nz; ++tz) {
+                                const uint32_t acc = first ? 0u : 1u;
+                                const uint64_t bdesc = bgrp + (uint64_t)((nz - tz) * N);
+#pragma unroll
+                                for (int dd = 0; dd < DPI; ++dd) {
+                                    const int d = d0 + dd;
+                                    const uint64_t ad = arow + (uint64_t)((d + tz) * row_zy);
+                                    if constexpr (F8) tc::mma_e4m3(tbase + d * N, ad, bdesc, IDESC, acc);
+                                    else tc::mma_bf16(tbase + d * N, ad, bdesc, IDESC, acc);
+                                }
+                                first = false;
+                            }
                         }
+                        bgrp += (uint64_t)((nz + 2) * N * 2);   // next group: (nz + 2) * N * 32 bytes
                     }
                     tc::mma_commit(&b_empty[st]);
                     ++bi;
@@ -230,9 +261,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
         __syncwarp();
         const int q = warp & 3;                 // tensor-memory lane quarter of this warp
         const int r = q * 32 + lane;            // M row = voxel of the slice
-        // warps 1 .. NI+4 share the slices of their lane quarter round robin
+        // warps 1 .. kWarps-1 share the slices of their lane quarter round robin
         int cq = 0, rq = 0;
-        for (int w2 = 1; w2 <= NI + 4; ++w2)
+        for (int w2 = 1; w2 < kWarps; ++w2)
             if ((w2 & 3) == q) {
                 if (w2 < warp) ++rq;
                 ++cq;
@@ -342,7 +373,7 @@ struct ConvTcPlan::Impl {
     CUtensorMap tmap;
     Args args;
     int N = 0, T = 0;
-    bool f8 = false;
+    bool f8 = false, pair = false;
     size_t smem = 0;
     unsigned grid = 0;
 };
@@ -352,8 +383,32 @@ ConvTcPlan::~ConvTcPlan() { delete impl; }
 
 int conv_tc_tile_slices(int c_out) { return c_out >= 256 ? 2 : c_out >= 128 ? 4 : 8; }
 
-size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int elem) {
-    return (size_t)cin_pad * elem * k * k * k * c_out;
+// Taps per dimension of parity phase ph: k at stride 1; (k + 1) / 2 and k / 2 for parities 0 / 1 at stride 2.
+static void phase_ntaps(int k, int stride, int ph, int &nz, int &ny, int &nx) {
+    if (stride == 1) {
+        nz = ny = nx = k;
+        return;
+    }
+    const int n[2] = {(k + 1) / 2, k / 2};
+    nz = n[(ph >> 2) & 1];
+    ny = n[(ph >> 1) & 1];
+    nx = n[ph & 1];
+}
+
+// Arranged bytes of one channel chunk: every phase's (ty, tx) groups of (nz + 2) x 2 x c_out 16-byte rows.
+static size_t chunk_weight_bytes(int c_out, int k, int stride) {
+    size_t rows = 0;
+    for (int ph = 0; ph < (stride == 1 ? 1 : 8); ++ph) {
+        int nz, ny, nx;
+        phase_ntaps(k, stride, ph, nz, ny, nx);
+        rows += (size_t)ny * nx * (nz + 2) * 2 * c_out;
+    }
+    return rows * 16;
+}
+
+size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem) {
+    const int chunk_bytes_in = 32;                         // one chunk = 32 bytes of channels per voxel
+    return (size_t)(cin_pad * elem / chunk_bytes_in) * chunk_weight_bytes(c_out, k, stride);
 }
 
 // float -> E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; largest finite 448, no
@@ -391,7 +446,8 @@ static uint16_t bf16_from_float(float v) {
 
 void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, int elem,
                              uint8_t *out, float *s_w) {
-    // blob layout w[co][ci][kd][kh][kw] -> [chunk][offset in phase order][16-byte plane][co][16 bytes]
+    // blob layout w[co][ci][kd][kh][kw] ->
+    //   [chunk][phase][ty][tx][8/16-channel half][tz = nz-1 .. 0 between two zero entries][co][16 bytes]
     const int cpr = elem == 2 ? 8 : 16;                // channels per 16-byte row
     const int nph = stride == 1 ? 1 : 8;
     const int k3 = k * k * k;
@@ -405,21 +461,22 @@ void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, i
     size_t idx = 0;
     for (int c = 0; c < cin_pad / (2 * cpr); ++c) {
         for (int ph = 0; ph < nph; ++ph) {
-            int pz = 0, py = 0, px = 0, nz = k, ny = k, nx = k;
-            if (stride == 2) {
-                pz = (ph >> 2) & 1; py = (ph >> 1) & 1; px = ph & 1;
-                nz = (k - pz + 1) / 2; ny = (k - py + 1) / 2; nx = (k - px + 1) / 2;
-            }
-            for (int tz = 0; tz < nz; ++tz)
-                for (int ty = 0; ty < ny; ++ty)
-                    for (int tx = 0; tx < nx; ++tx) {
-                        const int kd = pz + stride * tz, kh = py + stride * ty, kw = px + stride * tx;
-                        for (int half = 0; half < 2; ++half)
+            const int pz = stride == 1 ? 0 : (ph >> 2) & 1, py = stride == 1 ? 0 : (ph >> 1) & 1,
+                      px = stride == 1 ? 0 : ph & 1;
+            int nz, ny, nx;
+            phase_ntaps(k, stride, ph, nz, ny, nx);
+            for (int ty = 0; ty < ny; ++ty)
+                for (int tx = 0; tx < nx; ++tx)
+                    for (int half = 0; half < 2; ++half)
+                        for (int e = 0; e < nz + 2; ++e) {
+                            const int tz = nz - e;          // nz and -1: the zero entries
+                            const int kd = pz + stride * tz, kh = py + stride * ty, kw = px + stride * tx;
                             for (int co = 0; co < c_out; ++co)
-                                for (int e = 0; e < cpr; ++e) {
-                                    const int ci = c * 2 * cpr + half * cpr + e;
+                                for (int el = 0; el < cpr; ++el) {
+                                    const int ci = c * 2 * cpr + half * cpr + el;
                                     float v = 0.f;
-                                    if (ci < c_in) v = w[((((size_t)co * c_in + ci) * k + kd) * k + kh) * k + kw];
+                                    if (tz >= 0 && tz < nz && ci < c_in)
+                                        v = w[((((size_t)co * c_in + ci) * k + kd) * k + kh) * k + kw];
                                     if (elem == 2) {
                                         const uint16_t h = bf16_from_float(v);
                                         memcpy(out + idx, &h, 2);
@@ -428,7 +485,7 @@ void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, i
                                         out[idx++] = e4m3_from_float(v / s_w[co]);
                                     }
                                 }
-                    }
+                        }
         }
     }
 }
@@ -466,9 +523,19 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     g.plane_bytes = ((uint32_t)(g.hd * g.hh * g.hw) * 16 + 127) / 128 * 128;
     // about 48 KB of weights per stage in a ring of two: each stage hand-off costs a fixed few
     // hundred cycles, and fewer, larger stages measured faster than deeper rings of smaller ones
-    g.rows_per_stage = sp.rows_per_stage > 0 ? sp.rows_per_stage : 49152 / (ntmax * c_out * 32);
-    if (g.rows_per_stage < 1) g.rows_per_stage = 1;
-    g.stage_bytes = ((uint32_t)(g.rows_per_stage * ntmax) * c_out * 32 + 127) / 128 * 128;
+    const uint32_t gbytes_max = (uint32_t)(ntmax + 2) * c_out * 32;
+    g.groups_per_stage = sp.groups_per_stage > 0 ? sp.groups_per_stage : (int)(49152 / gbytes_max);
+    if (g.groups_per_stage < 1) g.groups_per_stage = 1;
+    g.stage_bytes = ((uint32_t)g.groups_per_stage * gbytes_max + 127) / 128 * 128;
+    g.chunk_wbytes = (uint32_t)chunk_weight_bytes(c_out, k, stride);
+    // slice pairs (one N = 2 c_out MMA for two output slices): by default for stride 1 up to 64 channels,
+    // where the 128 x c_out x K MMA is bound by its shared-memory operand reads
+    const bool pair_ok = T % 2 == 0 && 2 * c_out <= 256;
+    const bool pair = sp.pair < 0 ? (pair_ok && stride == 1 && c_out <= 64) : sp.pair != 0;
+    if (pair && !pair_ok) {
+        snprintf(why, why_len, "slice pairs need an even number of slices per CTA and c_out <= 128");
+        return -1;
+    }
     g.nbs = sp.nbs > 0 ? sp.nbs : 2;
     if (g.nbs < 2 || g.nbs > 8) {
         snprintf(why, why_len, "weight stages must be in [2, 8]");
@@ -529,34 +596,42 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     P.N = c_out;
     P.T = T;
     P.f8 = sp.elem == 1;
+    P.pair = pair;
     P.grid = (unsigned)(g.nbx * g.nby * g.nbz);   // per pose; times B at launch
     return 0;
 }
 
-template <int N, int T, bool F8>
+template <int N, int T, bool F8, bool PAIR>
 static void launch_t(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
-    cudaFuncSetAttribute(conv3d_tc_kernel<N, T, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
-    conv3d_tc_kernel<N, T, F8><<<P.grid * B, kThreads, P.smem, s>>>(P.tmap, P.args);
+    cudaFuncSetAttribute(conv3d_tc_kernel<N, T, F8, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
+    conv3d_tc_kernel<N, T, F8, PAIR><<<P.grid * B, kThreads, P.smem, s>>>(P.tmap, P.args);
 }
 
 template <bool F8>
 static void launch_n(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
-    switch (P.N * 16 + P.T) {
-    case 32 * 16 + 4: launch_t<32, 4, F8>(P, B, s); break;
-    case 32 * 16 + 8: launch_t<32, 8, F8>(P, B, s); break;
-    case 64 * 16 + 4: launch_t<64, 4, F8>(P, B, s); break;
-    case 64 * 16 + 8: launch_t<64, 8, F8>(P, B, s); break;
-    case 128 * 16 + 2: launch_t<128, 2, F8>(P, B, s); break;
-    case 128 * 16 + 4: launch_t<128, 4, F8>(P, B, s); break;
-    default: launch_t<256, 2, F8>(P, B, s); break;
+    switch ((P.N * 16 + P.T) * 2 + (P.pair ? 1 : 0)) {
+    case (32 * 16 + 4) * 2: launch_t<32, 4, F8, false>(P, B, s); break;
+    case (32 * 16 + 8) * 2: launch_t<32, 8, F8, false>(P, B, s); break;
+    case (64 * 16 + 4) * 2: launch_t<64, 4, F8, false>(P, B, s); break;
+    case (64 * 16 + 8) * 2: launch_t<64, 8, F8, false>(P, B, s); break;
+    case (128 * 16 + 2) * 2: launch_t<128, 2, F8, false>(P, B, s); break;
+    case (128 * 16 + 4) * 2: launch_t<128, 4, F8, false>(P, B, s); break;
+    case (32 * 16 + 4) * 2 + 1: launch_t<32, 4, F8, true>(P, B, s); break;
+    case (32 * 16 + 8) * 2 + 1: launch_t<32, 8, F8, true>(P, B, s); break;
+    case (64 * 16 + 4) * 2 + 1: launch_t<64, 4, F8, true>(P, B, s); break;
+    case (64 * 16 + 8) * 2 + 1: launch_t<64, 8, F8, true>(P, B, s); break;
+    case (128 * 16 + 2) * 2 + 1: launch_t<128, 2, F8, true>(P, B, s); break;
+    case (128 * 16 + 4) * 2 + 1: launch_t<128, 4, F8, true>(P, B, s); break;
+    default: launch_t<256, 2, F8, false>(P, B, s); break;
     }
 }
 
-void conv_tc_describe(const ConvTcPlan &plan, int *T, int *rows_per_stage, int *nbs, size_t *smem) {
+void conv_tc_describe(const ConvTcPlan &plan, int *T, int *groups_per_stage, int *nbs, size_t *smem, int *pair) {
     *T = plan.impl->T;
-    *rows_per_stage = plan.impl->args.g.rows_per_stage;
+    *groups_per_stage = plan.impl->args.g.groups_per_stage;
     *nbs = plan.impl->args.g.nbs;
     *smem = plan.impl->smem;
+    *pair = plan.impl->pair ? 1 : 0;
 }
 
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s) {
