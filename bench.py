@@ -37,6 +37,55 @@ WEIGHTS_SEED = 0
 F32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the four conv launches of one step, taken
+# with ncu on a 16-pose batch of this workload (activations 226 MB > L2) and scaled x4 to 64 poses (every
+# tensor but the weights scales with the pose count).  Valid only for the kernel source they were taken
+# on: the sha256 prefix of the conv kernel's source files; any other source reports null.
+CONV_TRAFFIC = {
+    "src": "ebebf7bec2de942a",
+    "poses": 64,
+    "bf16": [1144.4e6, 1649.5e6, 1655.2e6, 1104.3e6],
+    "fp8": [915.2e6, 2125.9e6, 2126.2e6, 568.0e6],
+}
+
+
+def conv_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("k_conv_tc.cu", "tc_ptx.cuh"):
+        with open(os.path.join(ROOT, "paper_2104_04547_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def conv_traffic(dtype, n_poses):
+    """Measured DRAM bytes per conv launch (mean of the step's launches), or None."""
+    if dtype not in CONV_TRAFFIC or n_poses != CONV_TRAFFIC["poses"] or conv_source_hash() != CONV_TRAFFIC["src"]:
+        return None
+    v = CONV_TRAFFIC[dtype]
+    return sum(v) / len(v)
+
+
+def conv_algorithmic_bytes(desc, dtype, n_poses):
+    """Input + output (+ bf16 residual source for FP8) + arranged weights, per conv launch (mean)."""
+    n, tot, cin = desc["grid_n"], [], 32
+    elem = 1 if dtype == "fp8" else 2
+    for cv in desc["conv"]:
+        p = cv["k"] // 2
+        m = (n + 2 * p - cv["k"]) // cv["stride"] + 1
+        k = cv["k"]
+        if cv["stride"] == 1:
+            taps = k * k * (k + 2)
+        else:
+            taps = k * k * ((k + 1) // 2 + k // 2 + 4)
+        wbytes = (cin * elem // 32) * taps * 2 * cv["c_out"] * 16
+        b = n ** 3 * cin * elem + m ** 3 * cv["c_out"] * 2
+        if elem == 1 and cv["residual"]:
+            b += n ** 3 * cin * 2
+        tot.append(b * n_poses + wbytes)
+        n, cin = m, cv["c_out"]
+    return sum(tot) / len(tot)
+
 
 def conv_flops_per_pose(desc):
     n, tot = desc["grid_n"], 0
@@ -259,6 +308,7 @@ def run_ours(args):
     conv_flops = conv_flops_per_pose(desc) * B
     achieved = conv_flops / (conv_ms / 1000.0) / 1e12
     pk, pk_src = peaks()
+    traffic = conv_traffic(args.dtype, B)
     if args.dtype == "f32":
         roof = {"bound": "alu", "achieved": achieved, "peak": F32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / F32_ALU_PEAK_TFLOPS, "traffic": None,
@@ -267,14 +317,17 @@ def run_ours(args):
     elif args.dtype == "bf16":
         p = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": p, "unit": "TFLOP/s", "frac": achieved / p,
-                "traffic": None, "kernel": "conv3d_tc_kernel bf16 (4 launches per step)",
+                "traffic": traffic, "kernel": "conv3d_tc_kernel bf16 (4 launches per step)",
                 "peak_source": f"bf16_tflops_sustained ({pk_src})"}
     else:
         # no FP8 peak is measured: the BF16 sustained measurement x the nominal FP8/BF16 ratio (4.5 / 2.25)
         p = pk["bf16_tflops_sustained"] * 2.0
         roof = {"bound": "tensor", "achieved": achieved, "peak": p, "unit": "TFLOP/s", "frac": achieved / p,
-                "traffic": None, "kernel": "conv3d_tc_kernel fp8 (4 launches per step)",
+                "traffic": traffic, "kernel": "conv3d_tc_kernel fp8 (4 launches per step)",
                 "peak_source": f"bf16_tflops_sustained ({pk_src}) x 2 (nominal fp8/bf16 ratio)"}
+    if args.dtype != "f32":
+        roof["traffic_unit"] = "DRAM bytes per conv launch (mean of the step's 4), ncu"
+        roof["algorithmic_bytes"] = conv_algorithmic_bytes(desc, args.dtype, B)
     stage_mean = {n: statistics.mean(s[n] for s in stage_ms) for n in stage_ms[0]}
     line = {
         "metric": METRIC, "value": value, "unit": "poses/s", "n_gpus": world, "steps": args.steps,
