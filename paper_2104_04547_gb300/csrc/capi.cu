@@ -210,6 +210,7 @@ struct fusion_model {
     float *atom_w = nullptr;
     void *grid = nullptr;
     int grid_cx = kGridCxF32;
+    int grid_fold = -1;                           // bf16 grid: features 16..18 folded along x at this pad, or -1
     void *act[FUSION_MAX_CONV] = {};
     void *pool_out = nullptr;
     void *qbuf = nullptr;         // FP8 input of the conv layer being computed
@@ -343,9 +344,10 @@ int load_weights(fusion_model *m, const float *blob) {
         const float *b = take();
         if (m->bf16) {
             const int elem = m->fp8 ? 1 : 2;
-            std::vector<uint8_t> t(conv_tc_weight_bytes(cx, c.c_out, c.k, c.stride, elem));
+            const bool fold = i == 0 && m->grid_fold >= 0;
+            std::vector<uint8_t> t(conv_tc_weight_bytes(cx, c.c_out, c.k, c.stride, elem, fold));
             std::vector<float> sw(c.c_out, 1.f);
-            conv_tc_arrange_weights(w, c.c_out, c.c_in, cx, c.k, c.stride, elem, t.data(), sw.data());
+            conv_tc_arrange_weights(w, c.c_out, c.c_in, cx, c.k, c.stride, elem, fold, t.data(), sw.data());
             RC(upload_raw(m, &m->conv[i].w, t.data(), t.size()));
             if (m->fp8) RC(upload(m, &m->conv_sw[i], sw));
         } else {
@@ -528,6 +530,7 @@ static ConvTcSpec conv_spec(fusion_model *m, int i) {
     sp.residual = c.residual;
     sp.err = m->err;
     sp.pair = m->pair_mode;
+    sp.fold = (i == 0 && m->grid_fold >= 0) ? 1 : 0;
     return sp;
 }
 
@@ -630,6 +633,14 @@ int fusion_create(const fusion_model_desc *desc, const void *weights, size_t wei
     m->fp8 = (m->d.dtype == FUSION_FP8);
     m->esz = m->bf16 ? 2 : 4;
     m->grid_cx = m->bf16 ? 32 : kGridCxF32;
+    {
+        // the bf16 tensor-core path stores the grid's 3 channels beyond 16 folded along x, so that the first
+        // conv's second channel chunk carries 15 real channels instead of 3 (FP8 keeps one 32-channel chunk)
+        const fusion_conv_desc &c0 = m->d.conv[0];
+        if (m->bf16 && !m->fp8 && !c0.residual &&
+            conv_tc_fold_ok(c0.c_in, m->grid_cx, c0.k, c0.stride, 2))
+            m->grid_fold = c0.k / 2;
+    }
     int rc = alloc_workspace(m);
     if (!rc) rc = load_weights(m, static_cast<const float *>(weights));
     if (!rc && m->bf16) rc = plan_tensor_core_convs(m);
@@ -747,7 +758,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     RC(check_launch("sg_gather"));
     sg_mark(3);
     VoxArgs va{off_d, feat_d, m->atom_vox, m->atom_w, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx,
-               m->bf16 ? 1 : 0};
+               m->bf16 ? 1 : 0, m->grid_fold};
     launch_voxelize(va, st);
     RC(check_launch("voxelize"));
     map[1] = ei; mark();
@@ -1020,8 +1031,10 @@ int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst,
         std::vector<float> t;
         RC(copy_as_f32(m, m->grid, (size_t)p * n3 * m->grid_cx, n3 * m->grid_cx, t));
         float *o = static_cast<float *>(dst);
+        // a folded grid holds feature 16 + f of voxel x in slot 16 + 3 p + f of the same voxel
         for (size_t v = 0; v < n3; ++v)
-            for (int c = 0; c < kFeat; ++c) o[v * kFeat + c] = t[v * m->grid_cx + c];
+            for (int c = 0; c < kFeat; ++c)
+                o[v * kFeat + c] = t[v * m->grid_cx + (c < 16 || m->grid_fold < 0 ? c : 16 + 3 * m->grid_fold + c - 16)];
         return FUSION_OK;
     }
     case FUSION_STAGE_CONV: {

@@ -52,6 +52,9 @@ struct VoxArgs {
     void *out;            // [B][n][n][n][cx]
     int cx;               // padded channel count of the output layout
     int out_bf16;         // 0: float32, 1: bfloat16
+    int fold_pad;         // bf16 only: -1 = plain channels; p >= 0 = channels 16..18 folded along x:
+                          // channel 16 + 3 s + f of voxel x holds feature 16 + f of voxel x - p + s
+                          // (s = 0..4, zero outside the grid), channel 31 zero
 };
 void launch_voxelize(const VoxArgs &a, cudaStream_t s);
 
@@ -98,13 +101,16 @@ struct ConvTcPlan {
 };
 // Output slices per CTA for a layer with c_out output channels.
 int conv_tc_tile_slices(int c_out);
-// Bytes of the arranged weights of one layer (elem = 2 for bf16, 1 for FP8 E4M3).
-size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem);
+// Bytes of the arranged weights of one layer (elem = 2 for bf16, 1 for FP8 E4M3; fold: the last
+// 16-channel chunk holds 3 channels folded along x, see VoxArgs::fold_pad).
+size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem, bool fold);
+// Whether a layer can read an x-folded input (bf16, stride 1, k in {3, 5, 7}, c_in = 16 x chunks + 3).
+bool conv_tc_fold_ok(int c_in, int cin_pad, int k, int stride, int elem);
 // Blob conv weights [co][ci][k][k][k] -> [channel chunk][phase][ty][tx][16-byte half][tz = nz..-1, the two ends
 // zero][co][16 bytes];
 // FP8 also returns the per-output-channel scales s_w[c_out] (weights = stored code * s_w).
 void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, int elem,
-                             uint8_t *out, float *s_w);
+                             bool fold, uint8_t *out, float *s_w);
 struct ConvTcSpec {
     const void *x;          // input (bf16 or FP8) [max_poses][n_in]^3[cin_pad], read by TMA
     int elem;               // 2 = bf16, 1 = FP8 E4M3
@@ -123,6 +129,7 @@ struct ConvTcSpec {
     int groups_per_stage;   // (ty, tx) kernel-offset groups per weight stage (0: about 48 KB per stage)
     int nbs;                // weight stages in the ring (0: 2)
     int pair;               // 1: two output slices per MMA (N = 2 c_out); 0: one; -1: default for the layer
+    int fold;               // 1: the input's last 16-channel chunk is x-folded (VoxArgs::fold_pad = k / 2)
 };
 // Build the plan; returns 0, or nonzero with a reason in `why`.
 int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &spec, char *why, size_t why_len);

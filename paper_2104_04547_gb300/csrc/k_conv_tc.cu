@@ -89,6 +89,7 @@ struct Args {
     const float *bias;          // [N]
     __nv_bfloat16 *y;           // [B][n_out]^3[N]
     int n_in, n_out, cin, k, stride, pad, residual;
+    int fold_nx;                // > 0: the last chunk is x-folded, read at fold_nx x-offsets pad, pad + 2
     Geo g;
     unsigned *err;
 };
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                     tc::tma_load_5d(sA + buf * a_bytes + j * g.plane_bytes, &tmap, &a_full[buf], c * 2 * CPR + j * CPR,
                                     x0 * S + px - a.pad, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
                 ++ai;
+                if (a.fold_nx > 0 && c == g.chunks - 1) nx = a.fold_nx;
                 const int ngr = ny * nx;
                 const uint32_t gbytes = (uint32_t)(nz + 2) * N * 32;
                 for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
@@ -207,6 +209,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                 // descriptors advance by plain integer adds: the start-address field counts 16-byte rows
                 const uint64_t adesc0 = tc::desc_kmajor(tc::smem_u32(sA + buf * a_bytes), g.plane_bytes, sbo_a);
                 const uint32_t lbo_b = (uint32_t)(nz + 2) * N * 16;    // between the two 8-channel halves
+                // an x-folded chunk reads its few x-offsets at halo columns pad, pad + 2 (tx -> pad + 2 tx)
+                const bool folded = a.fold_nx > 0 && c == g.chunks - 1;
+                if (folded) nx = a.fold_nx;
                 const int ngr = ny * nx;
                 for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
                     const int gend = min(g0 + g.groups_per_stage, ngr);
@@ -216,7 +221,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                     uint64_t bgrp = tc::desc_kmajor(tc::smem_u32(sB + st * g.stage_bytes), lbo_b, 128);
                     for (int gi = g0; gi < gend; ++gi) {
                         const int ty = gi / nx, tx = gi - (gi / nx) * nx;
-                        const uint64_t arow = adesc0 + (uint64_t)(ty * g.hw + tx);
+                        const int hx = folded ? a.pad + 2 * tx : tx;
+                        const uint64_t arow = adesc0 + (uint64_t)(ty * g.hw + hx);
                         if constexpr (PAIR) {
                             // plane u of pair j (slices 2j, 2j+1): rows W(tz = u) | W(tz = u - 1) from entry nz - u
                             for (int u = 0; u <= nz; ++u) {
@@ -406,9 +412,20 @@ static size_t chunk_weight_bytes(int c_out, int k, int stride) {
     return rows * 16;
 }
 
-size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem) {
+// x-offsets of an x-folded chunk: the 5 folded positions cover kernel columns 0..4 at halo column pad,
+// and for k = 7 columns 5, 6 at halo column pad + 2 (slots 3, 4).
+static int fold_nx(int k) { return k <= 5 ? 1 : 2; }
+
+bool conv_tc_fold_ok(int c_in, int cin_pad, int k, int stride, int elem) {
+    return elem == 2 && stride == 1 && (k == 3 || k == 5 || k == 7) && cin_pad % 16 == 0 && cin_pad >= 32 &&
+           c_in == cin_pad - 13;
+}
+
+size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem, bool fold) {
     const int chunk_bytes_in = 32;                         // one chunk = 32 bytes of channels per voxel
-    return (size_t)(cin_pad * elem / chunk_bytes_in) * chunk_weight_bytes(c_out, k, stride);
+    const int chunks = cin_pad * elem / chunk_bytes_in;
+    if (!fold) return (size_t)chunks * chunk_weight_bytes(c_out, k, stride);
+    return (size_t)(chunks - 1) * chunk_weight_bytes(c_out, k, 1) + (size_t)k * fold_nx(k) * (k + 2) * 2 * c_out * 16;
 }
 
 // float -> E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; largest finite 448, no
@@ -445,7 +462,7 @@ static uint16_t bf16_from_float(float v) {
 }
 
 void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, int elem,
-                             uint8_t *out, float *s_w) {
+                             bool fold, uint8_t *out, float *s_w) {
     // blob layout w[co][ci][kd][kh][kw] ->
     //   [chunk][phase][ty][tx][8/16-channel half][tz = nz-1 .. 0 between two zero entries][co][16 bytes]
     const int cpr = elem == 2 ? 8 : 16;                // channels per 16-byte row
@@ -459,7 +476,33 @@ void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, i
         }
     }
     size_t idx = 0;
-    for (int c = 0; c < cin_pad / (2 * cpr); ++c) {
+    const int nchunks = cin_pad / (2 * cpr);
+    for (int c = 0; c < nchunks; ++c) {
+        if (fold && c == nchunks - 1) {
+            // x-folded chunk: slot q < 15 holds channel 16 c + q % 3 at kernel column offset q / 3 from the
+            // group's first column (group 0: columns 0..4; group 1 for k = 7: slots 3, 4 -> columns 5, 6)
+            const int nxf = fold_nx(k);
+            for (int ty = 0; ty < k; ++ty)
+                for (int gx = 0; gx < nxf; ++gx)
+                    for (int half = 0; half < 2; ++half)
+                        for (int e = 0; e < k + 2; ++e) {
+                            const int tz = k - e;
+                            for (int co = 0; co < c_out; ++co)
+                                for (int el = 0; el < cpr; ++el) {
+                                    const int q = half * cpr + el, sl = q / 3;
+                                    const int ci = c * 2 * cpr + q % 3;
+                                    const int kw = 2 * gx + sl;
+                                    const bool used = q < 15 && tz >= 0 && tz < k && ci < c_in && kw < k &&
+                                                      (gx == 0 ? sl < 5 : sl >= 3);
+                                    const float v =
+                                        used ? w[((((size_t)co * c_in + ci) * k + tz) * k + ty) * k + kw] : 0.f;
+                                    const uint16_t h = bf16_from_float(v);
+                                    memcpy(out + idx, &h, 2);
+                                    idx += 2;
+                                }
+                        }
+            continue;
+        }
         for (int ph = 0; ph < nph; ++ph) {
             const int pz = stride == 1 ? 0 : (ph >> 2) & 1, py = stride == 1 ? 0 : (ph >> 1) & 1,
                       px = stride == 1 ? 0 : ph & 1;
@@ -507,6 +550,10 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     }
     if (sp.cin_pad % chunk_ch != 0 || (stride != 1 && stride != 2) || (sp.elem != 1 && sp.elem != 2)) {
         snprintf(why, why_len, "tensor-core conv needs input channels padded to %d and stride 1 or 2", chunk_ch);
+        return -1;
+    }
+    if (sp.fold && (!conv_tc_fold_ok(sp.cin_pad - 13, sp.cin_pad, k, stride, sp.elem) || sp.residual)) {
+        snprintf(why, why_len, "an x-folded input needs bf16, stride 1, k in {3, 5, 7} and no residual");
         return -1;
     }
     Geo g{};
@@ -591,6 +638,7 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     A.stride = stride;
     A.pad = k / 2;
     A.residual = sp.residual;
+    A.fold_nx = sp.fold ? fold_nx(k) : 0;
     A.g = g;
     A.err = sp.err;
     P.N = c_out;

@@ -13,6 +13,12 @@
 // memory and accumulates all channels of each voxel in registers in atom-index
 // order (deterministic, no atomics), then stores the voxel's channels as one
 // contiguous vector (16-byte stores) in the NDHWC layout the first conv reads.
+// For the bf16 tensor-core conv the 3 channels beyond the first 16 are stored
+// folded along x (fold_pad >= 0): the second 16-channel chunk of voxel x holds
+// features 16..18 of voxels x - p .. x - p + 4, so that chunk needs 2 x-offsets
+// of the 7^3 kernel instead of 7 (it would otherwise be 13/16 zero padding).
+// voxelize_kernel stores each voxel's own features 16..18 at slot s = p, and
+// fold_grid_kernel then builds the folded chunks row by row.
 #include "fusion_internal.cuh"
 
 #include <math.h>
@@ -176,12 +182,32 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
         const size_t vox = (((size_t)p * n + vz) * n + vy) * n + vx;
         if constexpr (BF16) {
             __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(a.out) + vox * CX;
+            if (a.fold_pad < 0) {
 #pragma unroll
-            for (int c0 = 0; c0 < CX; c0 += 8) {
-                __align__(16) __nv_bfloat16 v8[8];
+                for (int c0 = 0; c0 < CX; c0 += 8) {
+                    __align__(16) __nv_bfloat16 v8[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) v8[j] = __float2bfloat16_rn(c0 + j < kFeat ? acc[c0 + j] : 0.f);
-                *reinterpret_cast<uint4 *>(out + c0) = *reinterpret_cast<const uint4 *>(v8);
+                    for (int j = 0; j < 8; ++j) v8[j] = __float2bfloat16_rn(c0 + j < kFeat ? acc[c0 + j] : 0.f);
+                    *reinterpret_cast<uint4 *>(out + c0) = *reinterpret_cast<const uint4 *>(v8);
+                }
+            } else {
+                // folded layout, first pass: features 16..18 at slot s = p of the voxel's own second chunk
+                // (where the fold keeps them), the rest of that chunk zero; fold_grid_kernel fills it in
+                const int sp = 16 + 3 * a.fold_pad;
+#pragma unroll
+                for (int c0 = 0; c0 < CX; c0 += 8) {
+                    __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int c = c0 + j;
+                        // constant register indices only (sp is a runtime value)
+                        const int d = c - sp;
+                        const float v = c < 16 ? acc[c < 16 ? c : 0]
+                                               : d == 0 ? acc[16] : d == 1 ? acc[17] : d == 2 ? acc[18] : 0.f;
+                        v8[j] = __float2bfloat16_rn(v);
+                    }
+                    *reinterpret_cast<uint4 *>(out + c0) = *reinterpret_cast<const uint4 *>(v8);
+                }
             }
         } else {
             float *out = reinterpret_cast<float *>(a.out) + vox * CX;
@@ -195,6 +221,40 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
                 *reinterpret_cast<float4 *>(out + c0) = v4;
             }
         }
+    }
+}
+
+
+// Second pass of the folded layout: one CTA per 8 x-rows (all poses, z, y); each row's features
+// 16..18 (at slot 16 + 3p) are staged in shared memory first, then every voxel's second chunk is
+// rewritten as slot 16 + 3 s + f = feature 16 + f of voxel x - p + s (zero outside the grid) with
+// 16-byte stores.  Rows are independent, and a row is read completely before any of it is written.
+__global__ void __launch_bounds__(256) fold_grid_kernel(__nv_bfloat16 *grid, int rows, int n, int p) {
+    extern __shared__ __align__(16) __nv_bfloat16 s_r[];     // [8][n][3]
+    const int r0 = blockIdx.x * 8;
+    const int nr = min(8, rows - r0);
+    const int sp = 16 + 3 * p;
+    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
+        const __nv_bfloat16 *v = grid + ((size_t)r0 * n + e) * 32 + sp;
+        s_r[e * 3 + 0] = v[0];
+        s_r[e * 3 + 1] = v[1];
+        s_r[e * 3 + 2] = v[2];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
+        const int r = e / n, x = e - r * n;
+        __align__(16) __nv_bfloat16 v16[16];
+#pragma unroll
+        for (int sl = 0; sl < 5; ++sl) {
+            const int xs = x - p + sl;
+            const bool in = xs >= 0 && xs < n;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) v16[3 * sl + f] = in ? s_r[(r * n + xs) * 3 + f] : __float2bfloat16_rn(0.f);
+        }
+        v16[15] = __float2bfloat16_rn(0.f);
+        uint4 *dst = reinterpret_cast<uint4 *>(grid + ((size_t)r0 * n + e) * 32 + 16);
+        dst[0] = reinterpret_cast<const uint4 *>(v16)[0];
+        dst[1] = reinterpret_cast<const uint4 *>(v16)[1];
     }
 }
 
@@ -222,6 +282,11 @@ void launch_prep(const PrepArgs &a, cudaStream_t s) {
 void launch_voxelize(const VoxArgs &a, cudaStream_t s) {
     if (a.out_bf16) {
         launch_vox_t<true, 32>(a, s);
+        if (a.fold_pad >= 0) {
+            const int rows = a.n_poses * a.grid_n * a.grid_n;
+            fold_grid_kernel<<<(rows + 7) / 8, 256, (size_t)8 * a.grid_n * 3 * sizeof(__nv_bfloat16), s>>>(
+                static_cast<__nv_bfloat16 *>(a.out), rows, a.grid_n, a.fold_pad);
+        }
     } else if (a.cx == 24) {
         launch_vox_t<false, 24>(a, s);
     } else {
