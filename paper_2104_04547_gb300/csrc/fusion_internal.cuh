@@ -106,8 +106,7 @@ int conv_tc_tile_slices(int c_out);
 size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem, bool fold);
 // Whether a layer can read an x-folded input (bf16, stride 1, k in {3, 5, 7}, c_in = 16 x chunks + 3).
 bool conv_tc_fold_ok(int c_in, int cin_pad, int k, int stride, int elem);
-// Blob conv weights [co][ci][k][k][k] -> [channel chunk][phase][ty][tx][16-byte half][tz = nz..-1, the two ends
-// zero][co][16 bytes];
+// Blob conv weights [co][ci][k][k][k] -> [channel chunk][phase][ty][tx][16-byte half][tz = nz-1..0][co][16 bytes];
 // FP8 also returns the per-output-channel scales s_w[c_out] (weights = stored code * s_w).
 void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, int elem,
                              bool fold, uint8_t *out, float *s_w);

@@ -19,19 +19,21 @@
 //
 // Operand B (the weights) streams through a ring of shared-memory stages with
 // plain bulk copies.  The host arranges them per in-plane offset (ty, tx) as a
-// group [8-channel half][tz = nz, nz-1, .., 0, -1][co][16 bytes], the two end
-// entries zero.  Two uses of that order:
-//   - one slice, offset tz: B = the N rows of entry nz - tz;
-//   - a pair of adjacent output slices (z, z+1) and input plane z + u: the 2N
-//     rows from entry nz - u are W(tz = u) then W(tz = u - 1), which are the
-//     offsets that plane contributes to z and to z+1.  One M=128, N=2C MMA then
-//     serves both slices: the A tile is read from shared memory once for two
-//     slices, so the operand bytes per MMA clock drop from 6 KB / 32 to 8 KB /
-//     64 (at N = 64), for (nz + 1) / nz times the MMA work (the zero entries).
-// The accumulator of pair j spans columns [2jN, 2jN + 2N), so slice d sits at
-// column dN either way and the epilogue does not depend on the pairing.  The
-// summation order per output element is the same in both forms (offset groups
-// in (ty, tx) order, tz ascending, the paired form adding exact zeros).
+// group [8-channel half][tz = nz-1, .., 1, 0][co][16 bytes].  Two uses of that
+// order:
+//   - one slice, offset tz: B = the N rows of entry nz-1-tz;
+//   - a pair of adjacent output slices (z, z+1) and input plane z + u with
+//     0 < u < nz: the 2N rows from entry nz-1-u are W(tz = u) then
+//     W(tz = u - 1), the offsets that plane contributes to z and to z+1.  One
+//     M=128, N=2C MMA serves both slices: the A tile is read from shared memory
+//     once for two slices, so the operand bytes per MMA clock drop from 6 KB / 32
+//     to 8 KB / 64 (at N = 64).  Planes u = 0 and u = nz feed one slice each
+//     (one-slice MMAs into that slice's half of the pair accumulator).
+// The accumulators are zeroed in tensor memory first and every MMA
+// accumulates.  The accumulator of pair j spans columns [2jN, 2jN + 2N), so
+// slice d sits at column dN either way and the epilogue does not depend on the
+// pairing.  The summation order per output element is the same in both forms
+// (offset groups in (ty, tx) order, tz ascending).
 //
 // FP8 variant (E4M3 inputs, kind::f8f6f4, 32 channels per MMA): weights carry a
 // per-output-channel scale and activations a per-pose scale; the epilogue
@@ -82,7 +84,7 @@ struct Geo {
 struct Args {
     const __nv_bfloat16 *xres;  // bf16 copy of the input [B][n_in]^3[cres] (residual blocks)
     int cres;                   // channels of xres
-    const uint8_t *w;           // [chunk][phase][ty][tx][2 halves][tz = nz..-1][N][16 bytes]
+    const uint8_t *w;           // [chunk][phase][ty][tx][2 halves][tz = nz-1..0][N][16 bytes]
     const float *s_in;          // FP8: per-pose input scale [B]
     const float *s_w;           // FP8: per-output-channel weight scale [N]
     float *amax;                // FP8: per-pose max |output| [B] (atomic max; may be null)
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     constexpr uint32_t TCOLS = (T * N <= 32) ? 32 : (T * N <= 64) ? 64 : (T * N <= 128) ? 128 : (T * N <= 256) ? 256 : 512;
     constexpr int NM = PAIR ? 2 * N : N;  // MMA N
     constexpr uint32_t IDESC = F8 ? tc::idesc_e4m3(128, NM) : tc::idesc_bf16(128, NM);
+    constexpr uint32_t IDESC1 = F8 ? tc::idesc_e4m3(128, N) : tc::idesc_bf16(128, N);   // one slice
     constexpr int UNITS = PAIR ? T / 2 : T;            // accumulators (slices or slice pairs)
     constexpr int NI = kIssReq < UNITS ? kIssReq : UNITS;   // MMA-issuing warps, each owns UNITS / NI
     constexpr int DPI = UNITS / NI;
@@ -155,6 +158,15 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tbase = *tmem_slot;
+    // zero the accumulators so that every MMA accumulates (warps 1..8, two per tensor-memory lane quarter)
+    if (warp >= 1) {
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        for (uint32_t c = (warp >= 5 ? 32u : 0u); c < TCOLS; c += 64u) tc::tmem_st32_zero(tbase + lane_base + c);
+        tc::tmem_st_wait();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
 
     auto fail = [&]() {
         *abort_flag = 1;
@@ -179,8 +191,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                                     x0 * S + px - a.pad, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
                 ++ai;
                 if (a.fold_nx > 0 && c == g.chunks - 1) nx = a.fold_nx;
-                const int ngr = ny * nx;
-                const uint32_t gbytes = (uint32_t)(nz + 2) * N * 32;
+                const int ngr = nz > 0 ? ny * nx : 0;   // a phase without z taps adds nothing
+                const uint32_t gbytes = (uint32_t)nz * N * 32;
                 for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
                     const int cnt = min(g.groups_per_stage, ngr - g0);
                     const int st = bi % g.nbs;
@@ -197,7 +209,6 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
         const int d0 = (warp - 1) * DPI;
         // ---------------- MMA issuer ----------------
         int ai = 0, bi = 0;
-        bool first = true;
         const uint32_t sbo_a = (uint32_t)g.hw * 16;
         const uint32_t row_zy = (uint32_t)g.hh * g.hw;
         for (int c = 0; c < g.chunks && !*abort_flag; ++c) {
@@ -208,11 +219,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                 if (!tc::mbar_wait(&a_full[buf], (ai / g.na) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
                 // descriptors advance by plain integer adds: the start-address field counts 16-byte rows
                 const uint64_t adesc0 = tc::desc_kmajor(tc::smem_u32(sA + buf * a_bytes), g.plane_bytes, sbo_a);
-                const uint32_t lbo_b = (uint32_t)(nz + 2) * N * 16;    // between the two 8-channel halves
+                const uint32_t lbo_b = (uint32_t)nz * N * 16;    // between the two 8-channel halves
                 // an x-folded chunk reads its few x-offsets at halo columns pad, pad + 2 (tx -> pad + 2 tx)
                 const bool folded = a.fold_nx > 0 && c == g.chunks - 1;
                 if (folded) nx = a.fold_nx;
-                const int ngr = ny * nx;
+                const int ngr = nz > 0 ? ny * nx : 0;   // a phase without z taps adds nothing
                 for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
                     const int gend = min(g0 + g.groups_per_stage, ngr);
                     const int st = bi % g.nbs;
@@ -224,34 +235,47 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                         const int hx = folded ? a.pad + 2 * tx : tx;
                         const uint64_t arow = adesc0 + (uint64_t)(ty * g.hw + hx);
                         if constexpr (PAIR) {
-                            // plane u of pair j (slices 2j, 2j+1): rows W(tz = u) | W(tz = u - 1) from entry nz - u
-                            for (int u = 0; u <= nz; ++u) {
-                                const uint32_t acc = first ? 0u : 1u;
-                                const uint64_t bdesc = bgrp + (uint64_t)((nz - u) * N);
+                            // plane u of pair j (slices 2j, 2j+1): u = 0 feeds slice 2j alone (W(0), entry nz-1),
+                            // 0 < u < nz both slices (W(u) | W(u-1) from entry nz-1-u), u = nz slice 2j+1
+                            // alone (W(nz-1), entry 0); per slice the offsets arrive in ascending tz
+#pragma unroll
+                            for (int dd = 0; dd < DPI; ++dd) {
+                                const int j = d0 + dd;
+                                const uint64_t ad = arow + (uint64_t)(2 * j * row_zy);
+                                const uint64_t bd = bgrp + (uint64_t)((nz - 1) * N);
+                                if constexpr (F8) tc::mma_e4m3(tbase + 2 * j * N, ad, bd, IDESC1, 1u);
+                                else tc::mma_bf16(tbase + 2 * j * N, ad, bd, IDESC1, 1u);
+                            }
+                            for (int u = 1; u < nz; ++u) {
+                                const uint64_t bd = bgrp + (uint64_t)((nz - 1 - u) * N);
 #pragma unroll
                                 for (int dd = 0; dd < DPI; ++dd) {
                                     const int j = d0 + dd;
                                     const uint64_t ad = arow + (uint64_t)((2 * j + u) * row_zy);
-                                    if constexpr (F8) tc::mma_e4m3(tbase + 2 * j * N, ad, bdesc, IDESC, acc);
-                                    else tc::mma_bf16(tbase + 2 * j * N, ad, bdesc, IDESC, acc);
+                                    if constexpr (F8) tc::mma_e4m3(tbase + 2 * j * N, ad, bd, IDESC, 1u);
+                                    else tc::mma_bf16(tbase + 2 * j * N, ad, bd, IDESC, 1u);
                                 }
-                                first = false;
+                            }
+#pragma unroll
+                            for (int dd = 0; dd < DPI; ++dd) {
+                                const int j = d0 + dd;
+                                const uint64_t ad = arow + (uint64_t)((2 * j + nz) * row_zy);
+                                if constexpr (F8) tc::mma_e4m3(tbase + (2 * j + 1) * N, ad, bgrp, IDESC1, 1u);
+                                else tc::mma_bf16(tbase + (2 * j + 1) * N, ad, bgrp, IDESC1, 1u);
                             }
                         } else {
                             for (int tz = 0; tz < nz; ++tz) {
-                                const uint32_t acc = first ? 0u : 1u;
-                                const uint64_t bdesc = bgrp + (uint64_t)((nz - tz) * N);
+                                const uint64_t bd = bgrp + (uint64_t)((nz - 1 - tz) * N);
 #pragma unroll
                                 for (int dd = 0; dd < DPI; ++dd) {
                                     const int d = d0 + dd;
                                     const uint64_t ad = arow + (uint64_t)((d + tz) * row_zy);
-                                    if constexpr (F8) tc::mma_e4m3(tbase + d * N, ad, bdesc, IDESC, acc);
-                                    else tc::mma_bf16(tbase + d * N, ad, bdesc, IDESC, acc);
+                                    if constexpr (F8) tc::mma_e4m3(tbase + d * N, ad, bd, IDESC, 1u);
+                                    else tc::mma_bf16(tbase + d * N, ad, bd, IDESC, 1u);
                                 }
-                                first = false;
                             }
                         }
-                        bgrp += (uint64_t)((nz + 2) * N * 2);   // next group: (nz + 2) * N * 32 bytes
+                        bgrp += (uint64_t)(nz * N * 2);   // next group: nz * N * 32 bytes
                     }
                     tc::mma_commit(&b_empty[st]);
                     ++bi;
@@ -401,13 +425,13 @@ static void phase_ntaps(int k, int stride, int ph, int &nz, int &ny, int &nx) {
     nx = n[ph & 1];
 }
 
-// Arranged bytes of one channel chunk: every phase's (ty, tx) groups of (nz + 2) x 2 x c_out 16-byte rows.
+// Arranged bytes of one channel chunk: every phase's (ty, tx) groups of nz x 2 x c_out 16-byte rows.
 static size_t chunk_weight_bytes(int c_out, int k, int stride) {
     size_t rows = 0;
     for (int ph = 0; ph < (stride == 1 ? 1 : 8); ++ph) {
         int nz, ny, nx;
         phase_ntaps(k, stride, ph, nz, ny, nx);
-        rows += (size_t)ny * nx * (nz + 2) * 2 * c_out;
+        rows += (size_t)ny * nx * nz * 2 * c_out;
     }
     return rows * 16;
 }
@@ -425,7 +449,7 @@ size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem,
     const int chunk_bytes_in = 32;                         // one chunk = 32 bytes of channels per voxel
     const int chunks = cin_pad * elem / chunk_bytes_in;
     if (!fold) return (size_t)chunks * chunk_weight_bytes(c_out, k, stride);
-    return (size_t)(chunks - 1) * chunk_weight_bytes(c_out, k, 1) + (size_t)k * fold_nx(k) * (k + 2) * 2 * c_out * 16;
+    return (size_t)(chunks - 1) * chunk_weight_bytes(c_out, k, 1) + (size_t)k * fold_nx(k) * k * 2 * c_out * 16;
 }
 
 // float -> E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; largest finite 448, no
@@ -464,7 +488,7 @@ static uint16_t bf16_from_float(float v) {
 void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, int elem,
                              bool fold, uint8_t *out, float *s_w) {
     // blob layout w[co][ci][kd][kh][kw] ->
-    //   [chunk][phase][ty][tx][8/16-channel half][tz = nz-1 .. 0 between two zero entries][co][16 bytes]
+    //   [chunk][phase][ty][tx][8/16-channel half][tz = nz-1 .. 0][co][16 bytes]
     const int cpr = elem == 2 ? 8 : 16;                // channels per 16-byte row
     const int nph = stride == 1 ? 1 : 8;
     const int k3 = k * k * k;
@@ -485,15 +509,14 @@ void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, i
             for (int ty = 0; ty < k; ++ty)
                 for (int gx = 0; gx < nxf; ++gx)
                     for (int half = 0; half < 2; ++half)
-                        for (int e = 0; e < k + 2; ++e) {
-                            const int tz = k - e;
+                        for (int e = 0; e < k; ++e) {
+                            const int tz = k - 1 - e;
                             for (int co = 0; co < c_out; ++co)
                                 for (int el = 0; el < cpr; ++el) {
                                     const int q = half * cpr + el, sl = q / 3;
                                     const int ci = c * 2 * cpr + q % 3;
                                     const int kw = 2 * gx + sl;
-                                    const bool used = q < 15 && tz >= 0 && tz < k && ci < c_in && kw < k &&
-                                                      (gx == 0 ? sl < 5 : sl >= 3);
+                                    const bool used = q < 15 && ci < c_in && kw < k && (gx == 0 ? sl < 5 : sl >= 3);
                                     const float v =
                                         used ? w[((((size_t)co * c_in + ci) * k + tz) * k + ty) * k + kw] : 0.f;
                                     const uint16_t h = bf16_from_float(v);
@@ -511,15 +534,14 @@ void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, i
             for (int ty = 0; ty < ny; ++ty)
                 for (int tx = 0; tx < nx; ++tx)
                     for (int half = 0; half < 2; ++half)
-                        for (int e = 0; e < nz + 2; ++e) {
-                            const int tz = nz - e;          // nz and -1: the zero entries
+                        for (int e = 0; e < nz; ++e) {
+                            const int tz = nz - 1 - e;
                             const int kd = pz + stride * tz, kh = py + stride * ty, kw = px + stride * tx;
                             for (int co = 0; co < c_out; ++co)
                                 for (int el = 0; el < cpr; ++el) {
                                     const int ci = c * 2 * cpr + half * cpr + el;
                                     float v = 0.f;
-                                    if (tz >= 0 && tz < nz && ci < c_in)
-                                        v = w[((((size_t)co * c_in + ci) * k + kd) * k + kh) * k + kw];
+                                    if (ci < c_in) v = w[((((size_t)co * c_in + ci) * k + kd) * k + kh) * k + kw];
                                     if (elem == 2) {
                                         const uint16_t h = bf16_from_float(v);
                                         memcpy(out + idx, &h, 2);
@@ -570,7 +592,7 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     g.plane_bytes = ((uint32_t)(g.hd * g.hh * g.hw) * 16 + 127) / 128 * 128;
     // about 48 KB of weights per stage in a ring of two: each stage hand-off costs a fixed few
     // hundred cycles, and fewer, larger stages measured faster than deeper rings of smaller ones
-    const uint32_t gbytes_max = (uint32_t)(ntmax + 2) * c_out * 32;
+    const uint32_t gbytes_max = (uint32_t)ntmax * c_out * 32;
     g.groups_per_stage = sp.groups_per_stage > 0 ? sp.groups_per_stage : (int)(49152 / gbytes_max);
     if (g.groups_per_stage < 1) g.groups_per_stage = 1;
     g.stage_bytes = ((uint32_t)g.groups_per_stage * gbytes_max + 127) / 128 * 128;
