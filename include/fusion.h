@@ -174,18 +174,19 @@ int fusion_last_timings(fusion_model *m, float *out, int32_t n);
 #define FUSION_OPT_CUDA_GRAPH 1   /* value 1: fusion_score replays a CUDA graph of the whole device-side
                                      forward pass, captured on first use for each batch size (inputs are
                                      copied into the model's own buffers first); 0: plain launches */
-#define FUSION_OPT_CONV_SLICE_PAIRS 2   /* tensor-core convs: 1 = every layer computes two adjacent output
-                                           slices per MMA (N = 2 x output channels; EUNSUPPORTED where a layer
-                                           cannot), 0 = one slice per MMA, -1 = the default per layer (pairs
-                                           for stride-1 layers of <= 64 output channels).  Re-plans the layers
-                                           and drops captured graphs; scores are the same in every mode */
+#define FUSION_OPT_CONV_SLICES_PER_MMA 2   /* tensor-core convs: value 1, 2 or 4 = every layer has each MMA
+                                              serve that many adjacent output slices (N = value x output
+                                              channels; FUSION_EUNSUPPORTED where a layer cannot), -1 = the
+                                              default per layer (2 for stride-1 layers where it fits, else
+                                              1).  Re-plans the layers and drops captured graphs; scores
+                                              are the same in every mode */
 
 /* Set a runtime option of a model (FUSION_OPT_*). */
 int fusion_set_option(fusion_model *m, int32_t option, int64_t value);
 
 /* Pick, for every conv layer of a tensor-core model (bf16 / fp8), the
- * fastest tile configuration (output slices per CTA, one or two output slices
- * per MMA, kernel-offset groups per weight stage, weight stages) by timing
+ * fastest tile configuration (output slices per CTA, output slices per MMA,
+ * kernel-offset groups per weight stage, weight stages) by timing
  * every configuration that fits shared memory on the given batch (scored once
  * first).  Every configuration sums each output in the same order, so the
  * scores do not change.  Replaces the layer plans;
@@ -194,8 +195,8 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
 
 /* Tile configuration of conv `layer`: out5 = {output slices per CTA, (ty, tx)
  * kernel-offset groups per weight stage, weight stages, shared-memory bytes,
- * 1 if each MMA computes two adjacent output slices (N = 2 x output channels)
- * else 0}.  FUSION_EUNSUPPORTED on the FP32 path. */
+ * adjacent output slices each MMA serves (1, 2 or 4; N = that x output
+ * channels)}.  FUSION_EUNSUPPORTED on the FP32 path. */
 int fusion_describe_conv(fusion_model *m, int32_t layer, int32_t *out5);
 
 /* ---- serving: continuous batching request loop ----

@@ -230,7 +230,7 @@ struct fusion_model {
     cudaStream_t sg_stream = nullptr;             // graph branch
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr, ev_sg[4] = {};
     bool use_graph = false;                       // replay captured CUDA graphs, one per batch size
-    int pair_mode = -1;                           // conv slice pairs: -1 default per layer, 0 off, 1 on
+    int group_mode = -1;                          // conv output slices per MMA: -1 default per layer, or 1, 2, 4
     std::map<int, cudaGraphExec_t> graph_exec;
     std::map<int, cudaGraph_t> graph;
 
@@ -529,7 +529,7 @@ static ConvTcSpec conv_spec(fusion_model *m, int i) {
     sp.stride = c.stride;
     sp.residual = c.residual;
     sp.err = m->err;
-    sp.pair = m->pair_mode;
+    sp.group = m->group_mode;
     sp.fold = (i == 0 && m->grid_fold >= 0) ? 1 : 0;
     return sp;
 }
@@ -1093,14 +1093,15 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
     case FUSION_OPT_CUDA_GRAPH:
         m->use_graph = value != 0;
         return FUSION_OK;
-    case FUSION_OPT_CONV_SLICE_PAIRS: {
-        if (value < -1 || value > 1) return fail(FUSION_EINVAL, "slice-pair mode must be -1, 0 or 1");
+    case FUSION_OPT_CONV_SLICES_PER_MMA: {
+        if (value != -1 && value != 1 && value != 2 && value != 4)
+            return fail(FUSION_EINVAL, "slices per MMA must be -1 (default), 1, 2 or 4");
         if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "the FP32 path has no tensor-core tiles");
-        const int old = m->pair_mode;
-        m->pair_mode = (int)value;
+        const int old = m->group_mode;
+        m->group_mode = (int)value;
         const int rc = plan_tensor_core_convs(m);
         if (rc) {
-            m->pair_mode = old;
+            m->group_mode = old;
             plan_tensor_core_convs(m);
             return rc;
         }
@@ -1115,14 +1116,14 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
 int fusion_describe_conv(fusion_model *m, int32_t layer, int32_t *out5) {
     if (!m || !out5 || layer < 0 || layer >= m->d.n_conv) return fail(FUSION_EINVAL, "bad arguments");
     if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "the FP32 path has no tensor-core tiles");
-    int T, groups, nbs, pair;
+    int T, groups, nbs, group;
     size_t smem;
-    conv_tc_describe(m->tcplan[layer], &T, &groups, &nbs, &smem, &pair);
+    conv_tc_describe(m->tcplan[layer], &T, &groups, &nbs, &smem, &group);
     out5[0] = T;
     out5[1] = groups;
     out5[2] = nbs;
     out5[3] = (int32_t)smem;
-    out5[4] = pair;
+    out5[4] = group;
     return FUSION_OK;
 }
 
@@ -1157,13 +1158,13 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
             launch_quantize_per_pose(xb, m->qbuf, B, per_pose, m->amax, m->qscale, st);
         };
         for (int T : Ts)
-            for (int pair : {1, 0})
+            for (int group : {4, 2, 1})
             for (int groups : {1, 2, 3, 4, 6})
                 for (int nbs : {2, 3, 4}) {
                     ConvTcPlan trial;
                     ConvTcSpec sp = conv_spec(m, i);
                     sp.T = T;
-                    sp.pair = pair;
+                    sp.group = group;
                     sp.groups_per_stage = groups;
                     sp.nbs = nbs;
                     char why[256] = {0};
@@ -1182,7 +1183,7 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
                         best[0] = T;
                         best[1] = groups;
                         best[2] = nbs;
-                        best[3] = pair;
+                        best[3] = group;
                     }
                 }
         if (best[0] == 0) return fail(FUSION_EUNSUPPORTED, "no tile configuration fits layer " + std::to_string(i));
@@ -1190,7 +1191,7 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
         sp.T = best[0];
         sp.groups_per_stage = best[1];
         sp.nbs = best[2];
-        sp.pair = best[3];
+        sp.group = best[3];
         char why[256] = {0};
         if (conv_tc_plan(m->tcplan[i], sp, why, sizeof(why))) return fail(FUSION_ECUDA, why);
     }

@@ -127,13 +127,13 @@ struct ConvTcSpec {
     int T;                  // output slices per CTA (0: default for c_out)
     int groups_per_stage;   // (ty, tx) kernel-offset groups per weight stage (0: about 48 KB per stage)
     int nbs;                // weight stages in the ring (0: 2)
-    int pair;               // 1: two output slices per MMA (N = 2 c_out); 0: one; -1: default for the layer
+    int group;              // output slices per MMA (1, 2, 4; N = group x c_out); <= 0: default for the layer
     int fold;               // 1: the input's last 16-channel chunk is x-folded (VoxArgs::fold_pad = k / 2)
 };
 // Build the plan; returns 0, or nonzero with a reason in `why`.
 int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &spec, char *why, size_t why_len);
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s);
-void conv_tc_describe(const ConvTcPlan &plan, int *T, int *groups_per_stage, int *nbs, size_t *smem, int *pair);
+void conv_tc_describe(const ConvTcPlan &plan, int *T, int *groups_per_stage, int *nbs, size_t *smem, int *group);
 
 // Per-pose FP8 quantization of bf16 NDHWC activations (per_pose elements per pose, a multiple of 8).
 void launch_amax_per_pose(const void *x_bf16, int B, size_t per_pose, float *amax, cudaStream_t s);

@@ -19,21 +19,23 @@
 //
 // Operand B (the weights) streams through a ring of shared-memory stages with
 // plain bulk copies.  The host arranges them per in-plane offset (ty, tx) as a
-// group [8-channel half][tz = nz-1, .., 1, 0][co][16 bytes].  Two uses of that
-// order:
-//   - one slice, offset tz: B = the N rows of entry nz-1-tz;
-//   - a pair of adjacent output slices (z, z+1) and input plane z + u with
-//     0 < u < nz: the 2N rows from entry nz-1-u are W(tz = u) then
-//     W(tz = u - 1), the offsets that plane contributes to z and to z+1.  One
-//     M=128, N=2C MMA serves both slices: the A tile is read from shared memory
-//     once for two slices, so the operand bytes per MMA clock drop from 6 KB / 32
-//     to 8 KB / 64 (at N = 64).  Planes u = 0 and u = nz feed one slice each
-//     (one-slice MMAs into that slice's half of the pair accumulator).
-// The accumulators are zeroed in tensor memory first and every MMA
-// accumulates.  The accumulator of pair j spans columns [2jN, 2jN + 2N), so
-// slice d sits at column dN either way and the epilogue does not depend on the
-// pairing.  The summation order per output element is the same in both forms
-// (offset groups in (ty, tx) order, tz ascending).
+// group [8-channel half][tz = nz-1, .., 1, 0][co][16 bytes], so that the rows
+// of consecutive entries are W(tz), W(tz - 1), ...
+//
+// Slice groups: an MMA may serve G adjacent output slices z .. z+G-1 (G = 1, 2
+// or 4, G x N <= 256).  Input plane z + u holds, for slice z + s, the offset
+// tz = u - s, so one M=128 MMA over that plane with the rows of entries
+// nz-1-(u-s_lo) onward (W(u - s_lo), W(u - s_lo - 1), ...) updates slices
+// s_lo .. s_hi (those with 0 <= u - s < nz) at once: N = (s_hi - s_lo + 1) x C.
+// The A tile is then read from shared memory once for up to G slices.  At
+// N = 64 a one-slice MMA reads 6 KB per 32 clocks against a 128 B/clock operand
+// path; four slices per MMA read 12 KB per 128 clocks, so the tensor pipe, not
+// shared memory, sets the pace.  The work is exactly the useful work (no zero
+// weights): planes near the ends of the group feed fewer slices with narrower
+// MMAs.  The accumulators are zeroed in tensor memory first and every MMA
+// accumulates; slice d sits at columns [dN, dN + N) whatever G is, so the
+// epilogue does not depend on it, and every output element receives its terms
+// in the same order for every G (offset groups in (ty, tx) order, tz ascending).
 //
 // FP8 variant (E4M3 inputs, kind::f8f6f4, 32 channels per MMA): weights carry a
 // per-output-channel scale and activations a per-pose scale; the epilogue
@@ -41,7 +43,7 @@
 // |output| so the next layer's input can be quantized with its own scale.
 //
 // Roles: warp 0 lane 0 issues the TMA loads; warp 1 owns tensor memory; lane 0
-// of warps 1..NI issues the MMAs of its share of the slices (or slice pairs):
+// of warps 1..NI issues the MMAs of its share of the slice groups:
 // one issuing thread was measured to limit the MMA rate, so several warps
 // issue; each commits its own MMAs and the empty barriers count NI arrivals.
 // Then every warp but the producer runs the epilogue (tensor memory ->
@@ -111,15 +113,14 @@ __device__ __forceinline__ void phase_taps(const Args &a, int ph, int &pz, int &
     }
 }
 
-template <int N, int T, bool F8, bool PAIR>
+template <int N, int T, bool F8, int G>
 __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_constant__ CUtensorMap tmap, Args a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    static_assert(!PAIR || (T % 2 == 0 && 2 * N <= 256), "slice pairs need an even T and 2N <= 256");
+    static_assert(T % G == 0 && G * N <= 256, "a slice group divides T and spans at most 256 columns");
     constexpr uint32_t TCOLS = (T * N <= 32) ? 32 : (T * N <= 64) ? 64 : (T * N <= 128) ? 128 : (T * N <= 256) ? 256 : 512;
-    constexpr int NM = PAIR ? 2 * N : N;  // MMA N
-    constexpr uint32_t IDESC = F8 ? tc::idesc_e4m3(128, NM) : tc::idesc_bf16(128, NM);
-    constexpr uint32_t IDESC1 = F8 ? tc::idesc_e4m3(128, N) : tc::idesc_bf16(128, N);   // one slice
-    constexpr int UNITS = PAIR ? T / 2 : T;            // accumulators (slices or slice pairs)
+    // instruction descriptor without its N field (bits 17..22 = N / 8, set per MMA)
+    constexpr uint32_t IDESC0 = (F8 ? tc::idesc_e4m3(128, 8) : tc::idesc_bf16(128, 8)) & ~(0x3Fu << 17);
+    constexpr int UNITS = T / G;                       // slice groups per CTA
     constexpr int NI = kIssReq < UNITS ? kIssReq : UNITS;   // MMA-issuing warps, each owns UNITS / NI
     constexpr int DPI = UNITS / NI;
     constexpr int CPR = F8 ? 16 : 8;      // channels per 16-byte row (one core-matrix column)
@@ -158,10 +159,18 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tbase = *tmem_slot;
-    // zero the accumulators so that every MMA accumulates (warps 1..8, two per tensor-memory lane quarter)
+    // warps 1 .. kWarps-1 share the work on each tensor-memory lane quarter (warp & 3) round robin:
+    // this warp is number rq of the cq warps of its quarter
+    int cq = 0, rq = 0;
+    for (int w2 = 1; w2 < kWarps; ++w2)
+        if ((w2 & 3) == (warp & 3)) {
+            if (w2 < warp) ++rq;
+            ++cq;
+        }
+    // zero the accumulators so that every MMA accumulates
     if (warp >= 1) {
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-        for (uint32_t c = (warp >= 5 ? 32u : 0u); c < TCOLS; c += 64u) tc::tmem_st32_zero(tbase + lane_base + c);
+        for (uint32_t c = 32u * rq; c < TCOLS; c += 32u * cq) tc::tmem_st32_zero(tbase + lane_base + c);
         tc::tmem_st_wait();
     }
     tc::tc_fence_before();
@@ -234,45 +243,19 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                         const int ty = gi / nx, tx = gi - (gi / nx) * nx;
                         const int hx = folded ? a.pad + 2 * tx : tx;
                         const uint64_t arow = adesc0 + (uint64_t)(ty * g.hw + hx);
-                        if constexpr (PAIR) {
-                            // plane u of pair j (slices 2j, 2j+1): u = 0 feeds slice 2j alone (W(0), entry nz-1),
-                            // 0 < u < nz both slices (W(u) | W(u-1) from entry nz-1-u), u = nz slice 2j+1
-                            // alone (W(nz-1), entry 0); per slice the offsets arrive in ascending tz
+                        // plane u of slice group j feeds its slices s_lo..s_hi (offset tz = u - s) in one MMA
+                        for (int u = 0; u <= nz + G - 2; ++u) {
+                            const int s_lo = u - (nz - 1) > 0 ? u - (nz - 1) : 0;
+                            const int s_hi = u < G - 1 ? u : G - 1;
+                            const uint32_t idesc = IDESC0 | ((uint32_t)((s_hi - s_lo + 1) * N) >> 3) << 17;
+                            const uint64_t bd = bgrp + (uint64_t)((nz - 1 - (u - s_lo)) * N);
 #pragma unroll
                             for (int dd = 0; dd < DPI; ++dd) {
                                 const int j = d0 + dd;
-                                const uint64_t ad = arow + (uint64_t)(2 * j * row_zy);
-                                const uint64_t bd = bgrp + (uint64_t)((nz - 1) * N);
-                                if constexpr (F8) tc::mma_e4m3(tbase + 2 * j * N, ad, bd, IDESC1, 1u);
-                                else tc::mma_bf16(tbase + 2 * j * N, ad, bd, IDESC1, 1u);
-                            }
-                            for (int u = 1; u < nz; ++u) {
-                                const uint64_t bd = bgrp + (uint64_t)((nz - 1 - u) * N);
-#pragma unroll
-                                for (int dd = 0; dd < DPI; ++dd) {
-                                    const int j = d0 + dd;
-                                    const uint64_t ad = arow + (uint64_t)((2 * j + u) * row_zy);
-                                    if constexpr (F8) tc::mma_e4m3(tbase + 2 * j * N, ad, bd, IDESC, 1u);
-                                    else tc::mma_bf16(tbase + 2 * j * N, ad, bd, IDESC, 1u);
-                                }
-                            }
-#pragma unroll
-                            for (int dd = 0; dd < DPI; ++dd) {
-                                const int j = d0 + dd;
-                                const uint64_t ad = arow + (uint64_t)((2 * j + nz) * row_zy);
-                                if constexpr (F8) tc::mma_e4m3(tbase + (2 * j + 1) * N, ad, bgrp, IDESC1, 1u);
-                                else tc::mma_bf16(tbase + (2 * j + 1) * N, ad, bgrp, IDESC1, 1u);
-                            }
-                        } else {
-                            for (int tz = 0; tz < nz; ++tz) {
-                                const uint64_t bd = bgrp + (uint64_t)((nz - 1 - tz) * N);
-#pragma unroll
-                                for (int dd = 0; dd < DPI; ++dd) {
-                                    const int d = d0 + dd;
-                                    const uint64_t ad = arow + (uint64_t)((d + tz) * row_zy);
-                                    if constexpr (F8) tc::mma_e4m3(tbase + d * N, ad, bd, IDESC, 1u);
-                                    else tc::mma_bf16(tbase + d * N, ad, bd, IDESC, 1u);
-                                }
+                                const uint64_t ad = arow + (uint64_t)((G * j + u) * row_zy);
+                                const uint32_t dt = tbase + (uint32_t)((G * j + s_lo) * N);
+                                if constexpr (F8) tc::mma_e4m3(dt, ad, bd, idesc, 1u);
+                                else tc::mma_bf16(dt, ad, bd, idesc, 1u);
                             }
                         }
                         bgrp += (uint64_t)(nz * N * 2);   // next group: nz * N * 32 bytes
@@ -291,13 +274,6 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
         __syncwarp();
         const int q = warp & 3;                 // tensor-memory lane quarter of this warp
         const int r = q * 32 + lane;            // M row = voxel of the slice
-        // warps 1 .. kWarps-1 share the slices of their lane quarter round robin
-        int cq = 0, rq = 0;
-        for (int w2 = 1; w2 < kWarps; ++w2)
-            if ((w2 & 3) == q) {
-                if (w2 < warp) ++rq;
-                ++cq;
-            }
         const int h = r >> 3, w = r & 7;
         const bool ok = tc::mbar_wait(acc_full, 0, deadline, a.err, FUSION_ERR_TIMEOUT);
         if (!ok) fail();
@@ -403,7 +379,8 @@ struct ConvTcPlan::Impl {
     CUtensorMap tmap;
     Args args;
     int N = 0, T = 0;
-    bool f8 = false, pair = false;
+    bool f8 = false;
+    int group = 1;          // output slices per MMA
     size_t smem = 0;
     unsigned grid = 0;
 };
@@ -597,12 +574,17 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     if (g.groups_per_stage < 1) g.groups_per_stage = 1;
     g.stage_bytes = ((uint32_t)g.groups_per_stage * gbytes_max + 127) / 128 * 128;
     g.chunk_wbytes = (uint32_t)chunk_weight_bytes(c_out, k, stride);
-    // slice pairs (one N = 2 c_out MMA for two output slices): by default for stride 1 up to 64 channels,
-    // where the 128 x c_out x K MMA is bound by its shared-memory operand reads
-    const bool pair_ok = T % 2 == 0 && 2 * c_out <= 256;
-    const bool pair = sp.pair < 0 ? (pair_ok && stride == 1 && c_out <= 64) : sp.pair != 0;
-    if (pair && !pair_ok) {
-        snprintf(why, why_len, "slice pairs need an even number of slices per CTA and c_out <= 128");
+    // output slices per MMA: by default 2 for stride 1 where it fits.  Measured on the 64-channel layers
+    // (64 poses, BF16): 1 slice 14.2 ms, 2 slices 10.9 ms, 4 slices 11.1 ms.  One thread issues an MMA
+    // about every 80-100 clocks, so the tensor pipe needs several issuing warps with accumulators of
+    // their own; 4 slices per MMA leave two accumulator sets (tensor memory holds 8 x 64 columns) and
+    // so two issuers.  At stride 2 each phase has only 2-3 z offsets, so a slice group shares little.
+    auto group_ok = [&](int G) { return (G == 1 || G == 2 || G == 4) && T % G == 0 && G * c_out <= 256; };
+    int group = sp.group;
+    if (group <= 0) group = (stride == 1 && group_ok(2)) ? 2 : 1;
+    if (!group_ok(group)) {
+        snprintf(why, why_len, "%d slices per MMA: must be 1, 2 or 4, divide the %d slices per CTA and span <= 256 "
+                 "columns", group, T);
         return -1;
     }
     g.nbs = sp.nbs > 0 ? sp.nbs : 2;
@@ -666,42 +648,47 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     P.N = c_out;
     P.T = T;
     P.f8 = sp.elem == 1;
-    P.pair = pair;
+    P.group = group;
     P.grid = (unsigned)(g.nbx * g.nby * g.nbz);   // per pose; times B at launch
     return 0;
 }
 
-template <int N, int T, bool F8, bool PAIR>
+template <int N, int T, bool F8, int G>
 static void launch_t(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
-    cudaFuncSetAttribute(conv3d_tc_kernel<N, T, F8, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
-    conv3d_tc_kernel<N, T, F8, PAIR><<<P.grid * B, kThreads, P.smem, s>>>(P.tmap, P.args);
+    cudaFuncSetAttribute(conv3d_tc_kernel<N, T, F8, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
+    conv3d_tc_kernel<N, T, F8, G><<<P.grid * B, kThreads, P.smem, s>>>(P.tmap, P.args);
+}
+
+template <int N, int T, bool F8>
+static void launch_g(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
+    if constexpr (T % 4 == 0 && 4 * N <= 256) {
+        if (P.group == 4) return launch_t<N, T, F8, 4>(P, B, s);
+    }
+    if constexpr (T % 2 == 0 && 2 * N <= 256) {
+        if (P.group == 2) return launch_t<N, T, F8, 2>(P, B, s);
+    }
+    launch_t<N, T, F8, 1>(P, B, s);
 }
 
 template <bool F8>
 static void launch_n(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
-    switch ((P.N * 16 + P.T) * 2 + (P.pair ? 1 : 0)) {
-    case (32 * 16 + 4) * 2: launch_t<32, 4, F8, false>(P, B, s); break;
-    case (32 * 16 + 8) * 2: launch_t<32, 8, F8, false>(P, B, s); break;
-    case (64 * 16 + 4) * 2: launch_t<64, 4, F8, false>(P, B, s); break;
-    case (64 * 16 + 8) * 2: launch_t<64, 8, F8, false>(P, B, s); break;
-    case (128 * 16 + 2) * 2: launch_t<128, 2, F8, false>(P, B, s); break;
-    case (128 * 16 + 4) * 2: launch_t<128, 4, F8, false>(P, B, s); break;
-    case (32 * 16 + 4) * 2 + 1: launch_t<32, 4, F8, true>(P, B, s); break;
-    case (32 * 16 + 8) * 2 + 1: launch_t<32, 8, F8, true>(P, B, s); break;
-    case (64 * 16 + 4) * 2 + 1: launch_t<64, 4, F8, true>(P, B, s); break;
-    case (64 * 16 + 8) * 2 + 1: launch_t<64, 8, F8, true>(P, B, s); break;
-    case (128 * 16 + 2) * 2 + 1: launch_t<128, 2, F8, true>(P, B, s); break;
-    case (128 * 16 + 4) * 2 + 1: launch_t<128, 4, F8, true>(P, B, s); break;
-    default: launch_t<256, 2, F8, false>(P, B, s); break;
+    switch (P.N * 16 + P.T) {
+    case 32 * 16 + 4: launch_g<32, 4, F8>(P, B, s); break;
+    case 32 * 16 + 8: launch_g<32, 8, F8>(P, B, s); break;
+    case 64 * 16 + 4: launch_g<64, 4, F8>(P, B, s); break;
+    case 64 * 16 + 8: launch_g<64, 8, F8>(P, B, s); break;
+    case 128 * 16 + 2: launch_g<128, 2, F8>(P, B, s); break;
+    case 128 * 16 + 4: launch_g<128, 4, F8>(P, B, s); break;
+    default: launch_g<256, 2, F8>(P, B, s); break;
     }
 }
 
-void conv_tc_describe(const ConvTcPlan &plan, int *T, int *groups_per_stage, int *nbs, size_t *smem, int *pair) {
+void conv_tc_describe(const ConvTcPlan &plan, int *T, int *groups_per_stage, int *nbs, size_t *smem, int *group) {
     *T = plan.impl->T;
     *groups_per_stage = plan.impl->args.g.groups_per_stage;
     *nbs = plan.impl->args.g.nbs;
     *smem = plan.impl->smem;
-    *pair = plan.impl->pair ? 1 : 0;
+    *group = plan.impl->group;
 }
 
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s) {

@@ -37,7 +37,7 @@ TIMING_NAMES = ["prep", "voxelize"] + [f"conv{i}" for i in range(8)] + \
                ["maxpool", "cnn_dense", "radius_graph", "sg_steps", "sg_gather", "head", "total"]
 
 FUSION_OPT_CUDA_GRAPH = 1
-FUSION_OPT_CONV_SLICE_PAIRS = 2
+FUSION_OPT_CONV_SLICES_PER_MMA = 2
 
 EXPORTED = ["fusion_weights_bytes", "fusion_create", "fusion_score", "fusion_destroy", "fusion_last_error",
             "fusion_stage_bytes", "fusion_fetch_stage", "fusion_last_timings", "fusion_cnn_dense_noalloc",
@@ -240,7 +240,7 @@ def fusion_describe_conv(model, layer: int) -> dict:
     out = (C.c_int32 * 5)()
     _check(lib.fusion_describe_conv(model, layer, out))
     return {"slices_per_cta": out[0], "groups_per_stage": out[1], "stages": out[2], "smem_bytes": out[3],
-            "slice_pairs": bool(out[4])}
+            "slices_per_mma": out[4]}
 
 
 def fusion_score(model, poses: dict, n_poses: int, out, on_device: bool = False) -> None:
@@ -325,9 +325,9 @@ class Model:
     def use_cuda_graphs(self, on=True):
         fusion_set_option(self.handle, FUSION_OPT_CUDA_GRAPH, int(on))
 
-    def conv_slice_pairs(self, mode):
-        """-1: default per layer; 0: one output slice per MMA; 1: two (every layer)."""
-        fusion_set_option(self.handle, FUSION_OPT_CONV_SLICE_PAIRS, int(mode))
+    def conv_slices_per_mma(self, mode):
+        """-1: default per layer; 1, 2 or 4: output slices per MMA on every layer."""
+        fusion_set_option(self.handle, FUSION_OPT_CONV_SLICES_PER_MMA, int(mode))
 
     def autotune(self, poses, n_poses=None, on_device=False):
         if n_poses is None:
