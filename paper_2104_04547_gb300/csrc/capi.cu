@@ -211,6 +211,7 @@ struct fusion_model {
     void *grid = nullptr;
     int grid_cx = kGridCxF32;
     int grid_fold = -1;                           // bf16 grid: features 16..18 folded along x at this pad, or -1
+    int fp8_fold = -1;                            // FP8: first conv reads the folded FP8 grid (this pad), or -1
     void *act[FUSION_MAX_CONV] = {};
     void *pool_out = nullptr;
     void *qbuf = nullptr;         // FP8 input of the conv layer being computed
@@ -344,7 +345,7 @@ int load_weights(fusion_model *m, const float *blob) {
         const float *b = take();
         if (m->bf16) {
             const int elem = m->fp8 ? 1 : 2;
-            const bool fold = i == 0 && m->grid_fold >= 0;
+            const int fold = i != 0 ? 0 : m->grid_fold >= 0 ? 1 : m->fp8_fold >= 0 ? 2 : 0;
             std::vector<uint8_t> t(conv_tc_weight_bytes(cx, c.c_out, c.k, c.stride, elem, fold));
             std::vector<float> sw(c.c_out, 1.f);
             conv_tc_arrange_weights(w, c.c_out, c.c_in, cx, c.k, c.stride, elem, fold, t.data(), sw.data());
@@ -468,6 +469,7 @@ int alloc_workspace(fusion_model *m) {
     if (d.pool > 1) RC(dalloc_bytes(m, &m->pool_out, B * m->flat * m->esz));
     if (m->fp8) {
         size_t qmax = B * n3 * m->grid_cx;
+        if (m->fp8_fold >= 0) qmax = std::max(qmax, B * (size_t)d.grid_n * d.grid_n * (d.grid_n + 1) * 64);
         for (int i = 1; i < d.n_conv; ++i) {
             const Shape s = conv_out(d, i);
             qmax = std::max(qmax, B * (size_t)s.n * s.n * s.n * s.c);
@@ -530,7 +532,8 @@ static ConvTcSpec conv_spec(fusion_model *m, int i) {
     sp.residual = c.residual;
     sp.err = m->err;
     sp.group = m->group_mode;
-    sp.fold = (i == 0 && m->grid_fold >= 0) ? 1 : 0;
+    sp.fold = i != 0 ? 0 : m->grid_fold >= 0 ? 1 : m->fp8_fold >= 0 ? 2 : 0;
+    if (sp.fold == 2) sp.cin_pad = 64;
     return sp;
 }
 
@@ -640,6 +643,10 @@ int fusion_create(const fusion_model_desc *desc, const void *weights, size_t wei
         if (m->bf16 && !m->fp8 && !c0.residual &&
             conv_tc_fold_ok(c0.c_in, m->grid_cx, c0.k, c0.stride, 2))
             m->grid_fold = c0.k / 2;
+        // FP8: the first conv reads a quantized grid with channels 0..15 paired along x and 16..18 folded
+        // (4 + 1 x-offsets per kernel row instead of 7 for one 32-channel chunk 13/32 zero)
+        if (m->fp8 && !c0.residual && conv_tc_fold_ok(c0.c_in, m->grid_cx, c0.k, c0.stride, 1))
+            m->fp8_fold = c0.k / 2;
     }
     int rc = alloc_workspace(m);
     if (!rc) rc = load_weights(m, static_cast<const float *>(weights));
@@ -775,7 +782,10 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
                 CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
                 launch_amax_per_pose(m->grid, B, per_pose, m->amax, st);
             }
-            launch_quantize_per_pose(x, m->qbuf, B, per_pose, m->amax, m->qscale, st);
+            if (i == 0 && m->fp8_fold >= 0)
+                launch_quantize_fold_fp8(m->grid, m->qbuf, B, d.grid_n, m->fp8_fold, m->amax, m->qscale, st);
+            else
+                launch_quantize_per_pose(x, m->qbuf, B, per_pose, m->amax, m->qscale, st);
             CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
             conv_tc_launch(m->tcplan[i], B, st);
         } else if (m->bf16) {
@@ -1155,7 +1165,10 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
             const void *xb = (i == 0) ? m->grid : m->act[i - 1];
             cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st);
             launch_amax_per_pose(xb, B, per_pose, m->amax, st);
-            launch_quantize_per_pose(xb, m->qbuf, B, per_pose, m->amax, m->qscale, st);
+            if (i == 0 && m->fp8_fold >= 0)
+                launch_quantize_fold_fp8(xb, m->qbuf, B, d.grid_n, m->fp8_fold, m->amax, m->qscale, st);
+            else
+                launch_quantize_per_pose(xb, m->qbuf, B, per_pose, m->amax, m->qscale, st);
         };
         for (int T : Ts)
             for (int group : {4, 2, 1})

@@ -101,15 +101,16 @@ struct ConvTcPlan {
 };
 // Output slices per CTA for a layer with c_out output channels.
 int conv_tc_tile_slices(int c_out);
-// Bytes of the arranged weights of one layer (elem = 2 for bf16, 1 for FP8 E4M3; fold: the last
-// 16-channel chunk holds 3 channels folded along x, see VoxArgs::fold_pad).
-size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem, bool fold);
-// Whether a layer can read an x-folded input (bf16, stride 1, k in {3, 5, 7}, c_in = 16 x chunks + 3).
+// Bytes of the arranged weights of one layer (elem = 2 for bf16, 1 for FP8 E4M3; fold: 0 plain input,
+// 1 the bf16 grid with channels 16..18 folded along x (VoxArgs::fold_pad), 2 the FP8 folded grid of
+// launch_quantize_fold_fp8).
+size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem, int fold);
+// Whether a first layer can read an x-folded grid (19 channels in 32, stride 1, k in {3, 5, 7}).
 bool conv_tc_fold_ok(int c_in, int cin_pad, int k, int stride, int elem);
 // Blob conv weights [co][ci][k][k][k] -> [channel chunk][phase][ty][tx][16-byte half][tz = nz-1..0][co][16 bytes];
 // FP8 also returns the per-output-channel scales s_w[c_out] (weights = stored code * s_w).
 void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, int elem,
-                             bool fold, uint8_t *out, float *s_w);
+                             int fold, uint8_t *out, float *s_w);
 struct ConvTcSpec {
     const void *x;          // input (bf16 or FP8) [max_poses][n_in]^3[cin_pad], read by TMA
     int elem;               // 2 = bf16, 1 = FP8 E4M3
@@ -128,13 +129,20 @@ struct ConvTcSpec {
     int groups_per_stage;   // (ty, tx) kernel-offset groups per weight stage (0: about 48 KB per stage)
     int nbs;                // weight stages in the ring (0: 2)
     int group;              // output slices per MMA (1, 2, 4; N = group x c_out); <= 0: default for the layer
-    int fold;               // 1: the input's last 16-channel chunk is x-folded (VoxArgs::fold_pad = k / 2)
+    int fold;               // x-folded first-layer input: 0 no, 1 bf16 grid (VoxArgs::fold_pad = k / 2),
+                            // 2 FP8 grid of launch_quantize_fold_fp8 (cin_pad 64, stored from x = -1)
 };
 // Build the plan; returns 0, or nonzero with a reason in `why`.
 int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &spec, char *why, size_t why_len);
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s);
 void conv_tc_describe(const ConvTcPlan &plan, int *T, int *groups_per_stage, int *nbs, size_t *smem, int *group);
 
+// Per-pose FP8 quantization of the plain bf16 grid [B][n]^3[32] (channels 0..18) into the folded layout
+// the first FP8 conv reads, [B][n][n][n + 1][64]: stored voxel j holds channels 0..15 of grid voxels
+// j - 1 and j (slots 0..31), and channels 16..18 of voxels j - 1 - p + s, s = 0 .. 2p (slots 32 + 3 s + f),
+// zero outside the grid and in the unused slots; codes use the per-pose scale of launch_quantize_per_pose.
+void launch_quantize_fold_fp8(const void *grid_bf16, void *q_fp8, int B, int n, int p, const float *amax,
+                              float *scale, cudaStream_t s);
 // Per-pose FP8 quantization of bf16 NDHWC activations (per_pose elements per pose, a multiple of 8).
 void launch_amax_per_pose(const void *x_bf16, int B, size_t per_pose, float *amax, cudaStream_t s);
 void launch_quantize_per_pose(const void *x_bf16, void *q_fp8, int B, size_t per_pose, const float *amax, float *scale,

@@ -80,7 +80,6 @@ struct Geo {
     int nbs;               // B stages
     int na;                // A buffers
     int chunks;            // 16-channel (FP8: 32-channel) chunks of the input
-    uint32_t chunk_wbytes; // arranged weight bytes of one chunk (all phases)
 };
 
 struct Args {
@@ -93,7 +92,9 @@ struct Args {
     const float *bias;          // [N]
     __nv_bfloat16 *y;           // [B][n_out]^3[N]
     int n_in, n_out, cin, k, stride, pad, residual;
-    int fold_nx;                // > 0: the last chunk is x-folded, read at fold_nx x-offsets pad, pad + 2
+    // x-folded input (first layer): chunk c < 2 is read at xt_n[c] x-offsets xt_start[c] + xt_step[c] * t
+    // instead of 0 .. k-1, and the input's x coordinate 0 is voxel x_shift of the stored tensor
+    int xpat, xt_n[2], xt_step[2], xt_start[2], x_shift;
     Geo g;
     unsigned *err;
 };
@@ -186,8 +187,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     if (warp == 0 && lane == 0) {
         // ---------------- producer ----------------
         int &ai = prod_ai, &bi = prod_bi;
+        const uint8_t *wc = a.w;     // weights are consumed in storage order: chunk, phase, (ty, tx) group
         for (int c = 0; c < g.chunks && !*abort_flag; ++c) {
-            const uint8_t *wc = a.w + (size_t)c * g.chunk_wbytes;
             for (int ph = 0; ph < g.nphase && !*abort_flag; ++ph) {
                 int pz, py, px, nz, ny, nx;
                 phase_taps(a, ph, pz, py, px, nz, ny, nx);
@@ -197,9 +198,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                 const int S = a.stride;
                 for (int j = 0; j < 2; ++j)
                     tc::tma_load_5d(sA + buf * a_bytes + j * g.plane_bytes, &tmap, &a_full[buf], c * 2 * CPR + j * CPR,
-                                    x0 * S + px - a.pad, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
+                                    x0 * S + px - a.pad + a.x_shift, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
                 ++ai;
-                if (a.fold_nx > 0 && c == g.chunks - 1) nx = a.fold_nx;
+                if (a.xpat) nx = a.xt_n[c];
                 const int ngr = nz > 0 ? ny * nx : 0;   // a phase without z taps adds nothing
                 const uint32_t gbytes = (uint32_t)nz * N * 32;
                 for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
@@ -229,9 +230,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                 // descriptors advance by plain integer adds: the start-address field counts 16-byte rows
                 const uint64_t adesc0 = tc::desc_kmajor(tc::smem_u32(sA + buf * a_bytes), g.plane_bytes, sbo_a);
                 const uint32_t lbo_b = (uint32_t)nz * N * 16;    // between the two 8-channel halves
-                // an x-folded chunk reads its few x-offsets at halo columns pad, pad + 2 (tx -> pad + 2 tx)
-                const bool folded = a.fold_nx > 0 && c == g.chunks - 1;
-                if (folded) nx = a.fold_nx;
+                // an x-folded chunk reads its few x-offsets at halo columns xt_start + xt_step * tx
+                int xstep = 1, xstart = 0;
+                if (a.xpat) {
+                    nx = a.xt_n[c];
+                    xstep = a.xt_step[c];
+                    xstart = a.xt_start[c];
+                }
                 const int ngr = nz > 0 ? ny * nx : 0;   // a phase without z taps adds nothing
                 for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
                     const int gend = min(g0 + g.groups_per_stage, ngr);
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                     uint64_t bgrp = tc::desc_kmajor(tc::smem_u32(sB + st * g.stage_bytes), lbo_b, 128);
                     for (int gi = g0; gi < gend; ++gi) {
                         const int ty = gi / nx, tx = gi - (gi / nx) * nx;
-                        const int hx = folded ? a.pad + 2 * tx : tx;
+                        const int hx = xstart + xstep * tx;
                         const uint64_t arow = adesc0 + (uint64_t)(ty * g.hw + hx);
                         // plane u of slice group j feeds its slices s_lo..s_hi (offset tz = u - s) in one MMA
                         for (int u = 0; u <= nz + G - 2; ++u) {
@@ -413,20 +418,36 @@ static size_t chunk_weight_bytes(int c_out, int k, int stride) {
     return rows * 16;
 }
 
-// x-offsets of an x-folded chunk: the 5 folded positions cover kernel columns 0..4 at halo column pad,
-// and for k = 7 columns 5, 6 at halo column pad + 2 (slots 3, 4).
+// x-folded first-layer inputs (3 channels beyond the first 16; see VoxArgs::fold_pad and
+// launch_quantize_fold_fp8).  Mode 1 (bf16, two 16-channel chunks): chunk 0 plain; chunk 1 holds
+// channels 16..18 of voxels x-p .. x-p+4 and is read at halo columns p and p + 2 (kernel columns 0..4
+// and, for k = 7, 5..6 from slots 3, 4).  Mode 2 (FP8, two 32-channel chunks, stored from x = -1):
+// chunk 0 holds channels 0..15 of voxels x-1 and x and is read at halo columns 0, 2, 4, .. (kernel
+// columns 2t, 2t+1); chunk 1 holds channels 16..18 of voxels x-p .. x+p and is read at column p.
 static int fold_nx(int k) { return k <= 5 ? 1 : 2; }
 
 bool conv_tc_fold_ok(int c_in, int cin_pad, int k, int stride, int elem) {
-    return elem == 2 && stride == 1 && (k == 3 || k == 5 || k == 7) && cin_pad % 16 == 0 && cin_pad >= 32 &&
-           c_in == cin_pad - 13;
+    return stride == 1 && (k == 3 || k == 5 || k == 7) && c_in == 19 && cin_pad == 32 && (elem == 1 || elem == 2);
 }
 
-size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem, bool fold) {
+static void fold_pattern(int mode, int k, int n[2], int step[2], int start[2]) {
+    const int p = k / 2;
+    if (mode == 1) {
+        n[0] = k; step[0] = 1; start[0] = 0;
+        n[1] = fold_nx(k); step[1] = 2; start[1] = p;
+    } else {
+        n[0] = (k + 1) / 2; step[0] = 2; start[0] = 0;
+        n[1] = 1; step[1] = 1; start[1] = p;
+    }
+}
+
+size_t conv_tc_weight_bytes(int cin_pad, int c_out, int k, int stride, int elem, int fold) {
     const int chunk_bytes_in = 32;                         // one chunk = 32 bytes of channels per voxel
     const int chunks = cin_pad * elem / chunk_bytes_in;
     if (!fold) return (size_t)chunks * chunk_weight_bytes(c_out, k, stride);
-    return (size_t)(chunks - 1) * chunk_weight_bytes(c_out, k, 1) + (size_t)k * fold_nx(k) * k * 2 * c_out * 16;
+    int n[2], st[2], s0[2];
+    fold_pattern(fold, k, n, st, s0);
+    return (size_t)k * (n[0] + n[1]) * k * 2 * c_out * 16;
 }
 
 // float -> E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; largest finite 448, no
@@ -463,7 +484,7 @@ static uint16_t bf16_from_float(float v) {
 }
 
 void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, int k, int stride, int elem,
-                             bool fold, uint8_t *out, float *s_w) {
+                             int fold, uint8_t *out, float *s_w) {
     // blob layout w[co][ci][kd][kh][kw] ->
     //   [chunk][phase][ty][tx][8/16-channel half][tz = nz-1 .. 0][co][16 bytes]
     const int cpr = elem == 2 ? 8 : 16;                // channels per 16-byte row
@@ -477,32 +498,43 @@ void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, i
         }
     }
     size_t idx = 0;
-    const int nchunks = cin_pad / (2 * cpr);
-    for (int c = 0; c < nchunks; ++c) {
-        if (fold && c == nchunks - 1) {
-            // x-folded chunk: slot q < 15 holds channel 16 c + q % 3 at kernel column offset q / 3 from the
-            // group's first column (group 0: columns 0..4; group 1 for k = 7: slots 3, 4 -> columns 5, 6)
-            const int nxf = fold_nx(k);
+    auto put = [&](float v, int co) {
+        if (elem == 2) {
+            const uint16_t h = bf16_from_float(v);
+            memcpy(out + idx, &h, 2);
+            idx += 2;
+        } else {
+            out[idx++] = e4m3_from_float(v / s_w[co]);
+        }
+    };
+    if (fold) {
+        // folded first-layer input: two chunks of 2 x cpr slots; slot q of chunk c at x-offset t reads
+        // channel ch and kernel column kw, or nothing
+        int nt[2], st[2], s0[2];
+        fold_pattern(fold, k, nt, st, s0);
+        for (int c = 0; c < 2; ++c)
             for (int ty = 0; ty < k; ++ty)
-                for (int gx = 0; gx < nxf; ++gx)
+                for (int t = 0; t < nt[c]; ++t)
                     for (int half = 0; half < 2; ++half)
                         for (int e = 0; e < k; ++e) {
                             const int tz = k - 1 - e;
                             for (int co = 0; co < c_out; ++co)
                                 for (int el = 0; el < cpr; ++el) {
-                                    const int q = half * cpr + el, sl = q / 3;
-                                    const int ci = c * 2 * cpr + q % 3;
-                                    const int kw = 2 * gx + sl;
-                                    const bool used = q < 15 && ci < c_in && kw < k && (gx == 0 ? sl < 5 : sl >= 3);
-                                    const float v =
-                                        used ? w[((((size_t)co * c_in + ci) * k + tz) * k + ty) * k + kw] : 0.f;
-                                    const uint16_t h = bf16_from_float(v);
-                                    memcpy(out + idx, &h, 2);
-                                    idx += 2;
+                                    const int q = half * cpr + el;
+                                    int ch = -1, kw = -1;
+                                    if (fold == 1 && c == 0) { ch = q; kw = t; }
+                                    else if (fold == 1) {
+                                        const int sl = q / 3;
+                                        if (q < 15 && (t == 0 ? sl < 5 : sl >= 3)) { ch = 16 + q % 3; kw = 2 * t + sl; }
+                                    } else if (c == 0) { ch = el; kw = 2 * t + half; }
+                                    else if (q < 3 * k) { ch = 16 + q % 3; kw = q / 3; }
+                                    const bool used = ch >= 0 && ch < c_in && kw >= 0 && kw < k;
+                                    put(used ? w[((((size_t)co * c_in + ch) * k + tz) * k + ty) * k + kw] : 0.f, co);
                                 }
                         }
-            continue;
-        }
+        return;
+    }
+    for (int c = 0; c < cin_pad / (2 * cpr); ++c) {
         for (int ph = 0; ph < nph; ++ph) {
             const int pz = stride == 1 ? 0 : (ph >> 2) & 1, py = stride == 1 ? 0 : (ph >> 1) & 1,
                       px = stride == 1 ? 0 : ph & 1;
@@ -551,8 +583,11 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
         snprintf(why, why_len, "tensor-core conv needs input channels padded to %d and stride 1 or 2", chunk_ch);
         return -1;
     }
-    if (sp.fold && (!conv_tc_fold_ok(sp.cin_pad - 13, sp.cin_pad, k, stride, sp.elem) || sp.residual)) {
-        snprintf(why, why_len, "an x-folded input needs bf16, stride 1, k in {3, 5, 7} and no residual");
+    if (sp.fold && (sp.residual || !conv_tc_fold_ok(19, 32, k, stride, sp.elem) ||
+                    (sp.fold == 1 && (sp.elem != 2 || sp.cin_pad != 32)) ||
+                    (sp.fold == 2 && (sp.elem != 1 || sp.cin_pad != 64)) || sp.fold > 2)) {
+        snprintf(why, why_len, "an x-folded input needs 19 channels, stride 1, k in {3, 5, 7}, no residual, and "
+                 "32 bf16 (mode 1) or 64 FP8 (mode 2) stored channels");
         return -1;
     }
     Geo g{};
@@ -573,7 +608,6 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     g.groups_per_stage = sp.groups_per_stage > 0 ? sp.groups_per_stage : (int)(49152 / gbytes_max);
     if (g.groups_per_stage < 1) g.groups_per_stage = 1;
     g.stage_bytes = ((uint32_t)g.groups_per_stage * gbytes_max + 127) / 128 * 128;
-    g.chunk_wbytes = (uint32_t)chunk_weight_bytes(c_out, k, stride);
     // output slices per MMA: by default 2 for stride 1 where it fits.  Measured on the 64-channel layers
     // (64 poses, BF16): 1 slice 14.2 ms, 2 slices 10.9 ms, 4 slices 11.1 ms.  One thread issues an MMA
     // about every 80-100 clocks, so the tensor pipe needs several issuing warps with accumulators of
@@ -614,8 +648,9 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     }
     const cuuint64_t rowb = (cuuint64_t)sp.cin_pad * sp.elem;   // bytes per voxel
     const cuuint64_t n = (cuuint64_t)sp.n_in;
-    cuuint64_t dims[5] = {(cuuint64_t)sp.cin_pad, n, n, n, (cuuint64_t)sp.max_poses};
-    cuuint64_t strides[4] = {rowb, rowb * n, rowb * n * n, rowb * n * n * n};
+    const cuuint64_t nx_in = n + (sp.fold == 2 ? 1 : 0);          // FP8-folded input is stored from x = -1
+    cuuint64_t dims[5] = {(cuuint64_t)sp.cin_pad, nx_in, n, n, (cuuint64_t)sp.max_poses};
+    cuuint64_t strides[4] = {rowb, rowb * nx_in, rowb * nx_in * n, rowb * nx_in * n * n};
     cuuint32_t box[5] = {(cuuint32_t)(16 / sp.elem), (cuuint32_t)(g.hw * stride), (cuuint32_t)(g.hh * stride),
                          (cuuint32_t)(g.hd * stride), 1};
     cuuint32_t estr[5] = {1, (cuuint32_t)stride, (cuuint32_t)stride, (cuuint32_t)stride, 1};
@@ -642,7 +677,9 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     A.stride = stride;
     A.pad = k / 2;
     A.residual = sp.residual;
-    A.fold_nx = sp.fold ? fold_nx(k) : 0;
+    A.xpat = sp.fold ? 1 : 0;
+    A.x_shift = sp.fold == 2 ? 1 : 0;
+    if (sp.fold) fold_pattern(sp.fold, k, A.xt_n, A.xt_step, A.xt_start);
     A.g = g;
     A.err = sp.err;
     P.N = c_out;

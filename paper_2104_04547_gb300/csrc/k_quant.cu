@@ -56,7 +56,77 @@ __global__ void quantize_per_pose_kernel(const __nv_bfloat16 *x, uint8_t *q, siz
     }
 }
 
+// One CTA per 4 grid rows (b, z, y): the rows' channels 0..18 are loaded with 16-byte reads and
+// quantized into shared memory (codes are the same E4M3(x / s) as quantize_per_pose_kernel gives),
+// then each stored voxel j = 0 .. n of a row is assembled from them, as described at
+// launch_quantize_fold_fp8, and written with 16-byte stores.
+constexpr int kFoldRows = 4;
+
+__global__ void __launch_bounds__(256) quantize_fold_fp8_kernel(const __nv_bfloat16 *g, uint8_t *q, int B, int n,
+                                                                 int p, const float *amax, float *scale) {
+    extern __shared__ __align__(16) uint8_t s_code[];     // [kFoldRows][n][20] (19 channels + pad)
+    const int rows = B * n * n;
+    const int r0 = blockIdx.x * kFoldRows;
+    const int nr = min(kFoldRows, rows - r0);
+    const int nn = n * n;
+    for (int e = threadIdx.x; e < nr * n * 3; e += blockDim.x) {
+        // 8 channels (one 16-byte load) of voxel v of row r; chunks 0, 1 = channels 0..15, 2 = 16..23
+        const int r = e / (n * 3), rem = e - r * n * 3, v = rem / 3, part = rem - v * 3;
+        const int row = r0 + r, b = row / nn;
+        const float am = amax[b];
+        const float inv = 1.f / (am > 0.f ? am / kE4M3Max : 1.f);
+        const uint4 t = reinterpret_cast<const uint4 *>(g + ((size_t)row * n + v) * 32)[part];
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&t);
+        uint8_t *dst = s_code + ((size_t)r * n + v) * 20 + part * 8;
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+            const float2 f = __bfloat1622float2(h[k2]);
+            const uint16_t c2 = __nv_cvt_float2_to_fp8x2(make_float2(f.x * inv, f.y * inv), __NV_SATFINITE, __NV_E4M3);
+            if (part < 2 || 2 * k2 < 3) dst[2 * k2] = (uint8_t)(c2 & 0xFF);
+            if (part < 2 || 2 * k2 + 1 < 3) dst[2 * k2 + 1] = (uint8_t)(c2 >> 8);
+        }
+    }
+    if (threadIdx.x < nr && (r0 + threadIdx.x) % nn == 0) {
+        const int b = (r0 + threadIdx.x) / nn;
+        scale[b] = amax[b] > 0.f ? amax[b] / kE4M3Max : 1.f;
+    }
+    __syncthreads();
+    const int nx = n + 1;
+    for (int e = threadIdx.x; e < nr * nx; e += blockDim.x) {
+        const int r = e / nx, j = e - r * nx;
+        const uint8_t *cr = s_code + (size_t)r * n * 20;
+        __align__(16) uint8_t out[64];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int x = j - 1 + h;
+            const bool in = x >= 0 && x < n;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) out[16 * h + c] = in ? cr[x * 20 + c] : 0;
+        }
+#pragma unroll
+        for (int qq = 32; qq < 64; ++qq) out[qq] = 0;
+#pragma unroll
+        for (int sl = 0; sl < 7; ++sl) {              // 2p + 1 <= 7 positions (k <= 7); constant slot indices
+            const int x = j - 1 - p + sl;
+            if (sl > 2 * p || x < 0 || x >= n) continue;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) out[32 + 3 * sl + f] = cr[x * 20 + 16 + f];
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(q + ((size_t)(r0 + r) * nx + j) * 64);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dst[u] = reinterpret_cast<const uint4 *>(out)[u];
+    }
+}
+
 }  // namespace
+
+void launch_quantize_fold_fp8(const void *grid_bf16, void *q_fp8, int B, int n, int p, const float *amax,
+                              float *scale, cudaStream_t s) {
+    const int rows = B * n * n;
+    const size_t sm = (size_t)kFoldRows * n * 20;
+    quantize_fold_fp8_kernel<<<(unsigned)((rows + kFoldRows - 1) / kFoldRows), 256, sm, s>>>(
+        static_cast<const __nv_bfloat16 *>(grid_bf16), static_cast<uint8_t *>(q_fp8), B, n, p, amax, scale);
+}
 
 void launch_amax_per_pose(const void *x_bf16, int B, size_t per_pose, float *amax, cudaStream_t s) {
     const unsigned gx = (unsigned)((per_pose / 8 + 255) / 256 < 64 ? (per_pose / 8 + 255) / 256 : 64);
