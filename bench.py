@@ -42,10 +42,10 @@ L2_FLUSH_BYTES = 256 << 20
 # tensor but the weights scales with the pose count).  Valid only for the kernel source they were taken
 # on: the sha256 prefix of the conv kernel's source files; any other source reports null.
 CONV_TRAFFIC = {
-    "src": "ebebf7bec2de942a",
+    "src": "34e09b288bc27745",
     "poses": 64,
-    "bf16": [1144.4e6, 1649.5e6, 1655.2e6, 1104.3e6],
-    "fp8": [915.2e6, 2125.9e6, 2126.2e6, 568.0e6],
+    "bf16": [1140.7e6, 1649.4e6, 1654.5e6, 1074.9e6],
+    "fp8": [1148.2e6, 2124.2e6, 2119.6e6, 560.1e6],
 }
 
 
@@ -67,23 +67,33 @@ def conv_traffic(dtype, n_poses):
 
 
 def conv_algorithmic_bytes(desc, dtype, n_poses):
-    """Input + output (+ bf16 residual source for FP8) + arranged weights, per conv launch (mean)."""
+    """Input + output (+ the bf16 residual source for FP8) + arranged weights, per conv launch (mean).
+
+    The first layer reads the stored grid: 32 bf16 channels per voxel, or for FP8 the folded grid of
+    n x n x (n + 1) voxels x 64 codes; its weights are arranged for the folded input (BF16: 7 + 2
+    x-offsets per kernel row for k = 7; FP8: 4 + 1).  Other layers: k^3 x 32 bytes x C_out of weights
+    per 32-byte channel chunk."""
     n, tot, cin = desc["grid_n"], [], 32
     elem = 1 if dtype == "fp8" else 2
-    for cv in desc["conv"]:
+    for i, cv in enumerate(desc["conv"]):
         p = cv["k"] // 2
         m = (n + 2 * p - cv["k"]) // cv["stride"] + 1
-        k = cv["k"]
-        if cv["stride"] == 1:
-            taps = k * k * (k + 2)
+        k, co = cv["k"], cv["c_out"]
+        folded = i == 0 and grid_folded(desc)
+        if folded and elem == 2:
+            b_in = n ** 3 * 32 * 2
+            wbytes = k ** 3 * co * 32 + k * (1 if k <= 5 else 2) * k * co * 32
+        elif folded:
+            b_in = n * n * (n + 1) * 64
+            wbytes = k * ((k + 1) // 2 + 1) * k * co * 32
         else:
-            taps = k * k * ((k + 1) // 2 + k // 2 + 4)
-        wbytes = (cin * elem // 32) * taps * 2 * cv["c_out"] * 16
-        b = n ** 3 * cin * elem + m ** 3 * cv["c_out"] * 2
+            b_in = n ** 3 * cin * elem
+            wbytes = (cin * elem // 32) * k ** 3 * co * 32
+        b = b_in + m ** 3 * co * 2
         if elem == 1 and cv["residual"]:
             b += n ** 3 * cin * 2
         tot.append(b * n_poses + wbytes)
-        n, cin = m, cv["c_out"]
+        n, cin = m, co
     return sum(tot) / len(tot)
 
 
