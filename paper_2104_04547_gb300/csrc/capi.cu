@@ -195,6 +195,8 @@ struct fusion_model {
     bool fp8 = false;             // conv operands in FP8 E4M3 (per-channel weight, per-pose activation scales)
     size_t esz = 4;               // bytes per grid / activation element
     ConvTcPlan tcplan[FUSION_MAX_CONV];
+    DenseTcPlan dense_tc;                         // tensor-core CNN dense (bf16 / FP8 models)
+    int dense_tc_splits = 0;
     int pool_n = 0, pool_c = 0, flat = 0, splits = 1;
     float *we_t[FUSION_MAX_STAGES][2] = {}, *be[FUSION_MAX_STAGES][2] = {};
     float *wih_t[FUSION_MAX_STAGES] = {}, *whh_t[FUSION_MAX_STAGES] = {}, *bih[FUSION_MAX_STAGES] = {}, *bhh[FUSION_MAX_STAGES] = {};
@@ -478,7 +480,8 @@ int alloc_workspace(fusion_model *m) {
         RC(dalloc(m, &m->amax, B));
         RC(dalloc(m, &m->qscale, B));
     }
-    RC(dalloc(m, &m->dense_part, (size_t)m->splits * B * d.cnn_dense));
+    if (m->bf16) m->dense_tc_splits = dense_tc_splits(m->flat, d.cnn_dense);
+    RC(dalloc(m, &m->dense_part, (size_t)std::max(m->splits, m->dense_tc_splits) * B * d.cnn_dense));
     RC(dalloc(m, &m->cnn_lat, B * d.cnn_dense));
     for (int e = 0; e < 2; ++e) {
         RC(dalloc(m, &m->e_beg[e], A));
@@ -545,6 +548,16 @@ static int plan_tensor_core_convs(fusion_model *m) {
         if (r) return fail(r == -1 ? FUSION_EUNSUPPORTED : FUSION_ECUDA, std::string("conv layer ") +
                                                                              std::to_string(i) + ": " + why);
     }
+    return FUSION_OK;
+}
+
+// The dense layer reads the pooled map (or the last conv output when there is no pool).
+static int plan_tensor_core_dense(fusion_model *m) {
+    const void *x = m->d.pool > 1 ? m->pool_out : m->act[m->d.n_conv - 1];
+    char why[256] = {0};
+    const int r = dense_tc_plan(m->dense_tc, x, m->dense_w, m->d.max_poses, m->d.cnn_dense, m->flat, m->err, why,
+                                sizeof(why));
+    if (r) return fail(r == -1 ? FUSION_EUNSUPPORTED : FUSION_ECUDA, std::string("cnn dense: ") + why);
     return FUSION_OK;
 }
 
@@ -651,6 +664,7 @@ int fusion_create(const fusion_model_desc *desc, const void *weights, size_t wei
     int rc = alloc_workspace(m);
     if (!rc) rc = load_weights(m, static_cast<const float *>(weights));
     if (!rc && m->bf16) rc = plan_tensor_core_convs(m);
+    if (!rc && m->bf16) rc = plan_tensor_core_dense(m);
     if (rc) {
         std::string keep = g_err;
         fusion_destroy(m);
@@ -812,7 +826,14 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     }
     DenseArgs da{flat_in, m->dense_w, m->dense_b, m->dense_part, m->cnn_lat, B, d.cnn_dense, m->flat, m->splits,
                  m->bf16 ? 1 : 0, 1};
-    launch_dense(da, st);
+    if (m->bf16) {
+        // tensor cores: split partials, then the same fixed-order reduction
+        dense_tc_launch(m->dense_tc, B, m->dense_part, st);
+        da.splits = m->dense_tc_splits;
+        launch_dense_reduce(da, st);
+    } else {
+        launch_dense(da, st);
+    }
     RC(check_launch("dense"));
     map[11] = ei; mark();
 

@@ -88,6 +88,23 @@ struct DenseArgs {
 };
 void launch_dense(const DenseArgs &a, cudaStream_t s);
 int dense_splits(int K);
+// The fixed-order split reduction + bias + activation of launch_dense, on partials [splits][B][N].
+void launch_dense_reduce(const DenseArgs &a, cudaStream_t s);
+
+// Tensor-core (tcgen05) bf16 CNN dense: a plan holds the TMA tensor maps of the model's pooled-input
+// buffer x [max_poses][K] and weights w [N][K]; launch writes the FP32 split partials [splits][B][N].
+struct DenseTcPlan {
+    struct Impl;
+    Impl *impl;
+    DenseTcPlan();
+    ~DenseTcPlan();
+    DenseTcPlan(const DenseTcPlan &) = delete;
+    DenseTcPlan &operator=(const DenseTcPlan &) = delete;
+};
+int dense_tc_splits(int K, int N);
+int dense_tc_plan(DenseTcPlan &plan, const void *x, const void *w, int max_poses, int N, int K, unsigned *err,
+                  char *why, size_t why_len);
+void dense_tc_launch(DenseTcPlan &plan, int B, float *part, cudaStream_t s);
 
 // Tensor-core (tcgen05) BF16 conv: a plan per layer holds the TMA tensor map of
 // the layer's input buffer and the launch geometry.

@@ -154,6 +154,11 @@ void launch_dense(const DenseArgs &a, cudaStream_t s) {
     dense_reduce_kernel<<<(tot + 255) / 256, 256, 0, s>>>(a);
 }
 
+void launch_dense_reduce(const DenseArgs &a, cudaStream_t s) {
+    const int tot = a.B * a.N;
+    dense_reduce_kernel<<<(tot + 255) / 256, 256, 0, s>>>(a);
+}
+
 void launch_head(const HeadArgs &a, cudaStream_t s) {
     head_kernel<<<a.B, 256, 0, s>>>(a);
 }
