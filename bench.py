@@ -303,12 +303,24 @@ def run_ours(args):
 
     # |affinity difference| against the FP32 path on the same batch (outside the timed region)
     delta = None
+    fp32_path = None
     if args.dtype != "f32" and not args.no_f32_compare:
         got = out.float().cpu().numpy().copy()
         d32 = configs.model(MODEL, dtype="f32")
         m32 = F.Model(d32, weights.to_blob(d32, W), max_poses=B, max_atoms=1200, max_degree=64,
                       stream=stream.cuda_stream)
-        ref = m32.score(batch)
+        ref = m32.score(batch).copy()
+        # the plain FP32 path (CUDA cores) on the same GPU in the same run: one more step, timed
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        out32 = torch.empty(B, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m32.score(devb, n_poses=B, out=out32, on_device=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t32 = e0.elapsed_time(e1)
+        fp32_path = {"value": B / (t32 / 1000.0), "unit": "poses/s", "ms_per_step": t32,
+                     "note": "FP32 CUDA-core path, same batch and GPU, one step after one untimed step"}
         m32.close()
         dd = np.abs(got - ref)
         delta = {"vs": "f32 path, same poses and weights", "mean": float(dd.mean()), "max": float(dd.max()),
@@ -364,6 +376,8 @@ def run_ours(args):
     }
     if delta is not None:
         line["delta_affinity"] = delta
+    if fp32_path is not None:
+        line["fp32_path"] = fp32_path
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

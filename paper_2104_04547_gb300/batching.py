@@ -10,6 +10,14 @@ CUDA-graph replay).
 
 measures poses/s over the packed batches with plain launches, with CUDA graphs,
 and with graphs after the conv tile autotuner, and prints one JSON line each.
+
+    python -m paper_2104_04547_gb300.batching --batch-sweep 1,12,23,56,64,128,256
+
+is the batch-size study (the paper compares 12, 23 and 56 poses per rank and
+transfer, Section 4.3): for each size, the same pool is cut into batches of at
+most that many poses and scored end to end through the host-pointer call
+(host-to-device copy of each batch and device-to-host copy of its affinities
+included), one JSON line per size with poses/s and the per-call latency.
 """
 
 from __future__ import annotations
@@ -90,12 +98,50 @@ def run(args):
     m.close()
 
 
+def batch_sweep(args):
+    import torch
+
+    from paper_2104_04547_gb300 import build
+    build.build()
+    from paper_2104_04547_gb300 import fusion as F
+    from synth import configs, poses, weights
+
+    torch.cuda.set_device(0)
+    desc = configs.model("fusion-48grid-c64", dtype=args.dtype)
+    blob = weights.to_blob(desc, weights.init_weights(desc, 0))
+    pool = poses.make_uneven_pool(args.groups, 10)
+    sizes = [len(p[0]) for p in pool]
+    for mb in [int(v) for v in args.batch_sweep.split(",")]:
+        batches = pack_by_atoms(sizes, mb, mb * 700)
+        packed = [poses.pack([pool[i] for i in b]) for b in batches]
+        m = F.Model(desc, blob, max_poses=mb, max_atoms=1200)
+        for pb in packed[:2]:
+            m.score(pb)
+        lat = []
+        t0 = time.perf_counter()
+        for pb in packed:
+            t = time.perf_counter()
+            m.score(pb)                      # host inputs in, affinities back on the host
+            lat.append(time.perf_counter() - t)
+        dt = time.perf_counter() - t0
+        m.close()
+        print(json.dumps({"study": "poses per call", "dtype": args.dtype, "max_batch": mb, "calls": len(packed),
+                          "poses": len(pool), "poses_per_s": len(pool) / dt,
+                          "call_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
+                                      "p99": 1e3 * float(np.percentile(lat, 99))}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--groups", type=int, default=100)
     ap.add_argument("--dtype", choices=["f32", "bf16", "fp8"], default="bf16")
     ap.add_argument("--max-batch", type=int, default=64)
-    run(ap.parse_args())
+    ap.add_argument("--batch-sweep", default="", help="comma-separated batch sizes: run the batch-size study")
+    args = ap.parse_args()
+    if args.batch_sweep:
+        batch_sweep(args)
+    else:
+        run(args)
 
 
 if __name__ == "__main__":
