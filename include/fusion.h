@@ -49,6 +49,12 @@ extern "C" {
 #define FUSION_GATHER_LINEAR 0   /* sum_i (W h_i + b) over ligand atoms i */
 #define FUSION_GATHER_GATED  1   /* sum_i sigmoid(W_g [h_i, x_i] + b_g) * (W_o h_i + b_o) */
 
+/* Fusion forms (Section 2.2 and Section 3.3.3): how the two branch latents become an affinity. */
+#define FUSION_COHERENT 0   /* fusion layers on [cnn latent, sg latent] (Table V) */
+#define FUSION_MID      1   /* model-specific dense layers on each latent first, their outputs appended
+                               to the latents, then the fusion layers (Mid-level Fusion, Table IV) */
+#define FUSION_LATE     2   /* mean of the two branches' own affinities (Late Fusion); no fusion layers */
+
 #define FUSION_MAX_CONV   8
 #define FUSION_MAX_STAGES 2
 #define FUSION_MAX_HEAD   6
@@ -80,13 +86,20 @@ typedef struct {
     int32_t sg_gather_width;   /* G: width of the SG latent (<= 256) */
     float   cut_cov;           /* covalent cutoff, Angstrom */
     float   cut_nc;            /* non-covalent cutoff, Angstrom (> cut_cov) */
-    int32_t n_head;            /* fusion (head) layers (1..FUSION_MAX_HEAD) */
-    int32_t head[FUSION_MAX_HEAD];  /* output widths; the last must be 1 */
+    int32_t n_head;            /* fusion (head) layers (1..FUSION_MAX_HEAD; 0 for FUSION_LATE) */
+    int32_t head[FUSION_MAX_HEAD];  /* output widths (<= 1024); the last must be 1 */
     int32_t dtype;             /* FUSION_F32 / FUSION_BF16 / FUSION_FP8 */
     int32_t max_poses;         /* batch capacity of one fusion_score call */
     int32_t max_atoms;         /* atom capacity of one pose (<= 4096) */
     int32_t max_degree;        /* edge capacity per atom and edge type (mean over a pose) */
     int32_t keep_stages;       /* 1: keep every intermediate for fusion_fetch_stage (more memory) */
+    int32_t fusion;            /* FUSION_COHERENT / FUSION_MID / FUSION_LATE */
+    int32_t n_cnn_out;         /* branch layers on the CNN latent (0 for coherent; >= 1 otherwise) */
+    int32_t cnn_out[FUSION_MAX_HEAD];  /* their widths (late: the last must be 1) */
+    int32_t n_sg_out;          /* branch layers on the SG latent, as n_cnn_out */
+    int32_t sg_out[FUSION_MAX_HEAD];
+    int32_t head_residual;     /* 1: a hidden fusion layer whose input and output widths match returns
+                                  x + SELU(W x + b) */
 } fusion_model_desc;
 
 /* A batch of poses in packed structure-of-arrays form.  Ligand atoms come
@@ -110,7 +123,12 @@ typedef struct fusion_model fusion_model;
  *                GRU W_ih [3H][H], W_hh [3H][H], b_ih [3H], b_hh [3H] (gate rows reset, update, new);
  *                if sg_gate and s is not the last stage: W_i [H][2H], b_i [H], W_j [H][H], b_j [H]
  *   gather: gated: W_g [G][2H], b_g [G], W_o [G][H], b_o [G]; linear: W [G][H], b [G]
- *   per head layer l: W [out][in], b [out]  (in = cnn_dense + G for l = 0)
+ *   per CNN branch layer l: W [out][in], b [out]  (in = cnn_dense for l = 0)
+ *   per SG branch layer l: W [out][in], b [out]   (in = G for l = 0)
+ *   per head layer l: W [out][in], b [out]  (in = cnn_dense + G for l = 0, plus the last CNN and SG
+ *                                            branch widths for FUSION_MID)
+ * Branch layers: FUSION_MID applies SELU after each; FUSION_LATE applies ReLU between them, the last
+ * linear, and averages the two branch outputs.  Fusion layers: SELU between, the last linear.
  * Returns 0 if the descriptor is invalid. */
 size_t fusion_weights_bytes(const fusion_model_desc *desc);
 

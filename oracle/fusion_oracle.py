@@ -295,14 +295,51 @@ def selu(x):
     return SELU_SCALE * np.where(x > 0, x, SELU_ALPHA * (np.exp(np.minimum(x, 0.0)) - 1.0))
 
 
+def _dense(W, name, v):
+    return W[f"{name}.w"].astype(np.float64) @ v + W[f"{name}.b"].astype(np.float64)
+
+
 def head(desc, W, cnn, sg):
-    """Fusion layers (Section 3.3.3, Table V): Linear -> SELU ... -> Linear -> affinity."""
+    """Affinity from the two latents.
+
+    Coherent Fusion (Section 3.3.3, Table V): the concatenated latents through
+    the fusion layers, Linear -> SELU ... -> Linear.  Mid-level Fusion (Section
+    2.2, Table IV): each latent first through its model-specific dense layers
+    (Linear -> SELU each), those outputs concatenated after the two latents,
+    then the fusion layers.  Late Fusion (Section 2.2): the unweighted mean of
+    the two branches' own affinities, each branch a stack Linear -> ReLU ... ->
+    Linear of final width 1.  With head_residual, a hidden fusion layer whose
+    input and output widths match returns x + SELU(W x + b).
+    """
+    mode = desc.get("fusion", "coherent")
+    cnn = np.asarray(cnn, dtype=np.float64)
+    sg = np.asarray(sg, dtype=np.float64)
+    if mode == "late":
+        out = []
+        for br, v in (("cnn_out", cnn), ("sg_out", sg)):
+            n = len(desc[br])
+            for l in range(n):
+                v = _dense(W, f"{br}{l}", v)
+                if l + 1 < n:
+                    v = relu(v)
+            out.append(float(v[0]))
+        return 0.5 * (out[0] + out[1])
     v = np.concatenate([cnn, sg])
+    if mode == "mid":
+        parts = [cnn, sg]
+        for br, u in (("cnn_out", cnn), ("sg_out", sg)):
+            for l in range(len(desc[br])):
+                u = selu(_dense(W, f"{br}{l}", u))
+            parts.append(u)
+        v = np.concatenate(parts)
     L = len(desc["head"])
     for l in range(L):
-        v = W[f"head{l}.w"].astype(np.float64) @ v + W[f"head{l}.b"]
+        u = _dense(W, f"head{l}", v)
         if l + 1 < L:
-            v = selu(v)
+            u = selu(u)
+            if desc.get("head_residual", 0) and u.shape == v.shape:
+                u = v + u
+        v = u
     return float(v[0])
 
 

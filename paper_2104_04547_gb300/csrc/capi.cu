@@ -98,11 +98,29 @@ bool check_desc(const fusion_model_desc *d, std::string *why) {
     REQ(d->sg_gather == FUSION_GATHER_LINEAR || d->sg_gather == FUSION_GATHER_GATED, "bad sg_gather");
     REQ(d->sg_gather_width >= 1 && d->sg_gather_width <= 256, "sg_gather_width must be in [1, 256]");
     REQ(d->cnn_dense + d->sg_gather_width <= 512, "cnn_dense + sg_gather_width must be <= 512");
+    REQ(d->fusion == FUSION_COHERENT || d->fusion == FUSION_MID || d->fusion == FUSION_LATE, "bad fusion form");
+    REQ(d->n_cnn_out >= 0 && d->n_cnn_out <= FUSION_MAX_HEAD && d->n_sg_out >= 0 && d->n_sg_out <= FUSION_MAX_HEAD,
+        "branch layer counts must be in [0, 6]");
+    for (int l = 0; l < d->n_cnn_out; ++l) REQ(d->cnn_out[l] >= 1 && d->cnn_out[l] <= 1024, "branch widths must be in [1, 1024]");
+    for (int l = 0; l < d->n_sg_out; ++l) REQ(d->sg_out[l] >= 1 && d->sg_out[l] <= 1024, "branch widths must be in [1, 1024]");
+    REQ(d->head_residual == 0 || d->head_residual == 1, "head_residual must be 0 or 1");
+    if (d->fusion == FUSION_COHERENT) REQ(d->n_cnn_out == 0 && d->n_sg_out == 0, "coherent fusion has no branch layers");
+    if (d->fusion != FUSION_COHERENT) REQ(d->n_cnn_out >= 1 && d->n_sg_out >= 1, "mid and late fusion need branch layers");
+    if (d->fusion == FUSION_MID)
+        REQ(d->cnn_dense + d->sg_gather_width + d->cnn_out[d->n_cnn_out - 1] + d->sg_out[d->n_sg_out - 1] <= 1024,
+            "mid-level fusion input (latents + branch outputs) must be <= 1024 wide");
+    if (d->fusion == FUSION_LATE) {
+        REQ(d->cnn_out[d->n_cnn_out - 1] == 1 && d->sg_out[d->n_sg_out - 1] == 1,
+            "late fusion branch outputs must end in width 1");
+        REQ(d->n_head == 0, "late fusion has no fusion layers (n_head = 0)");
+    }
     REQ(std::isfinite(d->cut_cov) && std::isfinite(d->cut_nc) && d->cut_cov > 0.f && d->cut_nc > d->cut_cov,
         "cutoffs must satisfy 0 < cut_cov < cut_nc");
-    REQ(d->n_head >= 1 && d->n_head <= FUSION_MAX_HEAD, "n_head must be in [1, 6]");
-    for (int l = 0; l < d->n_head; ++l) REQ(d->head[l] >= 1 && d->head[l] <= 512, "head widths must be in [1, 512]");
-    REQ(d->head[d->n_head - 1] == 1, "the last head layer must have width 1");
+    if (d->fusion != FUSION_LATE) {
+        REQ(d->n_head >= 1 && d->n_head <= FUSION_MAX_HEAD, "n_head must be in [1, 6]");
+        for (int l = 0; l < d->n_head; ++l) REQ(d->head[l] >= 1 && d->head[l] <= 1024, "head widths must be in [1, 1024]");
+        REQ(d->head[d->n_head - 1] == 1, "the last head layer must have width 1");
+    }
     REQ(d->dtype == FUSION_F32 || d->dtype == FUSION_BF16 || d->dtype == FUSION_FP8, "bad dtype");
     REQ(d->max_poses >= 1 && d->max_poses <= 65535, "max_poses must be in [1, 65535]");
     REQ(d->max_atoms >= 1 && d->max_atoms <= 4096, "max_atoms must be in [1, 4096]");
@@ -111,6 +129,13 @@ bool check_desc(const fusion_model_desc *d, std::string *why) {
     REQ(((long long)f.c * f.n * f.n * f.n) % 8 == 0, "flattened CNN width must be a multiple of 8");
     return true;
 #undef REQ
+}
+
+// Width of the first fusion layer's input: the two latents, plus the branch outputs for mid-level fusion.
+static int head_input_width(const fusion_model_desc &d) {
+    int w = d.cnn_dense + d.sg_gather_width;
+    if (d.fusion == FUSION_MID) w += d.cnn_out[d.n_cnn_out - 1] + d.sg_out[d.n_sg_out - 1];
+    return w;
 }
 
 struct TensorSpec {
@@ -162,7 +187,18 @@ std::vector<TensorSpec> blob_layout(const fusion_model_desc &d) {
         L.push_back({"gather.w", G * H});
         L.push_back({"gather.b", G});
     }
-    size_t fin = d.cnn_dense + G;
+    for (int br = 0; br < 2; ++br) {
+        const int nl = br == 0 ? d.n_cnn_out : d.n_sg_out;
+        const int32_t *wd = br == 0 ? d.cnn_out : d.sg_out;
+        size_t bin = br == 0 ? (size_t)d.cnn_dense : G;
+        for (int l = 0; l < nl; ++l) {
+            const std::string p = (br == 0 ? "cnn_out" : "sg_out") + std::to_string(l);
+            L.push_back({p + ".w", (size_t)wd[l] * bin});
+            L.push_back({p + ".b", (size_t)wd[l]});
+            bin = wd[l];
+        }
+    }
+    size_t fin = head_input_width(d);
     for (int l = 0; l < d.n_head; ++l) {
         L.push_back({"head" + std::to_string(l) + ".w", (size_t)d.head[l] * fin});
         L.push_back({"head" + std::to_string(l) + ".b", (size_t)d.head[l]});
@@ -203,6 +239,7 @@ struct fusion_model {
     float *gi_t = nullptr, *gbi = nullptr, *gj_t = nullptr, *gbj = nullptr;
     float *gat_wg_t = nullptr, *gat_bg = nullptr, *gat_wo_t = nullptr, *gat_bo = nullptr;
     float *head_wt[FUSION_MAX_HEAD] = {}, *head_b[FUSION_MAX_HEAD] = {};
+    float *br_wt[2][FUSION_MAX_HEAD] = {}, *br_b[2][FUSION_MAX_HEAD] = {};   // CNN / SG branch layers
 
     // workspace (device)
     int32_t *in_off = nullptr, *in_nlig = nullptr;
@@ -428,7 +465,19 @@ int load_weights(fusion_model *m, const float *blob) {
         RC(upload(m, &m->gat_wo_t, transpose(w, G, H)));
         RC(upload(m, &m->gat_bo, std::vector<float>(b, b + G)));
     }
-    int fin = d.cnn_dense + G;
+    for (int br = 0; br < 2; ++br) {
+        const int nl = br == 0 ? d.n_cnn_out : d.n_sg_out;
+        const int32_t *wd = br == 0 ? d.cnn_out : d.sg_out;
+        int bin = br == 0 ? d.cnn_dense : G;
+        for (int l = 0; l < nl; ++l) {
+            const float *w = take();
+            const float *b = take();
+            RC(upload(m, &m->br_wt[br][l], transpose(w, wd[l], bin)));
+            RC(upload(m, &m->br_b[br][l], std::vector<float>(b, b + wd[l])));
+            bin = wd[l];
+        }
+    }
+    int fin = head_input_width(d);
     for (int l = 0; l < d.n_head; ++l) {
         const float *w = take();
         const float *b = take();
@@ -851,6 +900,18 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
         ha.width[l] = d.head[l];
     }
     ha.n_layers = d.n_head;
+    for (int br = 0; br < 2; ++br) {
+        const int nl = br == 0 ? d.n_cnn_out : d.n_sg_out;
+        const int32_t *wd = br == 0 ? d.cnn_out : d.sg_out;
+        ha.n_branch[br] = nl;
+        for (int l = 0; l < nl; ++l) {
+            ha.bwt[br][l] = m->br_wt[br][l];
+            ha.bb[br][l] = m->br_b[br][l];
+            ha.bwidth[br][l] = wd[l];
+        }
+    }
+    ha.mode = d.fusion;
+    ha.residual = d.head_residual;
     ha.B = B;
     ha.Dc = d.cnn_dense;
     ha.G = d.sg_gather_width;

@@ -223,13 +223,20 @@ void launch_sg_gather(const SgGatherArgs &a, cudaStream_t s);
 
 // ---- head ------------------------------------------------------------------
 
+constexpr int kHeadMaxWidth = 1024;
 struct HeadArgs {
     const float *cnn;      // [B][Dc]
     const float *sg;       // [B][G]
-    const float *wt[FUSION_MAX_HEAD];   // [in][out] transposed
+    const float *wt[FUSION_MAX_HEAD];   // fusion layers, [in][out] transposed
     const float *b[FUSION_MAX_HEAD];
     int width[FUSION_MAX_HEAD];
     int n_layers;
+    const float *bwt[2][FUSION_MAX_HEAD];   // branch layers (0: CNN latent, 1: SG latent), [in][out]
+    const float *bb[2][FUSION_MAX_HEAD];
+    int bwidth[2][FUSION_MAX_HEAD];
+    int n_branch[2];
+    int mode;              // FUSION_COHERENT / FUSION_MID / FUSION_LATE
+    int residual;          // hidden fusion layers with equal widths add their input
     int B, Dc, G;
     float *out;            // [B]
 };

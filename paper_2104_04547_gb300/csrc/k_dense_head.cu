@@ -127,24 +127,72 @@ __device__ __forceinline__ float selu(float x) {
     return x > 0.f ? scale * x : scale * alpha * expm1f(x);
 }
 
+// One dense layer of the head for one pose, all threads of the CTA: out[o] = act(b[o] + sum_k in[k] W[o][k])
+// (weights stored transposed, [in][out]); act 0 = none, 1 = ReLU, 2 = SELU; `res` adds in[o] after the
+// activation.  `in` and `out` are distinct shared-memory buffers.
+__device__ void head_layer(const float *in, int fin, float *out, int fout, const float *wt, const float *bias,
+                           int act, bool res) {
+    for (int o = threadIdx.x; o < fout; o += blockDim.x) {
+        float s = bias[o];
+        for (int k = 0; k < fin; ++k) s = fmaf(wt[(size_t)k * fout + o], in[k], s);
+        if (act == 1) s = fmaxf(s, 0.f);
+        else if (act == 2) s = selu(s);
+        out[o] = res ? in[o] + s : s;
+    }
+    __syncthreads();
+}
+
+// Coherent Fusion: fusion layers on [cnn, sg].  Mid-level: each latent through its branch layers (SELU
+// after each), the two results appended after the latents, then the fusion layers.  Late: each latent
+// through its own affinity stack (ReLU between, last linear), the mean of the two.
 __global__ void __launch_bounds__(256) head_kernel(HeadArgs a) {
-    __shared__ float v[2][512];
+    __shared__ float v[3][kHeadMaxWidth];
     const int p = blockIdx.x;
     const int fin0 = a.Dc + a.G;
     for (int i = threadIdx.x; i < fin0; i += blockDim.x)
         v[0][i] = i < a.Dc ? a.cnn[(size_t)p * a.Dc + i] : a.sg[(size_t)p * a.G + (i - a.Dc)];
     __syncthreads();
-    int fin = fin0, cur = 0;
+    if (a.mode == FUSION_LATE) {
+        float aff[2];
+        for (int br = 0; br < 2; ++br) {
+            const float *in = v[0] + (br == 0 ? 0 : a.Dc);
+            int fin = br == 0 ? a.Dc : a.G, cur = 1;
+            for (int l = 0; l < a.n_branch[br]; ++l) {
+                const bool last = l + 1 == a.n_branch[br];
+                head_layer(in, fin, v[cur], a.bwidth[br][l], a.bwt[br][l], a.bb[br][l], last ? 0 : 1, false);
+                in = v[cur];
+                cur = cur == 1 ? 2 : 1;
+                fin = a.bwidth[br][l];
+            }
+            aff[br] = in[0];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) a.out[p] = 0.5f * (aff[0] + aff[1]);
+        return;
+    }
+    int fin = fin0;
+    if (a.mode == FUSION_MID) {
+        for (int br = 0; br < 2; ++br) {
+            const float *in = v[0] + (br == 0 ? 0 : a.Dc);
+            int bin = br == 0 ? a.Dc : a.G, cur = 1;
+            for (int l = 0; l < a.n_branch[br]; ++l) {
+                head_layer(in, bin, v[cur], a.bwidth[br][l], a.bwt[br][l], a.bb[br][l], 2, false);
+                in = v[cur];
+                cur = cur == 1 ? 2 : 1;
+                bin = a.bwidth[br][l];
+            }
+            for (int i = threadIdx.x; i < bin; i += blockDim.x) v[0][fin + i] = in[i];
+            __syncthreads();
+            fin += bin;
+        }
+    }
+    int cur = 0;
     for (int l = 0; l < a.n_layers; ++l) {
         const int fout = a.width[l];
-        const float *wt = a.wt[l];
-        for (int o = threadIdx.x; o < fout; o += blockDim.x) {
-            float s = a.b[l][o];
-            for (int k = 0; k < fin; ++k) s = fmaf(wt[(size_t)k * fout + o], v[cur][k], s);
-            v[cur ^ 1][o] = (l + 1 < a.n_layers) ? selu(s) : s;
-        }
-        __syncthreads();
-        cur ^= 1;
+        const bool last = l + 1 == a.n_layers;
+        const int nxt = cur == 0 ? 1 : 0;
+        head_layer(v[cur], fin, v[nxt], fout, a.wt[l], a.b[l], last ? 0 : 2, !last && a.residual && fin == fout);
+        cur = nxt;
         fin = fout;
     }
     if (threadIdx.x == 0) a.out[p] = v[cur][0];

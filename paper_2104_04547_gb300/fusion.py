@@ -36,6 +36,9 @@ STAGE_EDGES_COV, STAGE_EDGES_NC, STAGE_SG_STATE, STAGE_SG_LATENT, STAGE_AFFINITY
 TIMING_NAMES = ["prep", "voxelize"] + [f"conv{i}" for i in range(8)] + \
                ["maxpool", "cnn_dense", "radius_graph", "sg_steps", "sg_gather", "head", "total"]
 
+FUSION_COHERENT, FUSION_MID, FUSION_LATE = 0, 1, 2
+FUSION_FORMS = {"coherent": FUSION_COHERENT, "mid": FUSION_MID, "late": FUSION_LATE}
+
 FUSION_OPT_CUDA_GRAPH = 1
 FUSION_OPT_CONV_SLICES_PER_MMA = 2
 
@@ -68,7 +71,9 @@ class fusion_model_desc(C.Structure):
                 ("sg_gather_width", C.c_int32), ("cut_cov", C.c_float), ("cut_nc", C.c_float),
                 ("n_head", C.c_int32), ("head", C.c_int32 * MAX_HEAD), ("dtype", C.c_int32),
                 ("max_poses", C.c_int32), ("max_atoms", C.c_int32), ("max_degree", C.c_int32),
-                ("keep_stages", C.c_int32)]
+                ("keep_stages", C.c_int32), ("fusion", C.c_int32), ("n_cnn_out", C.c_int32),
+                ("cnn_out", C.c_int32 * MAX_HEAD), ("n_sg_out", C.c_int32), ("sg_out", C.c_int32 * MAX_HEAD),
+                ("head_residual", C.c_int32)]
 
 
 class fusion_poses(C.Structure):
@@ -172,6 +177,14 @@ def make_desc(model: dict, max_poses: int = 64, max_atoms: int = 1200, max_degre
     d.n_head = len(model["head"])
     for l, w in enumerate(model["head"]):
         d.head[l] = w
+    d.fusion = FUSION_FORMS[model.get("fusion", "coherent")]
+    d.n_cnn_out = len(model.get("cnn_out", []))
+    for l, w in enumerate(model.get("cnn_out", [])):
+        d.cnn_out[l] = w
+    d.n_sg_out = len(model.get("sg_out", []))
+    for l, w in enumerate(model.get("sg_out", [])):
+        d.sg_out[l] = w
+    d.head_residual = int(model.get("head_residual", 0))
     d.dtype = DTYPES[dtype or model["dtype"]]
     d.max_poses = max_poses
     d.max_atoms = max_atoms

@@ -17,6 +17,13 @@ earlier FAST work):
   ligand atoms.
 * Fusion head: concatenated latents through dense layers with SELU
   (Section 3.3.3, Table V); dropout is the identity at inference.
+* Fusion variants (Section 2.2): "coherent" (the head above), "mid" (Mid-level
+  Fusion: model-specific dense layers with SELU on each latent, concatenated
+  with the latents themselves, then the fusion layers) and "late" (Late Fusion:
+  the mean of the two branches' own affinity outputs, each a dense stack with
+  ReLU between layers and a linear last layer of width 1).  ``head_residual``:
+  a hidden fusion layer whose input and output widths match adds its input,
+  y = x + SELU(W x + b) (the Mid-level model's residual fusion layers, Table IV).
 """
 
 from __future__ import annotations
@@ -50,6 +57,7 @@ FUSION_TINY = dict(
     sg_gather_width=64,
     cut_cov=1.6, cut_nc=4.5,
     head=[64, 1],
+    fusion="coherent", cnn_out=[], sg_out=[], head_residual=0,
     dtype="f32",
 )
 
@@ -72,6 +80,7 @@ FUSION_FULL = dict(
     sg_gather_width=128,
     cut_cov=1.6, cut_nc=4.5,
     head=[256, 64, 1],
+    fusion="coherent", cnn_out=[], sg_out=[], head_residual=0,
     dtype="f32",
 )
 
@@ -92,6 +101,7 @@ FUSION_RAGGED = dict(
     sg_gather_width=24,
     cut_cov=1.6, cut_nc=4.5,
     head=[32, 16, 1],
+    fusion="coherent", cnn_out=[], sg_out=[], head_residual=0,
     dtype="f32",
 )
 
@@ -114,10 +124,31 @@ FUSION_PAPER = dict(
     sg_gather_width=128,
     cut_cov=2.24, cut_nc=5.22,
     head=[128, 64, 24, 1],
+    fusion="coherent", cnn_out=[], sg_out=[], head_residual=0,
     dtype="f32",
 )
 
-MODELS = {m["name"]: m for m in (FUSION_TINY, FUSION_FULL, FUSION_RAGGED, FUSION_PAPER)}
+
+def _variant(base: dict, name: str, **kw) -> dict:
+    d = copy.deepcopy(base)
+    d.update(name=name, **kw)
+    return d
+
+
+# The earlier fusion forms on the same branches: Mid-level Fusion (model-specific dense layers, their
+# outputs concatenated with the latents, residual fusion layers; Table IV has 5 fusion layers) and
+# Late Fusion (mean of the two branches' own outputs).
+FUSION_TINY_MID = _variant(FUSION_TINY, "fusion-24grid-c32-mid", fusion="mid", cnn_out=[32], sg_out=[32],
+                           head=[96, 96, 1], head_residual=1)
+FUSION_TINY_LATE = _variant(FUSION_TINY, "fusion-24grid-c32-late", fusion="late", cnn_out=[32, 1],
+                            sg_out=[32, 1], head=[])
+FUSION_FULL_MID = _variant(FUSION_FULL, "fusion-48grid-c64-mid", fusion="mid", cnn_out=[128], sg_out=[64],
+                           head=[256, 256, 128, 128, 1], head_residual=1)
+FUSION_FULL_LATE = _variant(FUSION_FULL, "fusion-48grid-c64-late", fusion="late", cnn_out=[64, 1],
+                            sg_out=[64, 1], head=[])
+
+MODELS = {m["name"]: m for m in (FUSION_TINY, FUSION_FULL, FUSION_RAGGED, FUSION_PAPER, FUSION_TINY_MID,
+                                 FUSION_TINY_LATE, FUSION_FULL_MID, FUSION_FULL_LATE)}
 
 
 def model(name: str, dtype: str | None = None) -> dict:

@@ -83,7 +83,19 @@ def layout(desc):
     else:
         L.append(("gather.w", (G, H), "bias", H))
         L.append(("gather.b", (G,), "bias", H))
+    mode = desc.get("fusion", "coherent")
+    # branch output layers: Late Fusion's own affinity stacks (ReLU between), Mid-level's dense layers (SELU)
+    for br, fin in (("cnn_out", desc["cnn_dense"]), ("sg_out", G)):
+        widths = desc.get(br, [])
+        for l, w in enumerate(widths):
+            last = l + 1 == len(widths)
+            kind = "lecun" if mode == "mid" else ("bias" if last else "kaiming")
+            L.append((f"{br}{l}.w", (w, fin), kind, fin))
+            L.append((f"{br}{l}.b", (w,), "bias", fin))
+            fin = w
     fin = desc["cnn_dense"] + G
+    if mode == "mid":
+        fin += desc["cnn_out"][-1] + desc["sg_out"][-1]
     for l, w in enumerate(desc["head"]):
         last = l + 1 == len(desc["head"])
         L.append((f"head{l}.w", (w, fin), "bias" if last else "lecun", fin))
