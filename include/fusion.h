@@ -217,6 +217,20 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
  * channels)}.  FUSION_EUNSUPPORTED on the FP32 path. */
 int fusion_describe_conv(fusion_model *m, int32_t layer, int32_t *out5);
 
+/* ---- aggregation ----
+ * The paper ranks compounds by their strongest predicted affinity over all of
+ * their docked poses at a binding site (Section 4.4: the maximum for
+ * Coherent Fusion).  Given the affinities of n poses and the compound (or
+ * compound and site) index of each pose, best[c] = max over poses i of
+ * compound c of affinity[i] and best_pose[c] = the smallest such i attaining
+ * it; a compound with no poses gets best = -INFINITY and best_pose = -1.
+ * Host arrays: affinity [n], compound [n] with values in [0, n_compounds),
+ * best [n_compounds], best_pose [n_compounds] (may be NULL).  FUSION_EINVAL
+ * on a NULL array, a compound index out of range or a NaN affinity (nothing
+ * is written then).  Runs on the host; needs no device. */
+int fusion_best_per_compound(const float *affinity, const int32_t *compound, int32_t n, int32_t n_compounds,
+                             float *best, int32_t *best_pose);
+
 /* ---- serving: continuous batching request loop ----
  * The paper scores a job's poses in fixed batches and writes every result at
  * job end, noting that results should be written as they are computed

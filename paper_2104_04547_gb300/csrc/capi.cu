@@ -1205,6 +1205,29 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
     }
 }
 
+int fusion_best_per_compound(const float *affinity, const int32_t *compound, int32_t n, int32_t n_compounds,
+                             float *best, int32_t *best_pose) {
+    if (n < 0 || n_compounds < 0) return fail(FUSION_EINVAL, "negative count");
+    if ((n > 0 && (!affinity || !compound)) || (n_compounds > 0 && !best))
+        return fail(FUSION_EINVAL, "NULL array");
+    for (int32_t i = 0; i < n; ++i) {
+        if (compound[i] < 0 || compound[i] >= n_compounds) return fail(FUSION_EINVAL, "compound index out of range");
+        if (std::isnan(affinity[i])) return fail(FUSION_EINVAL, "NaN affinity");
+    }
+    std::vector<int32_t> idx(n_compounds, -1);
+    for (int32_t c = 0; c < n_compounds; ++c) best[c] = -INFINITY;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t c = compound[i];
+        // strictly greater after the first: the first pose reaching the maximum keeps it
+        if (idx[c] < 0 || affinity[i] > best[c]) {
+            best[c] = affinity[i];
+            idx[c] = i;
+        }
+    }
+    if (best_pose) std::copy(idx.begin(), idx.end(), best_pose);
+    return FUSION_OK;
+}
+
 int fusion_describe_conv(fusion_model *m, int32_t layer, int32_t *out5) {
     if (!m || !out5 || layer < 0 || layer >= m->d.n_conv) return fail(FUSION_EINVAL, "bad arguments");
     if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "the FP32 path has no tensor-core tiles");

@@ -46,7 +46,7 @@ EXPORTED = ["fusion_weights_bytes", "fusion_create", "fusion_score", "fusion_des
             "fusion_stage_bytes", "fusion_fetch_stage", "fusion_last_timings", "fusion_cnn_dense_noalloc",
             "fusion_server_create", "fusion_server_submit", "fusion_server_poll", "fusion_server_drain",
             "fusion_server_get_stats", "fusion_server_destroy", "fusion_set_option", "fusion_autotune",
-            "fusion_describe_conv"]
+            "fusion_describe_conv", "fusion_best_per_compound"]
 
 FUSION_NOALLOC_MAX_PARTIALS = 1 << 21
 
@@ -135,6 +135,9 @@ def _load():
     lib.fusion_autotune.restype = C.c_int
     lib.fusion_describe_conv.argtypes = [C.c_void_p, C.c_int32, P(C.c_int32)]
     lib.fusion_describe_conv.restype = C.c_int
+    lib.fusion_best_per_compound.argtypes = [P(C.c_float), P(C.c_int32), C.c_int32, C.c_int32, P(C.c_float),
+                                             P(C.c_int32)]
+    lib.fusion_best_per_compound.restype = C.c_int
     return lib
 
 
@@ -247,6 +250,22 @@ def fusion_autotune(model, poses: dict, n_poses: int, on_device: bool = False) -
     keep = []
     P = _poses_struct(poses, n_poses, on_device, keep)
     _check(lib.fusion_autotune(model, C.byref(P), n_poses))
+
+
+def fusion_best_per_compound(affinity, compound, n_compounds: int):
+    """Strongest affinity of each compound over its poses and the first pose reaching it
+    (-inf and -1 for a compound without poses)."""
+    aff = np.ascontiguousarray(affinity, dtype=np.float32)
+    cmp_ = np.ascontiguousarray(compound, dtype=np.int32)
+    if aff.shape != cmp_.shape:
+        raise ValueError("affinity and compound differ in length")
+    best = np.empty(n_compounds, dtype=np.float32)
+    idx = np.empty(n_compounds, dtype=np.int32)
+    P = C.POINTER
+    _check(lib.fusion_best_per_compound(aff.ctypes.data_as(P(C.c_float)), cmp_.ctypes.data_as(P(C.c_int32)),
+                                        len(aff), n_compounds, best.ctypes.data_as(P(C.c_float)),
+                                        idx.ctypes.data_as(P(C.c_int32))))
+    return best, idx
 
 
 def fusion_describe_conv(model, layer: int) -> dict:

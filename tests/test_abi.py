@@ -6,6 +6,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from synth import configs, weights
@@ -62,3 +63,26 @@ def test_create_without_device_is_an_error_not_a_crash(F):
     with pytest.raises(F.FusionError) as e:
         F.fusion_create(F.make_desc(d, max_poses=1), blob)
     assert e.value.code in (F.FUSION_ECUDA, F.FUSION_ENOMEM)
+
+
+def test_best_per_compound_matches_numpy_groupby(F):
+    """The per-compound maximum over poses (no device needed): values and the first index reaching them."""
+    rng = np.random.default_rng(5)
+    n, nc = 500, 37
+    comp = rng.integers(0, nc - 2, n).astype(np.int32)           # compounds nc-2, nc-1 have no poses
+    aff = np.round(rng.standard_normal(n).astype(np.float32), 1)   # rounding makes ties
+    best, idx = F.fusion_best_per_compound(aff, comp, nc)
+    for c in range(nc):
+        sel = np.nonzero(comp == c)[0]
+        if len(sel) == 0:
+            assert best[c] == -np.inf and idx[c] == -1
+            continue
+        m = aff[sel].max()
+        assert best[c] == m and idx[c] == sel[np.argmax(aff[sel] == m)]
+
+
+def test_best_per_compound_rejects_bad_input(F):
+    with pytest.raises(F.FusionError):
+        F.fusion_best_per_compound(np.zeros(3, np.float32), np.array([0, 1, 5], np.int32), 3)
+    with pytest.raises(F.FusionError):
+        F.fusion_best_per_compound(np.array([0, np.nan, 1], np.float32), np.zeros(3, np.int32), 1)
