@@ -42,14 +42,20 @@
 // multiplies the FP32 accumulator by both, and records the per-pose maximum
 // |output| so the next layer's input can be quantized with its own scale.
 //
-// Roles: warp 0 lane 0 issues the TMA loads; warp 1 owns tensor memory; lane 0
-// of warps 1..NI issues the MMAs of its share of the slice groups:
-// one issuing thread was measured to limit the MMA rate, so several warps
-// issue; each commits its own MMAs and the empty barriers count NI arrivals.
-// Then every warp but the producer runs the epilogue (tensor memory ->
-// registers, bias, ReLU, residual add, bf16 NDHWC stores), two warps per
-// tensor-memory lane quarter.  Every wait is bounded; a wait that runs out sets
-// FUSION_ERR_TIMEOUT and the CTA drains and returns.
+// Persistent schedule: one CTA per multiprocessor (the tile's shared memory
+// allows one), tiles taken round robin.  Roles: warp 0 lane 0 issues the TMA
+// loads, running ahead into the next tile while the current one finishes;
+// warp 1 owns tensor memory; lane 0 of warps 1..NI issues the MMAs of its share
+// of the slice groups (one issuing thread was measured to limit the MMA rate,
+// so several warps issue; each commits its own MMAs and the empty barriers
+// count NI arrivals); warps 5..8, one per tensor-memory lane quarter, run the
+// epilogue (tensor memory -> registers, bias, ReLU, residual add, bf16 NDHWC
+// stores).  The epilogue reads a slice group's accumulator into registers,
+// zeroes it in tensor memory and hands it back on that group's barrier before
+// doing the arithmetic and stores, so the next tile's MMAs into that group
+// start while the stores of this tile are still going out.  Every wait is
+// bounded (re-armed per tile); a wait that runs out sets FUSION_ERR_TIMEOUT and
+// the CTA drains and returns.
 #include "fusion_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -92,6 +98,7 @@ struct Args {
     const float *bias;          // [N]
     __nv_bfloat16 *y;           // [B][n_out]^3[N]
     int n_in, n_out, cin, k, stride, pad, residual;
+    int B;                      // poses of this launch (tiles = per-pose tiles x B)
     // x-folded input (first layer): chunk c < 2 is read at xt_n[c] x-offsets xt_start[c] + xt_step[c] * t
     // instead of 0 .. k-1, and the input's x coordinate 0 is voxel x_shift of the stored tensor
     int xpat, xt_n[2], xt_step[2], xt_start[2], x_shift;
@@ -121,9 +128,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     constexpr uint32_t TCOLS = (T * N <= 32) ? 32 : (T * N <= 64) ? 64 : (T * N <= 128) ? 128 : (T * N <= 256) ? 256 : 512;
     // instruction descriptor without its N field (bits 17..22 = N / 8, set per MMA)
     constexpr uint32_t IDESC0 = (F8 ? tc::idesc_e4m3(128, 8) : tc::idesc_bf16(128, 8)) & ~(0x3Fu << 17);
-    constexpr int UNITS = T / G;                       // slice groups per CTA
+    constexpr int UNITS = T / G;                       // slice groups per tile
     constexpr int NI = kIssReq < UNITS ? kIssReq : UNITS;   // MMA-issuing warps, each owns UNITS / NI
     constexpr int DPI = UNITS / NI;
+    constexpr int UCOLS = G * N;                       // accumulator columns of one slice group
+    constexpr int PART = UCOLS < 128 ? UCOLS : 128;    // columns an epilogue thread holds at once
     constexpr int CPR = F8 ? 16 : 8;      // channels per 16-byte row (one core-matrix column)
     const Geo &g = a.g;
     const uint32_t a_bytes = 2 * g.plane_bytes;                     // buffer stride (128-byte aligned planes)
@@ -135,23 +144,26 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     uint64_t *a_empty = bars + 2;       // [2]
     uint64_t *b_full = bars + 4;        // [nbs]
     uint64_t *b_empty = b_full + g.nbs; // [nbs]
-    uint64_t *acc_full = b_empty + g.nbs;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_full + 1);
+    uint64_t *acc_full = b_empty + g.nbs;   // [UNITS]: the tile's MMAs of the group are complete
+    uint64_t *acc_empty = acc_full + UNITS; // [UNITS]: the epilogue has read and re-zeroed the group
+    uint64_t *mma_done = acc_empty + UNITS;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    int blk = blockIdx.x;
-    const int bx = blk % g.nbx; blk /= g.nbx;
-    const int by = blk % g.nby; blk /= g.nby;
-    const int bz = blk % g.nbz;
-    const int b = blk / g.nbz;
-    const int x0 = bx * 8, y0 = by * 16, z0 = bz * T;
-    const uint64_t deadline = tc::globaltimer() + kWaitNs;
+    const int n_tiles = g.nbx * g.nby * g.nbz * a.B;
+    auto decode = [&](int t, int &x0, int &y0, int &z0, int &b) {
+        x0 = (t % g.nbx) * 8; t /= g.nbx;
+        y0 = (t % g.nby) * 16; t /= g.nby;
+        z0 = (t % g.nbz) * T;
+        b = t / g.nbz;
+    };
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) { tc::mbar_init(&a_full[i], 1); tc::mbar_init(&a_empty[i], NI); }
         for (int i = 0; i < g.nbs; ++i) { tc::mbar_init(&b_full[i], 1); tc::mbar_init(&b_empty[i], NI); }
-        tc::mbar_init(acc_full, NI);
+        for (int u = 0; u < UNITS; ++u) { tc::mbar_init(&acc_full[u], 1); tc::mbar_init(&acc_empty[u], 4); }
+        tc::mbar_init(mma_done, NI);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -160,18 +172,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tbase = *tmem_slot;
-    // warps 1 .. kWarps-1 share the work on each tensor-memory lane quarter (warp & 3) round robin:
-    // this warp is number rq of the cq warps of its quarter
-    int cq = 0, rq = 0;
-    for (int w2 = 1; w2 < kWarps; ++w2)
-        if ((w2 & 3) == (warp & 3)) {
-            if (w2 < warp) ++rq;
-            ++cq;
-        }
-    // zero the accumulators so that every MMA accumulates
-    if (warp >= 1) {
+    // the epilogue warps 5..8 (one per tensor-memory lane quarter, warp & 3) zero the accumulators; after
+    // that each group is re-zeroed by the epilogue that reads it, so every MMA accumulates
+    if (warp >= 5) {
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-        for (uint32_t c = 32u * rq; c < TCOLS; c += 32u * cq) tc::tmem_st32_zero(tbase + lane_base + c);
+        for (uint32_t c = 0; c < TCOLS; c += 32u) tc::tmem_st32_zero(tbase + lane_base + c);
         tc::tmem_st_wait();
     }
     tc::tc_fence_before();
@@ -183,155 +188,191 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
         atomicOr(a.err, FUSION_ERR_TIMEOUT);
     };
 
+    // Tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...  Every wait's deadline is re-armed per tile.
     int prod_ai = 0, prod_bi = 0;
     if (warp == 0 && lane == 0) {
         // ---------------- producer ----------------
         int &ai = prod_ai, &bi = prod_bi;
-        const uint8_t *wc = a.w;     // weights are consumed in storage order: chunk, phase, (ty, tx) group
-        for (int c = 0; c < g.chunks && !*abort_flag; ++c) {
-            for (int ph = 0; ph < g.nphase && !*abort_flag; ++ph) {
-                int pz, py, px, nz, ny, nx;
-                phase_taps(a, ph, pz, py, px, nz, ny, nx);
-                const int buf = ai % g.na;
-                if (!tc::mbar_wait(&a_empty[buf], ((ai / g.na) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
-                tc::mbar_expect_tx(&a_full[buf], a_tx);
-                const int S = a.stride;
-                for (int j = 0; j < 2; ++j)
-                    tc::tma_load_5d(sA + buf * a_bytes + j * g.plane_bytes, &tmap, &a_full[buf], c * 2 * CPR + j * CPR,
-                                    x0 * S + px - a.pad + a.x_shift, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
-                ++ai;
-                if (a.xpat) nx = a.xt_n[c];
-                const int ngr = nz > 0 ? ny * nx : 0;   // a phase without z taps adds nothing
-                const uint32_t gbytes = (uint32_t)nz * N * 32;
-                for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
-                    const int cnt = min(g.groups_per_stage, ngr - g0);
-                    const int st = bi % g.nbs;
-                    if (!tc::mbar_wait(&b_empty[st], ((bi / g.nbs) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
-                    const uint32_t bytes = (uint32_t)cnt * gbytes;
-                    tc::mbar_expect_tx(&b_full[st], bytes);
-                    tc::bulk_load(sB + st * g.stage_bytes, wc + (size_t)g0 * gbytes, bytes, &b_full[st]);
-                    ++bi;
+        for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+            int x0, y0, z0, b;
+            decode(tile, x0, y0, z0, b);
+            const uint64_t deadline = tc::globaltimer() + kWaitNs;
+            const uint8_t *wc = a.w;     // weights are consumed in storage order: chunk, phase, (ty, tx) group
+            for (int c = 0; c < g.chunks && !*abort_flag; ++c) {
+                for (int ph = 0; ph < g.nphase && !*abort_flag; ++ph) {
+                    int pz, py, px, nz, ny, nx;
+                    phase_taps(a, ph, pz, py, px, nz, ny, nx);
+                    const int buf = ai % g.na;
+                    if (!tc::mbar_wait(&a_empty[buf], ((ai / g.na) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
+                    tc::mbar_expect_tx(&a_full[buf], a_tx);
+                    const int S = a.stride;
+                    for (int j = 0; j < 2; ++j)
+                        tc::tma_load_5d(sA + buf * a_bytes + j * g.plane_bytes, &tmap, &a_full[buf], c * 2 * CPR + j * CPR,
+                                        x0 * S + px - a.pad + a.x_shift, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
+                    ++ai;
+                    if (a.xpat) nx = a.xt_n[c];
+                    const int ngr = nz > 0 ? ny * nx : 0;   // a phase without z taps adds nothing
+                    const uint32_t gbytes = (uint32_t)nz * N * 32;
+                    for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
+                        const int cnt = min(g.groups_per_stage, ngr - g0);
+                        const int st = bi % g.nbs;
+                        if (!tc::mbar_wait(&b_empty[st], ((bi / g.nbs) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
+                        const uint32_t bytes = (uint32_t)cnt * gbytes;
+                        tc::mbar_expect_tx(&b_full[st], bytes);
+                        tc::bulk_load(sB + st * g.stage_bytes, wc + (size_t)g0 * gbytes, bytes, &b_full[st]);
+                        ++bi;
+                    }
+                    wc += (size_t)ngr * gbytes;
                 }
-                wc += (size_t)ngr * gbytes;
             }
         }
     } else if (warp >= 1 && warp <= NI && lane == 0) {
         const int d0 = (warp - 1) * DPI;
         // ---------------- MMA issuer ----------------
-        int ai = 0, bi = 0;
+        int ai = 0, bi = 0, it = 0;
         const uint32_t sbo_a = (uint32_t)g.hw * 16;
         const uint32_t row_zy = (uint32_t)g.hh * g.hw;
-        for (int c = 0; c < g.chunks && !*abort_flag; ++c) {
-            for (int ph = 0; ph < g.nphase && !*abort_flag; ++ph) {
-                int pz, py, px, nz, ny, nx;
-                phase_taps(a, ph, pz, py, px, nz, ny, nx);
-                const int buf = ai % g.na;
-                if (!tc::mbar_wait(&a_full[buf], (ai / g.na) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
-                // descriptors advance by plain integer adds: the start-address field counts 16-byte rows
-                const uint64_t adesc0 = tc::desc_kmajor(tc::smem_u32(sA + buf * a_bytes), g.plane_bytes, sbo_a);
-                const uint32_t lbo_b = (uint32_t)nz * N * 16;    // between the two 8-channel halves
-                // an x-folded chunk reads its few x-offsets at halo columns xt_start + xt_step * tx
-                int xstep = 1, xstart = 0;
-                if (a.xpat) {
-                    nx = a.xt_n[c];
-                    xstep = a.xt_step[c];
-                    xstart = a.xt_start[c];
-                }
-                const int ngr = nz > 0 ? ny * nx : 0;   // a phase without z taps adds nothing
-                for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
-                    const int gend = min(g0 + g.groups_per_stage, ngr);
-                    const int st = bi % g.nbs;
-                    if (!tc::mbar_wait(&b_full[st], (bi / g.nbs) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
-                    tc::tc_fence_after();
-                    uint64_t bgrp = tc::desc_kmajor(tc::smem_u32(sB + st * g.stage_bytes), lbo_b, 128);
-                    for (int gi = g0; gi < gend; ++gi) {
-                        const int ty = gi / nx, tx = gi - (gi / nx) * nx;
-                        const int hx = xstart + xstep * tx;
-                        const uint64_t arow = adesc0 + (uint64_t)(ty * g.hw + hx);
-                        // plane u of slice group j feeds its slices s_lo..s_hi (offset tz = u - s) in one MMA
-                        for (int u = 0; u <= nz + G - 2; ++u) {
-                            const int s_lo = u - (nz - 1) > 0 ? u - (nz - 1) : 0;
-                            const int s_hi = u < G - 1 ? u : G - 1;
-                            const uint32_t idesc = IDESC0 | ((uint32_t)((s_hi - s_lo + 1) * N) >> 3) << 17;
-                            const uint64_t bd = bgrp + (uint64_t)((nz - 1 - (u - s_lo)) * N);
-#pragma unroll
-                            for (int dd = 0; dd < DPI; ++dd) {
-                                const int j = d0 + dd;
-                                const uint64_t ad = arow + (uint64_t)((G * j + u) * row_zy);
-                                const uint32_t dt = tbase + (uint32_t)((G * j + s_lo) * N);
-                                if constexpr (F8) tc::mma_e4m3(dt, ad, bd, idesc, 1u);
-                                else tc::mma_bf16(dt, ad, bd, idesc, 1u);
-                            }
-                        }
-                        bgrp += (uint64_t)(nz * N * 2);   // next group: nz * N * 32 bytes
+        for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x, ++it) {
+            const uint64_t deadline = tc::globaltimer() + kWaitNs;
+            // this warp's slice groups must have been read (and re-zeroed) by the previous tile's epilogue
+            bool ok = true;
+            for (int dd = 0; dd < DPI && ok; ++dd)
+                ok = tc::mbar_wait(&acc_empty[d0 + dd], (it & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT);
+            if (!ok) { fail(); break; }
+            tc::tc_fence_after();
+            for (int c = 0; c < g.chunks && !*abort_flag; ++c) {
+                for (int ph = 0; ph < g.nphase && !*abort_flag; ++ph) {
+                    int pz, py, px, nz, ny, nx;
+                    phase_taps(a, ph, pz, py, px, nz, ny, nx);
+                    const int buf = ai % g.na;
+                    if (!tc::mbar_wait(&a_full[buf], (ai / g.na) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
+                    // descriptors advance by plain integer adds: the start-address field counts 16-byte rows
+                    const uint64_t adesc0 = tc::desc_kmajor(tc::smem_u32(sA + buf * a_bytes), g.plane_bytes, sbo_a);
+                    const uint32_t lbo_b = (uint32_t)nz * N * 16;    // between the two 8-channel halves
+                    // an x-folded chunk reads its few x-offsets at halo columns xt_start + xt_step * tx
+                    int xstep = 1, xstart = 0;
+                    if (a.xpat) {
+                        nx = a.xt_n[c];
+                        xstep = a.xt_step[c];
+                        xstart = a.xt_start[c];
                     }
-                    tc::mma_commit(&b_empty[st]);
-                    ++bi;
+                    const int ngr = nz > 0 ? ny * nx : 0;   // a phase without z taps adds nothing
+                    for (int g0 = 0; g0 < ngr; g0 += g.groups_per_stage) {
+                        const int gend = min(g0 + g.groups_per_stage, ngr);
+                        const int st = bi % g.nbs;
+                        if (!tc::mbar_wait(&b_full[st], (bi / g.nbs) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
+                        tc::tc_fence_after();
+                        uint64_t bgrp = tc::desc_kmajor(tc::smem_u32(sB + st * g.stage_bytes), lbo_b, 128);
+                        for (int gi = g0; gi < gend; ++gi) {
+                            const int ty = gi / nx, tx = gi - (gi / nx) * nx;
+                            const int hx = xstart + xstep * tx;
+                            const uint64_t arow = adesc0 + (uint64_t)(ty * g.hw + hx);
+                            // plane u of slice group j feeds its slices s_lo..s_hi (offset tz = u - s) in one MMA
+                            for (int u = 0; u <= nz + G - 2; ++u) {
+                                const int s_lo = u - (nz - 1) > 0 ? u - (nz - 1) : 0;
+                                const int s_hi = u < G - 1 ? u : G - 1;
+                                const uint32_t idesc = IDESC0 | ((uint32_t)((s_hi - s_lo + 1) * N) >> 3) << 17;
+                                const uint64_t bd = bgrp + (uint64_t)((nz - 1 - (u - s_lo)) * N);
+#pragma unroll
+                                for (int dd = 0; dd < DPI; ++dd) {
+                                    const int j = d0 + dd;
+                                    const uint64_t ad = arow + (uint64_t)((G * j + u) * row_zy);
+                                    const uint32_t dt = tbase + (uint32_t)((G * j + s_lo) * N);
+                                    if constexpr (F8) tc::mma_e4m3(dt, ad, bd, idesc, 1u);
+                                    else tc::mma_bf16(dt, ad, bd, idesc, 1u);
+                                }
+                            }
+                            bgrp += (uint64_t)(nz * N * 2);   // next group: nz * N * 32 bytes
+                        }
+                        tc::mma_commit(&b_empty[st]);
+                        ++bi;
+                    }
+                    tc::mma_commit(&a_empty[buf]);
+                    ++ai;
                 }
-                tc::mma_commit(&a_empty[buf]);
-                ++ai;
             }
+            for (int dd = 0; dd < DPI; ++dd) tc::mma_commit(&acc_full[d0 + dd]);
         }
-        tc::mma_commit(acc_full);
-    }
-    if (warp >= 1) {
-        // ---------------- epilogue (the MMA warps join once they have issued everything) ----------------
-        __syncwarp();
-        const int q = warp & 3;                 // tensor-memory lane quarter of this warp
+        tc::mma_commit(mma_done);
+    } else if (warp >= 5) {
+        // ---------------- epilogue: one warp per tensor-memory lane quarter ----------------
+        const int q = warp & 3;                 // lane quarter
         const int r = q * 32 + lane;            // M row = voxel of the slice
         const int h = r >> 3, w = r & 7;
-        const bool ok = tc::mbar_wait(acc_full, 0, deadline, a.err, FUSION_ERR_TIMEOUT);
-        if (!ok) fail();
-        tc::tc_fence_after();
-        if (ok && !*abort_flag) {
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x, ++it) {
+            int x0, y0, z0, b;
+            decode(tile, x0, y0, z0, b);
+            const uint64_t deadline = tc::globaltimer() + kWaitNs;
             const int yy = y0 + h, xx = x0 + w;
             const float sx = F8 ? a.s_in[b] : 1.f;
             float vmax = 0.f;
-            for (int d = rq; d < T; d += cq) {
-                const int zz = z0 + d;
-                const bool valid = zz < a.n_out && yy < a.n_out && xx < a.n_out;
-                const size_t vox = (((size_t)b * a.n_out + zz) * a.n_out + yy) * a.n_out + xx;
+            bool ok = true;
+            for (int u = 0; u < UNITS && ok; ++u) {
+                ok = tc::mbar_wait(&acc_full[u], it & 1, deadline, a.err, FUSION_ERR_TIMEOUT);
+                if (!ok) { fail(); break; }
+                tc::tc_fence_after();
 #pragma unroll 1
-                for (int cc = 0; cc < N / 32; ++cc) {
-                    uint32_t acc[32];
-                    tc::tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + d * N + cc * 32, acc);
+                for (int part = 0; part < UCOLS; part += PART) {
+                    uint32_t acc[PART / 32][32];
+#pragma unroll
+                    for (int c32 = 0; c32 < PART / 32; ++c32)
+                        tc::tmem_ld32(tbase + lane_base + (uint32_t)(u * UCOLS + part + c32 * 32), acc[c32]);
                     tc::tmem_ld_wait();
-                    if (!valid) continue;
-                    float v[32];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        float t = __uint_as_float(acc[j]);
-                        if constexpr (F8) t *= sx * a.s_w[cc * 32 + j];
-                        v[j] = fmaxf(t + a.bias[cc * 32 + j], 0.f);
+                    if (part + PART >= UCOLS) {
+                        // the whole group has been read: zero it for the next tile and hand it back
+#pragma unroll 1
+                        for (int c = 0; c < UCOLS; c += 32) tc::tmem_st32_zero(tbase + lane_base + (uint32_t)(u * UCOLS + c));
+                        tc::tmem_st_wait();
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&acc_empty[u]);
                     }
-                    if (a.residual) {
-                        const uint4 *src = reinterpret_cast<const uint4 *>(a.xres + vox * a.cres + cc * 32);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const uint4 t4 = src[u];
-                            const __nv_bfloat162 *hp = reinterpret_cast<const __nv_bfloat162 *>(&t4);
+                    for (int c32 = 0; c32 < PART / 32; ++c32) {
+                        const int col = u * UCOLS + part + c32 * 32;     // slice d = col / N, channels col % N ..
+                        const int d = col / N, cc = col % N;
+                        const int zz = z0 + d;
+                        if (zz >= a.n_out || yy >= a.n_out || xx >= a.n_out) continue;
+                        const size_t vox = (((size_t)b * a.n_out + zz) * a.n_out + yy) * a.n_out + xx;
+                        uint32_t *v = acc[c32];      // the arithmetic happens in place (float bits)
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            float t = __uint_as_float(v[j]);
+                            if constexpr (F8) t *= sx * a.s_w[cc + j];
+                            v[j] = __float_as_uint(fmaxf(t + a.bias[cc + j], 0.f));
+                        }
+                        if (a.residual) {
+                            const uint4 *src = reinterpret_cast<const uint4 *>(a.xres + vox * a.cres + cc);
+#pragma unroll
+                            for (int k4 = 0; k4 < 4; ++k4) {
+                                const uint4 t4 = src[k4];
+                                const __nv_bfloat162 *hp = reinterpret_cast<const __nv_bfloat162 *>(&t4);
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const float2 f = __bfloat1622float2(hp[e]);
+                                    v[k4 * 8 + 2 * e] = __float_as_uint(__uint_as_float(v[k4 * 8 + 2 * e]) + f.x);
+                                    v[k4 * 8 + 2 * e + 1] = __float_as_uint(__uint_as_float(v[k4 * 8 + 2 * e + 1]) + f.y);
+                                }
+                            }
+                        }
+                        uint4 *dst = reinterpret_cast<uint4 *>(a.y + vox * N + cc);
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4) {
+                            uint4 t4;
+                            __nv_bfloat162 *hp = reinterpret_cast<__nv_bfloat162 *>(&t4);
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
-                                const float2 f = __bfloat1622float2(hp[e]);
-                                v[u * 8 + 2 * e] += f.x;
-                                v[u * 8 + 2 * e + 1] += f.y;
+                                hp[e] = __floats2bfloat162_rn(__uint_as_float(v[k4 * 8 + 2 * e]),
+                                                              __uint_as_float(v[k4 * 8 + 2 * e + 1]));
+                                if constexpr (F8) {
+                                    const float2 rr = __bfloat1622float2(hp[e]);
+                                    vmax = fmaxf(vmax, fmaxf(fabsf(rr.x), fabsf(rr.y)));
+                                }
                             }
+                            dst[k4] = t4;
                         }
-                    }
-                    uint4 *dst = reinterpret_cast<uint4 *>(a.y + vox * N + cc * 32);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        uint4 t4;
-                        __nv_bfloat162 *hp = reinterpret_cast<__nv_bfloat162 *>(&t4);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            hp[e] = __floats2bfloat162_rn(v[u * 8 + 2 * e], v[u * 8 + 2 * e + 1]);
-                            if constexpr (F8) {
-                                const float2 r = __bfloat1622float2(hp[e]);
-                                vmax = fmaxf(vmax, fmaxf(fabsf(r.x), fabsf(r.y)));
-                            }
-                        }
-                        dst[u] = t4;
                     }
                 }
             }
@@ -340,11 +381,12 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                 if (lane == 0 && a.amax && vmax > 0.f)
                     atomicMax(reinterpret_cast<unsigned *>(a.amax + b), __float_as_uint(vmax));
             }
+            if (!ok) break;
         }
     }
-    // the MMA issuer's final commit covers every MMA; wait for it before freeing tensor memory
+    // every MMA must be complete before tensor memory is freed: each issuer's last commit covers its MMAs
     if (warp == 1) {
-        if (lane == 0 && !tc::mbar_wait(acc_full, 0, deadline)) fail();
+        if (lane == 0 && !tc::mbar_wait(mma_done, 0, tc::globaltimer() + kWaitNs)) fail();
         __syncwarp();
     }
     tc::tc_fence_before();
@@ -386,6 +428,7 @@ struct ConvTcPlan::Impl {
     int N = 0, T = 0;
     bool f8 = false;
     int group = 1;          // output slices per MMA
+    int sms = 1;            // multiprocessors of the device (persistent grid size)
     size_t smem = 0;
     unsigned grid = 0;
 };
@@ -627,7 +670,9 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
         return -1;
     }
     g.chunks = sp.cin_pad / chunk_ch;
-    const size_t bar_bytes = (size_t)(5 + 2 * g.nbs) * 8 + 16;
+    // a_full/a_empty [2] each, b_full/b_empty [nbs] each, acc_full/acc_empty [T / group] each, mma_done,
+    // then the tensor-memory slot and the abort flag
+    const size_t bar_bytes = (size_t)(4 + 2 * g.nbs + 2 * (T / group) + 1) * 8 + 16;
     const size_t limit = 227 * 1024;
     const size_t b_total = (size_t)g.nbs * g.stage_bytes;
     const size_t a1 = 2 * (size_t)g.plane_bytes;
@@ -686,14 +731,25 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     P.T = T;
     P.f8 = sp.elem == 1;
     P.group = group;
-    P.grid = (unsigned)(g.nbx * g.nby * g.nbz);   // per pose; times B at launch
+    P.grid = (unsigned)(g.nbx * g.nby * g.nbz);   // tiles per pose; times B at launch
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || sms <= 0) {
+        snprintf(why, why_len, "cannot read the multiprocessor count");
+        return -2;
+    }
+    P.sms = sms;
     return 0;
 }
 
 template <int N, int T, bool F8, int G>
 static void launch_t(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
     cudaFuncSetAttribute(conv3d_tc_kernel<N, T, F8, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
-    conv3d_tc_kernel<N, T, F8, G><<<P.grid * B, kThreads, P.smem, s>>>(P.tmap, P.args);
+    // persistent: one CTA per multiprocessor (one fits at this shared-memory size), tiles round robin
+    P.args.B = B;
+    const unsigned tiles = P.grid * (unsigned)B;
+    const unsigned grid = tiles < (unsigned)P.sms ? tiles : (unsigned)P.sms;
+    conv3d_tc_kernel<N, T, F8, G><<<grid, kThreads, P.smem, s>>>(P.tmap, P.args);
 }
 
 template <int N, int T, bool F8>
