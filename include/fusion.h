@@ -195,8 +195,8 @@ int fusion_last_timings(fusion_model *m, float *out, int32_t n);
 #define FUSION_OPT_CONV_SLICES_PER_MMA 2   /* tensor-core convs: value 1, 2 or 4 = every layer has each MMA
                                               serve that many adjacent output slices (N = value x output
                                               channels; FUSION_EUNSUPPORTED where a layer cannot), -1 = the
-                                              default per layer (2 for stride-1 layers where it fits, else
-                                              1).  Re-plans the layers and drops captured graphs; scores
+                                              default per layer (for stride-1 layers 4 where it fits,
+                                              else 2, else 1; 1 for stride 2).  Re-plans the layers and drops captured graphs; scores
                                               are the same in every mode */
 
 /* Set a runtime option of a model (FUSION_OPT_*). */

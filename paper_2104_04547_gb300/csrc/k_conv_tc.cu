@@ -651,14 +651,15 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     g.groups_per_stage = sp.groups_per_stage > 0 ? sp.groups_per_stage : (int)(49152 / gbytes_max);
     if (g.groups_per_stage < 1) g.groups_per_stage = 1;
     g.stage_bytes = ((uint32_t)g.groups_per_stage * gbytes_max + 127) / 128 * 128;
-    // output slices per MMA: by default 2 for stride 1 where it fits.  Measured on the 64-channel layers
-    // (64 poses, BF16): 1 slice 14.2 ms, 2 slices 10.9 ms, 4 slices 11.1 ms.  One thread issues an MMA
-    // about every 80-100 clocks, so the tensor pipe needs several issuing warps with accumulators of
-    // their own; 4 slices per MMA leave two accumulator sets (tensor memory holds 8 x 64 columns) and
-    // so two issuers.  At stride 2 each phase has only 2-3 z offsets, so a slice group shares little.
+    // output slices per MMA: by default the most (4, else 2) that fit, for stride 1.  Measured on the
+    // 64-channel layers (64 poses, BF16, persistent kernel): 2 slices 10.4-10.5 ms, 4 slices 10.1-10.3 ms per
+    // residual layer.  (Before the epilogue had warps of its own, 4 lost to 2: one thread issues an MMA
+    // about every 80-100 clocks, and 4 slices per MMA leave two accumulator sets, hence two issuers, whose
+    // warps also ran the epilogue.)  At stride 2 each phase has only 2-3 z offsets, so a slice group
+    // shares little: 1.
     auto group_ok = [&](int G) { return (G == 1 || G == 2 || G == 4) && T % G == 0 && G * c_out <= 256; };
     int group = sp.group;
-    if (group <= 0) group = (stride == 1 && group_ok(2)) ? 2 : 1;
+    if (group <= 0) group = stride != 1 ? 1 : group_ok(4) ? 4 : group_ok(2) ? 2 : 1;
     if (!group_ok(group)) {
         snprintf(why, why_len, "%d slices per MMA: must be 1, 2 or 4, divide the %d slices per CTA and span <= 256 "
                  "columns", group, T);
