@@ -199,6 +199,13 @@ int fusion_last_timings(fusion_model *m, float *out, int32_t n);
                                               else 2, else 1; 1 for stride 2).  Re-plans the layers and drops captured graphs; scores
                                               are the same in every mode */
 
+#define FUSION_OPT_TEST_WAIT_TIMEOUT 3   /* value 1: test of failure detection.  In the next fusion_score
+                                            call the first tensor-core conv launch loads nothing, so its
+                                            bounded waits run out (about 1 s): the call returns
+                                            FUSION_ETIMEOUT with the output untouched, and later calls are
+                                            normal.  Nothing faults or hangs.  FUSION_EUNSUPPORTED on the
+                                            FP32 path or with CUDA graphs on */
+
 /* Set a runtime option of a model (FUSION_OPT_*). */
 int fusion_set_option(fusion_model *m, int32_t option, int64_t value);
 

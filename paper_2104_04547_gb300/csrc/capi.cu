@@ -1185,6 +1185,13 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
     case FUSION_OPT_CUDA_GRAPH:
         m->use_graph = value != 0;
         return FUSION_OK;
+    case FUSION_OPT_TEST_WAIT_TIMEOUT: {
+        if (value != 1) return fail(FUSION_EINVAL, "the wait-timeout test takes value 1");
+        if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "the FP32 path has no bounded tensor-core waits");
+        if (m->use_graph) return fail(FUSION_EUNSUPPORTED, "turn CUDA graphs off for the wait-timeout test");
+        conv_tc_stall_next(m->tcplan[0]);
+        return FUSION_OK;
+    }
     case FUSION_OPT_CONV_SLICES_PER_MMA: {
         if (value != -1 && value != 1 && value != 2 && value != 4)
             return fail(FUSION_EINVAL, "slices per MMA must be -1 (default), 1, 2 or 4");

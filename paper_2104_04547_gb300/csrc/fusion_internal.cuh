@@ -152,6 +152,9 @@ struct ConvTcSpec {
 // Build the plan; returns 0, or nonzero with a reason in `why`.
 int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &spec, char *why, size_t why_len);
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s);
+// Test of the bounded waits: the plan's next launch issues no loads, so its waits run out (about 1 s)
+// and it sets FUSION_ERR_TIMEOUT; later launches are normal.
+void conv_tc_stall_next(ConvTcPlan &plan);
 void conv_tc_describe(const ConvTcPlan &plan, int *T, int *groups_per_stage, int *nbs, size_t *smem, int *group);
 
 // Per-pose FP8 quantization of the plain bf16 grid [B][n]^3[32] (channels 0..18) into the folded layout

@@ -99,6 +99,8 @@ struct Args {
     __nv_bfloat16 *y;           // [B][n_out]^3[N]
     int n_in, n_out, cin, k, stride, pad, residual;
     int B;                      // poses of this launch (tiles = per-pose tiles x B)
+    int stall;                  // test of the bounded waits: the producer issues nothing, so every MMA
+                                // issuer's first wait runs out and the launch reports FUSION_ERR_TIMEOUT
     // x-folded input (first layer): chunk c < 2 is read at xt_n[c] x-offsets xt_start[c] + xt_step[c] * t
     // instead of 0 .. k-1, and the input's x coordinate 0 is voxel x_shift of the stored tensor
     int xpat, xt_n[2], xt_step[2], xt_start[2], x_shift;
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     if (warp == 0 && lane == 0) {
         // ---------------- producer ----------------
         int &ai = prod_ai, &bi = prod_bi;
-        for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+        for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag && !a.stall; tile += gridDim.x) {
             int x0, y0, z0, b;
             decode(tile, x0, y0, z0, b);
             const uint64_t deadline = tc::globaltimer() + kWaitNs;
@@ -312,6 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
             for (int u = 0; u < UNITS && ok; ++u) {
                 ok = tc::mbar_wait(&acc_full[u], it & 1, deadline, a.err, FUSION_ERR_TIMEOUT);
                 if (!ok) { fail(); break; }
+                if (*abort_flag) { ok = false; break; }   // the issuers gave up: nothing valid to store
                 tc::tc_fence_after();
 #pragma unroll 1
                 for (int part = 0; part < UCOLS; part += PART) {
@@ -785,10 +788,13 @@ void conv_tc_describe(const ConvTcPlan &plan, int *T, int *groups_per_stage, int
     *group = plan.impl->group;
 }
 
+void conv_tc_stall_next(ConvTcPlan &plan) { plan.impl->args.stall = 1; }
+
 void conv_tc_launch(ConvTcPlan &plan, int B, cudaStream_t s) {
     ConvTcPlan::Impl &P = *plan.impl;
     if (P.f8) launch_n<true>(P, B, s);
     else launch_n<false>(P, B, s);
+    P.args.stall = 0;   // one launch only
 }
 
 }  // namespace fusion

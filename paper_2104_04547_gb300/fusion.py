@@ -41,6 +41,7 @@ FUSION_FORMS = {"coherent": FUSION_COHERENT, "mid": FUSION_MID, "late": FUSION_L
 
 FUSION_OPT_CUDA_GRAPH = 1
 FUSION_OPT_CONV_SLICES_PER_MMA = 2
+FUSION_OPT_TEST_WAIT_TIMEOUT = 3
 
 EXPORTED = ["fusion_weights_bytes", "fusion_create", "fusion_score", "fusion_destroy", "fusion_last_error",
             "fusion_stage_bytes", "fusion_fetch_stage", "fusion_last_timings", "fusion_cnn_dense_noalloc",

@@ -108,3 +108,25 @@ def test_atoms_outside_grid_and_single_atom_ligand(F):
         x, f, nl = poses.pose_slice(b, p)
         exp = O.score_pose(desc, W, x, f, nl)
         assert abs(float(got[p]) - exp) <= 1e-4, (p, got[p], exp)
+
+
+def test_bounded_wait_runs_out_and_model_recovers(F):
+    """Failure detection without a fault: the first conv launch of the next call is armed to load
+    nothing, so its bounded waits run out; the call returns FUSION_ETIMEOUT within a few seconds, the
+    output is untouched, and the next call gives the normal result."""
+    import time
+    desc = configs.model("fusion-20grid-ragged", dtype="bf16")
+    W = weights.init_weights(configs.model("fusion-20grid-ragged"), 3)
+    m = F.Model(desc, weights.to_blob(desc, W), max_poses=4, max_atoms=256)
+    batch = poses.pack([poses.make_pose(s, (10, 20), (40, 80)) for s in (1, 2, 3)])
+    ref = m.score(batch).copy()
+    F.fusion_set_option(m.handle, F.FUSION_OPT_TEST_WAIT_TIMEOUT, 1)
+    out = np.full(3, 7.0, dtype=np.float32)
+    t0 = time.perf_counter()
+    _expect(F, F.FUSION_ETIMEOUT, lambda: m.score(batch, out=out))
+    assert time.perf_counter() - t0 < 10.0
+    assert np.all(out == 7.0)
+    np.testing.assert_array_equal(m.score(batch), ref)
+    m.use_cuda_graphs(True)
+    _expect(F, F.FUSION_EUNSUPPORTED, lambda: F.fusion_set_option(m.handle, F.FUSION_OPT_TEST_WAIT_TIMEOUT, 1))
+    m.close()
