@@ -235,10 +235,23 @@ __global__ void __launch_bounds__(256) fold_grid_kernel(__nv_bfloat16 *grid, int
     const int nr = min(8, rows - r0);
     const int sp = 16 + 3 * p;
     for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
-        const __nv_bfloat16 *v = grid + ((size_t)r0 * n + e) * 32 + sp;
-        s_r[e * 3 + 0] = v[0];
-        s_r[e * 3 + 1] = v[1];
-        s_r[e * 3 + 2] = v[2];
+        // the voxel's channels 16..31 in two 16-byte loads (one 32-byte sector), then the 3 at slot sp
+        const uint4 *src = reinterpret_cast<const uint4 *>(grid + ((size_t)r0 * n + e) * 32 + 16);
+        const uint4 a0 = src[0], a1 = src[1];
+        const uint32_t wd[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        // select with constant indices (sp is a runtime value; a runtime index would go to local memory)
+        const int o = sp - 16;
+        unsigned short v0 = 0, v1 = 0, v2 = 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const unsigned short hv = (unsigned short)((i & 1) ? (wd[i >> 1] >> 16) : (wd[i >> 1] & 0xFFFFu));
+            if (i == o) v0 = hv;
+            if (i == o + 1) v1 = hv;
+            if (i == o + 2) v2 = hv;
+        }
+        s_r[e * 3 + 0] = __ushort_as_bfloat16(v0);
+        s_r[e * 3 + 1] = __ushort_as_bfloat16(v1);
+        s_r[e * 3 + 2] = __ushort_as_bfloat16(v2);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
