@@ -268,7 +268,8 @@ struct fusion_model {
 
     cudaEvent_t ev[18] = {};
     cudaStream_t sg_stream = nullptr;             // graph branch
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr, ev_sg[4] = {};
+    cudaStream_t cnn_stream = nullptr;            // grid branch (highest priority)
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr, cnn_join_ev = nullptr, ev_sg[4] = {};
     bool use_graph = false;                       // replay captured CUDA graphs, one per batch size
     int group_mode = -1;                          // conv output slices per MMA: -1 default per layer, or 1, 2, 4
     std::map<int, cudaGraphExec_t> graph_exec;
@@ -553,7 +554,11 @@ int alloc_workspace(fusion_model *m) {
     for (auto &e : m->ev_sg) CU(cudaEventCreate(&e));
     CU(cudaEventCreateWithFlags(&m->fork_ev, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&m->join_ev, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&m->cnn_join_ev, cudaEventDisableTiming));
     CU(cudaStreamCreateWithFlags(&m->sg_stream, cudaStreamNonBlocking));
+    int least = 0, greatest = 0;
+    CU(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CU(cudaStreamCreateWithPriority(&m->cnn_stream, cudaStreamNonBlocking, greatest));
     return FUSION_OK;
 }
 
@@ -649,9 +654,14 @@ void fusion_destroy(fusion_model *m) {
         if (e) cudaEventDestroy(e);
     if (m->fork_ev) cudaEventDestroy(m->fork_ev);
     if (m->join_ev) cudaEventDestroy(m->join_ev);
+    if (m->cnn_join_ev) cudaEventDestroy(m->cnn_join_ev);
     if (m->sg_stream) {
         cudaStreamSynchronize(m->sg_stream);
         cudaStreamDestroy(m->sg_stream);
+    }
+    if (m->cnn_stream) {
+        cudaStreamSynchronize(m->cnn_stream);
+        cudaStreamDestroy(m->cnn_stream);
     }
     for (void *p : m->allocs) cudaFree(p);
     for (void *p : m->host_allocs) cudaFreeHost(p);
@@ -733,29 +743,36 @@ static int check_launch(const char *what) {
 static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, const int32_t *off_d,
                            const int32_t *nlig_d, const float *xyz_d, const float *feat_d, bool timed, int *map) {
     const fusion_model_desc &d = m->d;
-    cudaStream_t st = m->stream;
-    CU(cudaMemsetAsync(m->err, 0, 4 * sizeof(unsigned), st));
+    cudaStream_t ms = m->stream;        // the model's (caller-visible) stream: prep, join, head
+    cudaStream_t st = m->cnn_stream;    // the grid branch, at the highest stream priority
+    CU(cudaMemsetAsync(m->err, 0, 4 * sizeof(unsigned), ms));
 
     int ei = 0;
-    auto mark = [&]() {
-        if (timed) cudaEventRecord(m->ev[ei], st);
+    auto mark = [&](cudaStream_t s) {
+        if (timed) cudaEventRecord(m->ev[ei], s);
         ++ei;
     };
-    mark();
+    mark(ms);
 
     // pose prep + voxelize
     PrepArgs pa{off_d, nlig_d, xyz_d, B, d.max_atoms, d.grid_n, d.grid_h, d.sigma, d.support,
                 m->origin, m->atom_vox, m->atom_w, m->err};
-    launch_prep(pa, st);
+    launch_prep(pa, ms);
     RC(check_launch("prep"));
-    map[0] = ei; mark();
+    map[0] = ei; mark(ms);
 
     // The graph branch (radius graph, gated graph convolution, ligand gather)
-    // is independent of the grid branch until the head: it runs on a second
-    // stream, forked here and joined before the head.
+    // is independent of the grid branch until the head: the two run on streams
+    // of their own, forked here and joined before the head.  The grid branch
+    // (the convolutions, one CTA per SM each) has the higher priority, so the
+    // graph branch's blocks take the SMs the convolutions leave free (layer
+    // tails, the small kernels) instead of holding SMs a conv CTA waits for:
+    // measured on the 64-pose batch, serializing the two branches cost 2-3%,
+    // and sharing the SMs without priorities slowed each conv layer.
     cudaStream_t sgs = m->sg_stream;
-    CU(cudaEventRecord(m->fork_ev, st));
+    CU(cudaEventRecord(m->fork_ev, ms));
     CU(cudaStreamWaitEvent(sgs, m->fork_ev, 0));
+    CU(cudaStreamWaitEvent(st, m->fork_ev, 0));
     auto sg_mark = [&](int k) {
         if (timed) cudaEventRecord(m->ev_sg[k], sgs);
     };
@@ -831,7 +848,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
                m->bf16 ? 1 : 0, m->grid_fold};
     launch_voxelize(va, st);
     RC(check_launch("voxelize"));
-    map[1] = ei; mark();
+    map[1] = ei; mark(st);
 
     // 3D-CNN
     const void *x = m->grid;
@@ -862,7 +879,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
         RC(check_launch("conv3d"));
         m->last_conv_out[i] = m->act[i];
         x = m->act[i];
-        map[2 + i] = ei; mark();
+        map[2 + i] = ei; mark(st);
     }
     const void *flat_in = x;
     if (d.pool > 1) {
@@ -871,7 +888,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
         launch_maxpool(po, st);
         RC(check_launch("maxpool"));
         flat_in = m->pool_out;
-        map[10] = ei; mark();
+        map[10] = ei; mark(st);
     }
     DenseArgs da{flat_in, m->dense_w, m->dense_b, m->dense_part, m->cnn_lat, B, d.cnn_dense, m->flat, m->splits,
                  m->bf16 ? 1 : 0, 1};
@@ -884,12 +901,14 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
         launch_dense(da, st);
     }
     RC(check_launch("dense"));
-    map[11] = ei; mark();
+    map[11] = ei; mark(st);
 
-    // join the graph branch
-    CU(cudaEventRecord(m->join_ev, m->sg_stream));
-    CU(cudaStreamWaitEvent(st, m->join_ev, 0));
-    mark();
+    // join both branches
+    CU(cudaEventRecord(m->cnn_join_ev, st));
+    CU(cudaStreamWaitEvent(ms, m->cnn_join_ev, 0));
+    CU(cudaEventRecord(m->join_ev, sgs));
+    CU(cudaStreamWaitEvent(ms, m->join_ev, 0));
+    mark(ms);
 
     HeadArgs ha{};
     ha.cnn = m->cnn_lat;
@@ -916,9 +935,9 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     ha.Dc = d.cnn_dense;
     ha.G = d.sg_gather_width;
     ha.out = m->aff;
-    launch_head(ha, st);
+    launch_head(ha, ms);
     RC(check_launch("head"));
-    map[15] = ei; mark();
+    map[15] = ei; mark(ms);
     return FUSION_OK;
 }
 
