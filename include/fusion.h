@@ -33,7 +33,7 @@ extern "C" {
 #define FUSION_ECAPACITY    -4  /* a device capacity flag was raised (edge capacity of a pose exceeded) */
 #define FUSION_ECUDA        -5  /* a CUDA runtime call failed */
 #define FUSION_ETIMEOUT     -6  /* a bounded device wait ran out */
-#define FUSION_EUNSUPPORTED -7  /* descriptor valid but not supported by this build (dtype or shape) */
+#define FUSION_EUNSUPPORTED -7  /* descriptor valid but not supported by this library (dtype or shape) */
 #define FUSION_EAGAIN       -8  /* server: queue full, or the result is not ready yet */
 
 /* Compute dtypes of the CNN contractions (density, distances, pooling and head stay FP32). */
