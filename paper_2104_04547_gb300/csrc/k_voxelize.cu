@@ -145,6 +145,8 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
     const int vx = t0x + (tid & 7);
     const int vy = t0y + ((tid >> 3) & 7);
     const int vz = t0z + (tid >> 6);
+    const int wz = vz;                                  // this warp's z-slice and y-rows
+    const int wy0 = t0y + ((tid >> 3) & 4), wy1 = wy0 + 3;
     float acc[kFeat];
 #pragma unroll
     for (int c = 0; c < kFeat; ++c) acc[c] = 0.f;
@@ -161,17 +163,32 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
             s_f[e] = a.feat[(size_t)(a0 + s_list[r + s]) * kFeat + q];
         }
         __syncthreads();
-        for (int s = 0; s < nr; ++s) {
-            const int4 v = s_v[s];
-            const unsigned dz = (unsigned)(vz - (v.x - K));
-            const unsigned dy = (unsigned)(vy - (v.y - K));
-            const unsigned dx = (unsigned)(vx - (v.z - K));
-            if (dz < (unsigned)KW && dy < (unsigned)KW && dx < (unsigned)KW) {
-                const float *w = s_w + s * 3 * KW;
-                const float wv = (w[dz] * w[KW + dy]) * w[2 * KW + dx];
-                const float *f = s_f + s * kFeat;
+        // A warp covers one z-slice, 4 y-rows and the 8 x-columns of the tile: 32 staged atoms at a time,
+        // each lane tests one against that box and the warp then visits only the atoms that can reach it,
+        // in ascending order (so every voxel still sums its atoms in atom-index order).
+        for (int base = 0; base < nr; base += 32) {
+            const int sl = base + lane;
+            bool rel = false;
+            if (sl < nr) {
+                const int4 v = s_v[sl];
+                rel = v.x - K <= wz && v.x + K >= wz && v.y - K <= wy1 && v.y + K >= wy0 && v.z - K <= t0x + 7 &&
+                      v.z + K >= t0x;
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, rel);
+            while (todo) {
+                const int s = base + __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int4 v = s_v[s];
+                const unsigned dz = (unsigned)(vz - (v.x - K));
+                const unsigned dy = (unsigned)(vy - (v.y - K));
+                const unsigned dx = (unsigned)(vx - (v.z - K));
+                if (dz < (unsigned)KW && dy < (unsigned)KW && dx < (unsigned)KW) {
+                    const float *w = s_w + s * 3 * KW;
+                    const float wv = (w[dz] * w[KW + dy]) * w[2 * KW + dx];
+                    const float *f = s_f + s * kFeat;
 #pragma unroll
-                for (int c = 0; c < kFeat; ++c) acc[c] = fmaf(wv, f[c], acc[c]);
+                    for (int c = 0; c < kFeat; ++c) acc[c] = fmaf(wv, f[c], acc[c]);
+                }
             }
         }
         __syncthreads();
