@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a) {
 
 constexpr int kTile = 8;
 constexpr int kStage = 256;
+constexpr int kFeatPad = 20;   // staged features per atom: 19 + 1 zero, so a thread reads them as 5 float4
 
 template <bool BF16, int CX>
 __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
@@ -103,8 +104,8 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
 
     int4 *s_v = reinterpret_cast<int4 *>(smem);                  // [kStage]
     float *s_w = reinterpret_cast<float *>(s_v + kStage);        // [kStage][3*KW]
-    float *s_f = s_w + kStage * 3 * KW;                          // [kStage][19]
-    int *s_list = reinterpret_cast<int *>(s_f + kStage * kFeat); // [max_atoms]
+    float *s_f = s_w + kStage * 3 * KW;                          // [kStage][20], 16-byte aligned rows
+    int *s_list = reinterpret_cast<int *>(s_f + kStage * kFeatPad); // [max_atoms]
     __shared__ int s_wsum[16];
     __shared__ int s_total;
 
@@ -158,9 +159,9 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
             const int s = e / (3 * KW), q = e - s * 3 * KW;
             s_w[e] = a.atom_w[(size_t)(a0 + s_list[r + s]) * 3 * KW + q];
         }
-        for (int e = tid; e < nr * kFeat; e += 512) {
-            const int s = e / kFeat, q = e - s * kFeat;
-            s_f[e] = a.feat[(size_t)(a0 + s_list[r + s]) * kFeat + q];
+        for (int e = tid; e < nr * kFeatPad; e += 512) {
+            const int s = e / kFeatPad, q = e - s * kFeatPad;
+            s_f[e] = q < kFeat ? a.feat[(size_t)(a0 + s_list[r + s]) * kFeat + q] : 0.f;
         }
         __syncthreads();
         // A warp covers one z-slice, 4 y-rows and the 8 x-columns of the tile: 32 staged atoms at a time,
@@ -185,9 +186,15 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
                 if (dz < (unsigned)KW && dy < (unsigned)KW && dx < (unsigned)KW) {
                     const float *w = s_w + s * 3 * KW;
                     const float wv = (w[dz] * w[KW + dy]) * w[2 * KW + dx];
-                    const float *f = s_f + s * kFeat;
+                    const float4 *f4 = reinterpret_cast<const float4 *>(s_f + s * kFeatPad);
 #pragma unroll
-                    for (int c = 0; c < kFeat; ++c) acc[c] = fmaf(wv, f[c], acc[c]);
+                    for (int c4 = 0; c4 < kFeatPad / 4; ++c4) {
+                        const float4 f = f4[c4];
+                        acc[4 * c4] = fmaf(wv, f.x, acc[4 * c4]);
+                        acc[4 * c4 + 1] = fmaf(wv, f.y, acc[4 * c4 + 1]);
+                        acc[4 * c4 + 2] = fmaf(wv, f.z, acc[4 * c4 + 2]);
+                        if (4 * c4 + 3 < kFeat) acc[4 * c4 + 3] = fmaf(wv, f.w, acc[4 * c4 + 3]);
+                    }
                 }
             }
         }
@@ -290,7 +297,7 @@ __global__ void __launch_bounds__(256) fold_grid_kernel(__nv_bfloat16 *grid, int
 
 size_t vox_smem(int k, int max_atoms) {
     const int KW = 2 * k + 1;
-    return (size_t)kStage * sizeof(int4) + (size_t)kStage * 3 * KW * 4 + (size_t)kStage * kFeat * 4 +
+    return (size_t)kStage * sizeof(int4) + (size_t)kStage * 3 * KW * 4 + (size_t)kStage * kFeatPad * 4 +
            (size_t)max_atoms * 4;
 }
 
