@@ -1,5 +1,6 @@
-// BF16 3D convolution on the tcgen05 tensor cores (Section 3.3.1, Table III:
-// the convolutions of the 3D-CNN are the one dense contraction of the path).
+// BF16 and FP8 3D convolution on the tcgen05 tensor cores (Section 3.3.1,
+// Table III: the convolutions of the 3D-CNN are the one dense contraction of
+// the path).
 //
 // Implicit GEMM: M = output voxels, N = output channels, K = input channels x
 // kernel offsets.  A CTA owns T output slices of 16 x 8 voxels (T M-tiles of
@@ -36,6 +37,14 @@
 // accumulates; slice d sits at columns [dN, dN + N) whatever G is, so the
 // epilogue does not depend on it, and every output element receives its terms
 // in the same order for every G (offset groups in (ty, tx) order, tz ascending).
+//
+// Folded first-layer input: the grid's 19 channels fill neither two 16-channel
+// chunks (BF16) nor one 32-channel chunk (FP8) well, so the first layer reads a
+// grid whose chunks hold some channels at several x positions (the BF16 grid's
+// second chunk: channels 16..18 of voxels x-p .. x-p+4; the FP8 grid: channels
+// 0..15 of voxels x-1 and x, then 16..18 of voxels x-p .. x+p).  Such a chunk
+// is read at a few x-offsets (xt_start + xt_step * t) instead of k, with
+// weights arranged to match (conv_tc_arrange_weights, fold modes 1 and 2).
 //
 // FP8 variant (E4M3 inputs, kind::f8f6f4, 32 channels per MMA): weights carry a
 // per-output-channel scale and activations a per-pose scale; the epilogue
