@@ -564,6 +564,30 @@ int alloc_workspace(fusion_model *m) {
 
 }  // namespace
 
+// FP8 inputs of the stride-1 layers are stored channel-blocked (whole W-lines per TMA box row); the
+// stride-2 layers read NDHWC, since their halos step through x by 2.
+static bool fp8_blocked(const fusion_model *m, int i) { return m->fp8 && m->d.conv[i].stride == 1; }
+
+// BF16 model: layer i reads its input in place, channel-blocked when it is a stride-1 layer and that
+// input is a conv output (the previous layer then stores it so) or the folded grid.
+static bool bf16_blocked_in(const fusion_model *m, int i) {
+    return m->bf16 && !m->fp8 && i < m->d.n_conv && m->d.conv[i].stride == 1 && (i > 0 || m->grid_fold >= 0);
+}
+// Layout of conv layer l's bf16 output.
+static bool conv_out_blocked(const fusion_model *m, int l) { return bf16_blocked_in(m, l + 1); }
+
+// FP8: quantize layer i's bf16 input xb per pose into m->qbuf, in the layout its conv plan reads.
+static void quantize_conv_input(fusion_model *m, int i, const void *xb, int B, cudaStream_t st) {
+    const fusion_model_desc &d = m->d;
+    const Shape si = conv_out(d, i);
+    if (i == 0 && m->fp8_fold >= 0)
+        launch_quantize_fold_fp8(xb, m->qbuf, B, d.grid_n, m->fp8_fold, m->amax, m->qscale, fp8_blocked(m, i) ? 1 : 0, st);
+    else if (fp8_blocked(m, i))
+        launch_quantize_blocked(xb, m->qbuf, B, si.n, m->conv[i].cx_in, m->amax, m->qscale, st);
+    else
+        launch_quantize_per_pose(xb, m->qbuf, B, (size_t)si.n * si.n * si.n * m->conv[i].cx_in, m->amax, m->qscale, st);
+}
+
 static ConvTcSpec conv_spec(fusion_model *m, int i) {
     const fusion_model_desc &d = m->d;
     const fusion_conv_desc &c = d.conv[i];
@@ -591,6 +615,9 @@ static ConvTcSpec conv_spec(fusion_model *m, int i) {
     sp.group = m->group_mode;
     sp.fold = i != 0 ? 0 : m->grid_fold >= 0 ? 1 : m->fp8_fold >= 0 ? 2 : 0;
     if (sp.fold == 2) sp.cin_pad = 64;
+    sp.blocked = (fp8_blocked(m, i) || bf16_blocked_in(m, i)) ? 1 : 0;
+    sp.out_blocked = conv_out_blocked(m, i) ? 1 : 0;
+    sp.res_blocked = bf16_blocked_in(m, i) ? 1 : 0;   // BF16: the residual source is the input itself
     return sp;
 }
 
@@ -845,7 +872,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     RC(check_launch("sg_gather"));
     sg_mark(3);
     VoxArgs va{off_d, feat_d, m->atom_vox, m->atom_w, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx,
-               m->bf16 ? 1 : 0, m->grid_fold};
+               m->bf16 ? 1 : 0, m->grid_fold, bf16_blocked_in(m, 0) ? 1 : 0};
     launch_voxelize(va, st);
     RC(check_launch("voxelize"));
     map[1] = ei; mark(st);
@@ -862,10 +889,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
                 CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
                 launch_amax_per_pose(m->grid, B, per_pose, m->amax, st);
             }
-            if (i == 0 && m->fp8_fold >= 0)
-                launch_quantize_fold_fp8(m->grid, m->qbuf, B, d.grid_n, m->fp8_fold, m->amax, m->qscale, st);
-            else
-                launch_quantize_per_pose(x, m->qbuf, B, per_pose, m->amax, m->qscale, st);
+            quantize_conv_input(m, i, x, B, st);
             CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
             conv_tc_launch(m->tcplan[i], B, st);
         } else if (m->bf16) {
@@ -1091,6 +1115,17 @@ static int copy_as_f32(fusion_model *m, const void *src, size_t elem_off, size_t
     return FUSION_OK;
 }
 
+// One pose's channel-blocked map [n][n][C / 8][n][8] in NDHWC order [n][n][n][C].
+static std::vector<float> unblock(const std::vector<float> &t, int n, int C) {
+    std::vector<float> o(t.size());
+    for (size_t row = 0; row < (size_t)n * n; ++row)
+        for (int cb = 0; cb < C / 8; ++cb)
+            for (int x = 0; x < n; ++x)
+                for (int c = 0; c < 8; ++c)
+                    o[(row * n + x) * C + cb * 8 + c] = t[((row * (C / 8) + cb) * n + x) * 8 + c];
+    return o;
+}
+
 int64_t fusion_stage_bytes(fusion_model *m, int32_t stage, int32_t index) {
     if (!m || m->last_B == 0) return fail(FUSION_EINVAL, "no scoring call to fetch from");
     const fusion_model_desc &d = m->d;
@@ -1141,6 +1176,7 @@ int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst,
         const size_t n3 = (size_t)d.grid_n * d.grid_n * d.grid_n;
         std::vector<float> t;
         RC(copy_as_f32(m, m->grid, (size_t)p * n3 * m->grid_cx, n3 * m->grid_cx, t));
+        if (bf16_blocked_in(m, 0)) t = unblock(t, d.grid_n, m->grid_cx);
         float *o = static_cast<float *>(dst);
         // a folded grid holds feature 16 + f of voxel x in slot 16 + 3 p + f of the same voxel
         for (size_t v = 0; v < n3; ++v)
@@ -1153,6 +1189,7 @@ int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst,
         if (!d.keep_stages && l != d.n_conv - 1) return fail(FUSION_EINVAL, "conv stages need keep_stages");
         std::vector<float> t;
         RC(copy_as_f32(m, m->last_conv_out[l], (size_t)p * (need / 4), need / 4, t));
+        if (conv_out_blocked(m, l)) t = unblock(t, conv_out(d, l + 1).n, conv_out(d, l + 1).c);
         std::memcpy(dst, t.data(), need);
         return FUSION_OK;
     }
@@ -1296,10 +1333,7 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
             const void *xb = (i == 0) ? m->grid : m->act[i - 1];
             cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st);
             launch_amax_per_pose(xb, B, per_pose, m->amax, st);
-            if (i == 0 && m->fp8_fold >= 0)
-                launch_quantize_fold_fp8(xb, m->qbuf, B, d.grid_n, m->fp8_fold, m->amax, m->qscale, st);
-            else
-                launch_quantize_per_pose(xb, m->qbuf, B, per_pose, m->amax, m->qscale, st);
+            quantize_conv_input(m, i, xb, B, st);
         };
         for (int T : Ts)
             for (int group : {4, 2, 1})

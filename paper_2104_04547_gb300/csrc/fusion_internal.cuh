@@ -55,6 +55,7 @@ struct VoxArgs {
     int fold_pad;         // bf16 only: -1 = plain channels; p >= 0 = channels 16..18 folded along x:
                           // channel 16 + 3 s + f of voxel x holds feature 16 + f of voxel x - p + s
                           // (s = 0..4, zero outside the grid), channel 31 zero
+    int blocked;          // bf16 only: store channel-blocked, [B][n][n][cx / 8][n][8]
 };
 void launch_voxelize(const VoxArgs &a, cudaStream_t s);
 
@@ -148,6 +149,11 @@ struct ConvTcSpec {
     int group;              // output slices per MMA (1, 2, 4; N = group x c_out); <= 0: default for the layer
     int fold;               // x-folded first-layer input: 0 no, 1 bf16 grid (VoxArgs::fold_pad = k / 2),
                             // 2 FP8 grid of launch_quantize_fold_fp8 (cin_pad 64, stored from x = -1)
+    int blocked;            // input stored channel-blocked, [pose][z][y][16-byte channel block][x][16 bytes],
+                            // so a halo row is hw x 16 contiguous bytes (one TMA box row per 16-byte block and
+                            // W-line instead of one per voxel); stride 1 only
+    int out_blocked;        // write the bf16 output channel-blocked, [pose][z][y][c_out / 8][x][8]
+    int res_blocked;        // the bf16 residual source is channel-blocked, [pose][z][y][cres / 8][x][8]
 };
 // Build the plan; returns 0, or nonzero with a reason in `why`.
 int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &spec, char *why, size_t why_len);
@@ -161,12 +167,17 @@ void conv_tc_describe(const ConvTcPlan &plan, int *T, int *groups_per_stage, int
 // the first FP8 conv reads, [B][n][n][n + 1][64]: stored voxel j holds channels 0..15 of grid voxels
 // j - 1 and j (slots 0..31), and channels 16..18 of voxels j - 1 - p + s, s = 0 .. 2p (slots 32 + 3 s + f),
 // zero outside the grid and in the unused slots; codes use the per-pose scale of launch_quantize_per_pose.
+// blocked != 0: the same codes stored channel-blocked, [B][n][n][4][n + 1][16] (see ConvTcSpec::blocked).
 void launch_quantize_fold_fp8(const void *grid_bf16, void *q_fp8, int B, int n, int p, const float *amax,
-                              float *scale, cudaStream_t s);
+                              float *scale, int blocked, cudaStream_t s);
 // Per-pose FP8 quantization of bf16 NDHWC activations (per_pose elements per pose, a multiple of 8).
 void launch_amax_per_pose(const void *x_bf16, int B, size_t per_pose, float *amax, cudaStream_t s);
 void launch_quantize_per_pose(const void *x_bf16, void *q_fp8, int B, size_t per_pose, const float *amax, float *scale,
                               cudaStream_t s);
+// The same codes for bf16 NDHWC activations [B][n]^3[C] (C a multiple of 16), stored channel-blocked:
+// [B][n][n][C / 16][n][16] (z, y, 16-channel block, x, channel in block).
+void launch_quantize_blocked(const void *x_bf16, void *q_fp8, int B, int n, int C, const float *amax, float *scale,
+                             cudaStream_t s);
 
 // ---- radius graph ----------------------------------------------------------
 

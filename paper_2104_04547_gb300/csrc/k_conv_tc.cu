@@ -18,6 +18,15 @@
 // 8 channels, 16 bytes per row, W-lines at a stride of the halo width).  So
 // each input element is fetched once per chunk, not once per offset.
 //
+// Channel-blocked inputs ([pose][z][y][16-byte channel block][x][16 bytes],
+// written so by the previous layer or the quantizer for stride-1 layers): the
+// chunk's two blocks then come in one TMA box whose rows are whole halo
+// W-lines (hw x 16 bytes) instead of single voxels (16 bytes).  A TMA load
+// costs about a clock per box row, so a 138 KB halo takes 1.7-2.2 us instead
+// of 4.7-4.9 us (measured on all SMs at once), and the tensor pipe waits that
+// much less at each chunk.  The halo buffer is then [z][y][K half][x][16 bytes]:
+// the descriptor's K-half offset is hw x 16 bytes and its W-line stride 2 hw x 16.
+//
 // Operand B (the weights) streams through a ring of shared-memory stages with
 // plain bulk copies.  The host arranges them per in-plane offset (ty, tx) as a
 // group [8-channel half][tz = nz-1, .., 1, 0][co][16 bytes], so that the rows
@@ -57,12 +66,16 @@
 // warp 1 owns tensor memory; lane 0 of warps 1..NI issues the MMAs of its share
 // of the slice groups (one issuing thread was measured to limit the MMA rate,
 // so several warps issue; each commits its own MMAs and the empty barriers
-// count NI arrivals); warps 5..8, one per tensor-memory lane quarter, run the
-// epilogue (tensor memory -> registers, bias, ReLU, residual add, bf16 NDHWC
-// stores).  The epilogue reads a slice group's accumulator into registers,
-// zeroes it in tensor memory and hands it back on that group's barrier before
-// doing the arithmetic and stores, so the next tile's MMAs into that group
-// start while the stores of this tile are still going out.  Every wait is
+// count NI arrivals); the remaining 4 x EPW warps run the epilogue (tensor
+// memory -> registers, bias, ReLU, residual add, bf16 NDHWC stores), EPW per
+// tensor-memory lane quarter (a warp reaches only the lanes of quarter
+// warp % 4), each holding up to 128 columns of a slice group: two per quarter
+// when a group spans 256 columns, so a group is read in one pass.  Each
+// epilogue warp reads its columns, zeroes them in tensor memory and hands them
+// back on the group's barrier before any arithmetic, so the next tile's MMAs
+// into the group wait only for the reads, not for the residual loads and the
+// stores.  At the start of a tile the epilogue warps ask L2 for the residual
+// input lines they will add, while the tile's MMAs run.  Every wait is
 // bounded (re-armed per tile); a wait that runs out sets FUSION_ERR_TIMEOUT and
 // the CTA drains and returns.
 #include "fusion_internal.cuh"
@@ -80,8 +93,19 @@ namespace fusion {
 namespace {
 
 constexpr int kIssReq = 4;
-constexpr int kWarps = 1 + kIssReq + 4;
-constexpr int kThreads = 32 * kWarps;
+
+// Warp roles of one kernel instance: warp 0 loads, warps 1..NI issue MMAs, then 4 x EPW epilogue warps
+// (EPW per tensor-memory lane quarter, each holding PART columns of a slice group).
+template <int N, int T, int G>
+struct Roles {
+    static constexpr int UNITS = T / G;                          // slice groups per tile
+    static constexpr int NI = kIssReq < UNITS ? kIssReq : UNITS;  // MMA-issuing warps, each owns UNITS / NI
+    static constexpr int UCOLS = G * N;                          // accumulator columns of one slice group
+    static constexpr int EPW = UCOLS > 128 ? UCOLS / 128 : 1;
+    static constexpr int PART = UCOLS / EPW;
+    static constexpr int EPI0 = 1 + NI;                           // first epilogue warp
+    static constexpr int THREADS = 32 * (EPI0 + 4 * EPW);
+};
 constexpr uint64_t kWaitNs = 1000000000ull;    // 1 s
 
 struct Geo {
@@ -89,7 +113,10 @@ struct Geo {
     int nphase;            // 1 or 8
     int ntap[2];           // taps per dim for parity 0 / 1 (stride 2), or k (stride 1)
     int hd, hh, hw;        // halo extents
-    uint32_t plane_bytes;  // one 8-channel plane of the halo, 128-byte aligned
+    uint32_t plane_bytes;  // one 8-channel plane of the halo, 128-byte aligned (plain input)
+    uint32_t a_bytes;      // one halo buffer (both K halves), 128-byte aligned
+    uint32_t lbo_a;        // bytes between the two K halves of a voxel row in the buffer
+    int ystep;             // 16-byte rows between consecutive y rows of the buffer
     uint32_t stage_bytes;  // one B stage
     int groups_per_stage;  // (ty, tx) offset groups per B stage
     int nbs;               // B stages
@@ -113,6 +140,9 @@ struct Args {
     // x-folded input (first layer): chunk c < 2 is read at xt_n[c] x-offsets xt_start[c] + xt_step[c] * t
     // instead of 0 .. k-1, and the input's x coordinate 0 is voxel x_shift of the stored tensor
     int xpat, xt_n[2], xt_step[2], xt_start[2], x_shift;
+    int blocked;                // input stored channel-blocked (ConvTcSpec::blocked): one TMA box per chunk
+    int out_blocked;            // write y channel-blocked: [pose][z][y][N / 8][x][8]
+    int res_blocked;            // xres is channel-blocked: [pose][z][y][cres / 8][x][8]
     Geo g;
     unsigned *err;
 };
@@ -133,20 +163,18 @@ __device__ __forceinline__ void phase_taps(const Args &a, int ph, int &pz, int &
 }
 
 template <int N, int T, bool F8, int G>
-__global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_constant__ CUtensorMap tmap, Args a) {
+__global__ void __launch_bounds__(Roles<N, T, G>::THREADS, 1) conv3d_tc_kernel(const __grid_constant__ CUtensorMap tmap, Args a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     static_assert(T % G == 0 && G * N <= 256, "a slice group divides T and spans at most 256 columns");
     constexpr uint32_t TCOLS = (T * N <= 32) ? 32 : (T * N <= 64) ? 64 : (T * N <= 128) ? 128 : (T * N <= 256) ? 256 : 512;
     // instruction descriptor without its N field (bits 17..22 = N / 8, set per MMA)
     constexpr uint32_t IDESC0 = (F8 ? tc::idesc_e4m3(128, 8) : tc::idesc_bf16(128, 8)) & ~(0x3Fu << 17);
-    constexpr int UNITS = T / G;                       // slice groups per tile
-    constexpr int NI = kIssReq < UNITS ? kIssReq : UNITS;   // MMA-issuing warps, each owns UNITS / NI
+    using R = Roles<N, T, G>;
+    constexpr int UNITS = R::UNITS, NI = R::NI, UCOLS = R::UCOLS, EPW = R::EPW, PART = R::PART, EPI0 = R::EPI0;
     constexpr int DPI = UNITS / NI;
-    constexpr int UCOLS = G * N;                       // accumulator columns of one slice group
-    constexpr int PART = UCOLS < 128 ? UCOLS : 128;    // columns an epilogue thread holds at once
     constexpr int CPR = F8 ? 16 : 8;      // channels per 16-byte row (one core-matrix column)
     const Geo &g = a.g;
-    const uint32_t a_bytes = 2 * g.plane_bytes;                     // buffer stride (128-byte aligned planes)
+    const uint32_t a_bytes = g.a_bytes;                             // buffer stride
     const uint32_t a_tx = 2u * (uint32_t)(g.hd * g.hh * g.hw) * 16u;  // bytes the two TMA loads deliver
     unsigned char *sA = smem;
     unsigned char *sB = smem + g.na * a_bytes;
@@ -173,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) { tc::mbar_init(&a_full[i], 1); tc::mbar_init(&a_empty[i], NI); }
         for (int i = 0; i < g.nbs; ++i) { tc::mbar_init(&b_full[i], 1); tc::mbar_init(&b_empty[i], NI); }
-        for (int u = 0; u < UNITS; ++u) { tc::mbar_init(&acc_full[u], 1); tc::mbar_init(&acc_empty[u], 4); }
+        for (int u = 0; u < UNITS; ++u) { tc::mbar_init(&acc_full[u], 1); tc::mbar_init(&acc_empty[u], 4 * EPW); }
         tc::mbar_init(mma_done, NI);
         *abort_flag = 0;
         tc::fence_mbar_init();
@@ -183,9 +211,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tbase = *tmem_slot;
-    // the epilogue warps 5..8 (one per tensor-memory lane quarter, warp & 3) zero the accumulators; after
+    // the first four epilogue warps (one per tensor-memory lane quarter, warp & 3) zero the accumulators; after
     // that each group is re-zeroed by the epilogue that reads it, so every MMA accumulates
-    if (warp >= 5) {
+    if (warp >= EPI0 && warp < EPI0 + 4) {
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         for (uint32_t c = 0; c < TCOLS; c += 32u) tc::tmem_st32_zero(tbase + lane_base + c);
         tc::tmem_st_wait();
@@ -217,9 +245,16 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                     if (!tc::mbar_wait(&a_empty[buf], ((ai / g.na) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
                     tc::mbar_expect_tx(&a_full[buf], a_tx);
                     const int S = a.stride;
-                    for (int j = 0; j < 2; ++j)
-                        tc::tma_load_5d(sA + buf * a_bytes + j * g.plane_bytes, &tmap, &a_full[buf], c * 2 * CPR + j * CPR,
-                                        x0 * S + px - a.pad + a.x_shift, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
+                    if (a.blocked) {
+                        // buffer [z][y][K half][x][16 bytes]: the chunk's two 16-byte channel blocks in one box
+                        tc::tma_load_5d(sA + buf * a_bytes, &tmap, &a_full[buf], (x0 - a.pad + a.x_shift) * CPR, 2 * c,
+                                        y0 - a.pad, z0 - a.pad, b);
+                    } else {
+                        // buffer [K half][z][y][x][16 bytes]: one box per 16-byte channel block
+                        for (int j = 0; j < 2; ++j)
+                            tc::tma_load_5d(sA + buf * a_bytes + j * g.plane_bytes, &tmap, &a_full[buf], c * 2 * CPR + j * CPR,
+                                            x0 * S + px - a.pad + a.x_shift, y0 * S + py - a.pad, z0 * S + pz - a.pad, b);
+                    }
                     ++ai;
                     if (a.xpat) nx = a.xt_n[c];
                     const int ngr = nz > 0 ? ny * nx : 0;   // a phase without z taps adds nothing
@@ -241,8 +276,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
         const int d0 = (warp - 1) * DPI;
         // ---------------- MMA issuer ----------------
         int ai = 0, bi = 0, it = 0;
-        const uint32_t sbo_a = (uint32_t)g.hw * 16;
-        const uint32_t row_zy = (uint32_t)g.hh * g.hw;
+        const uint32_t sbo_a = (uint32_t)g.ystep * 16;
+        const uint32_t row_zy = (uint32_t)g.hh * g.ystep;
         for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x, ++it) {
             const uint64_t deadline = tc::globaltimer() + kWaitNs;
             // this warp's slice groups must have been read (and re-zeroed) by the previous tile's epilogue
@@ -258,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                     const int buf = ai % g.na;
                     if (!tc::mbar_wait(&a_full[buf], (ai / g.na) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
                     // descriptors advance by plain integer adds: the start-address field counts 16-byte rows
-                    const uint64_t adesc0 = tc::desc_kmajor(tc::smem_u32(sA + buf * a_bytes), g.plane_bytes, sbo_a);
+                    const uint64_t adesc0 = tc::desc_kmajor(tc::smem_u32(sA + buf * a_bytes), g.lbo_a, sbo_a);
                     const uint32_t lbo_b = (uint32_t)nz * N * 16;    // between the two 8-channel halves
                     // an x-folded chunk reads its few x-offsets at halo columns xt_start + xt_step * tx
                     int xstep = 1, xstart = 0;
@@ -277,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                         for (int gi = g0; gi < gend; ++gi) {
                             const int ty = gi / nx, tx = gi - (gi / nx) * nx;
                             const int hx = xstart + xstep * tx;
-                            const uint64_t arow = adesc0 + (uint64_t)(ty * g.hw + hx);
+                            const uint64_t arow = adesc0 + (uint64_t)(ty * g.ystep + hx);
                             // plane u of slice group j feeds its slices s_lo..s_hi (offset tz = u - s) in one MMA
                             for (int u = 0; u <= nz + G - 2; ++u) {
                                 const int s_lo = u - (nz - 1) > 0 ? u - (nz - 1) : 0;
@@ -305,9 +340,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
             for (int dd = 0; dd < DPI; ++dd) tc::mma_commit(&acc_full[d0 + dd]);
         }
         tc::mma_commit(mma_done);
-    } else if (warp >= 5) {
-        // ---------------- epilogue: one warp per tensor-memory lane quarter ----------------
+    } else if (warp >= EPI0) {
+        // ---------------- epilogue: EPW warps per tensor-memory lane quarter ----------------
         const int q = warp & 3;                 // lane quarter
+        const int half = (warp - EPI0) >> 2;    // which PART columns of a slice group this warp holds
         const int r = q * 32 + lane;            // M row = voxel of the slice
         const int h = r >> 3, w = r & 7;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
@@ -318,6 +354,32 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
             const uint64_t deadline = tc::globaltimer() + kWaitNs;
             const int yy = y0 + h, xx = x0 + w;
             const float sx = F8 ? a.s_in[b] : 1.f;
+            // element offset of channel c of this thread's voxel in slice zz, NDHWC or channel-blocked
+            // Both layouts are affine in (slice zz, channel c, c a multiple of 8) for this thread's voxel:
+            //   NDHWC    ((b n + zz) n + yy) n + xx) C + c
+            //   blocked  ((((b n + zz) n + yy) C/8 + c/8) n + xx) 8
+            //   = b n^3 C + zz n^2 C + yy n C + (blocked ? xx 8 + c n : xx C + c)
+            const int n = a.n_out;
+            const size_t zstep_y = (size_t)n * n * N, zstep_r = (size_t)n * n * a.cres;
+            const size_t ybase = (size_t)b * n * zstep_y + (size_t)yy * n * N + (a.out_blocked ? xx * 8 : xx * N);
+            const size_t rbase = (size_t)b * n * zstep_r + (size_t)yy * n * a.cres + (a.res_blocked ? xx * 8 : xx * a.cres);
+            const int ycc = a.out_blocked ? n : 1, rcc = a.res_blocked ? n : 1;   // per channel
+            if (a.residual && yy < a.n_out && xx < a.n_out) {
+                // ask L2 for the residual input this tile's stores will add, while its MMAs run (one line per
+                // voxel row of a 16-byte block when blocked, taken by the lane at the row's first voxel)
+#pragma unroll 1
+                for (int u = 0; u < UNITS; ++u)
+#pragma unroll 1
+                    for (int c32 = 0; c32 < PART / 32; ++c32) {
+                        const int col = u * UCOLS + half * PART + c32 * 32;
+                        const int zz = z0 + col / N, cc = col % N;
+                        if (zz >= a.n_out) continue;
+                        const __nv_bfloat16 *r0 = a.xres + rbase + zz * zstep_r + (size_t)cc * rcc;
+                        if (!a.res_blocked) tc::prefetch_line_l2(r0);
+                        else if (w == 0)
+                            for (int k4 = 0; k4 < 4; ++k4) tc::prefetch_line_l2(r0 + (size_t)k4 * 8 * n);
+                    }
+            }
             float vmax = 0.f;
             bool ok = true;
             for (int u = 0; u < UNITS && ok; ++u) {
@@ -325,66 +387,66 @@ __global__ void __launch_bounds__(kThreads, 1) conv3d_tc_kernel(const __grid_con
                 if (!ok) { fail(); break; }
                 if (*abort_flag) { ok = false; break; }   // the issuers gave up: nothing valid to store
                 tc::tc_fence_after();
-#pragma unroll 1
-                for (int part = 0; part < UCOLS; part += PART) {
-                    uint32_t acc[PART / 32][32];
+                // read this warp's columns of the group, zero them for the next tile and hand them back
+                // before any arithmetic, so the next tile's MMAs into the group wait only for the reads
+                const int col0 = u * UCOLS + half * PART;
+                uint32_t acc[PART / 32][32];
 #pragma unroll
-                    for (int c32 = 0; c32 < PART / 32; ++c32)
-                        tc::tmem_ld32(tbase + lane_base + (uint32_t)(u * UCOLS + part + c32 * 32), acc[c32]);
-                    tc::tmem_ld_wait();
-                    if (part + PART >= UCOLS) {
-                        // the whole group has been read: zero it for the next tile and hand it back
-#pragma unroll 1
-                        for (int c = 0; c < UCOLS; c += 32) tc::tmem_st32_zero(tbase + lane_base + (uint32_t)(u * UCOLS + c));
-                        tc::tmem_st_wait();
-                        tc::tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&acc_empty[u]);
+                for (int c32 = 0; c32 < PART / 32; ++c32)
+                    tc::tmem_ld32(tbase + lane_base + (uint32_t)(col0 + c32 * 32), acc[c32]);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int c32 = 0; c32 < PART / 32; ++c32) tc::tmem_st32_zero(tbase + lane_base + (uint32_t)(col0 + c32 * 32));
+                tc::tmem_st_wait();
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&acc_empty[u]);
+#pragma unroll
+                for (int c32 = 0; c32 < PART / 32; ++c32) {
+                    const int col = col0 + c32 * 32;     // slice d = col / N, channels col % N ..
+                    const int d = col / N, cc = col % N;
+                    const int zz = z0 + d;
+                    if (zz >= a.n_out || yy >= a.n_out || xx >= a.n_out) continue;
+                    uint32_t *v = acc[c32];      // the arithmetic happens in place (float bits)
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        float t = __uint_as_float(v[j]);
+                        if constexpr (F8) t *= sx * a.s_w[cc + j];
+                        v[j] = __float_as_uint(fmaxf(t + a.bias[cc + j], 0.f));
                     }
-#pragma unroll
-                    for (int c32 = 0; c32 < PART / 32; ++c32) {
-                        const int col = u * UCOLS + part + c32 * 32;     // slice d = col / N, channels col % N ..
-                        const int d = col / N, cc = col % N;
-                        const int zz = z0 + d;
-                        if (zz >= a.n_out || yy >= a.n_out || xx >= a.n_out) continue;
-                        const size_t vox = (((size_t)b * a.n_out + zz) * a.n_out + yy) * a.n_out + xx;
-                        uint32_t *v = acc[c32];      // the arithmetic happens in place (float bits)
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            float t = __uint_as_float(v[j]);
-                            if constexpr (F8) t *= sx * a.s_w[cc + j];
-                            v[j] = __float_as_uint(fmaxf(t + a.bias[cc + j], 0.f));
-                        }
-                        if (a.residual) {
-                            const uint4 *src = reinterpret_cast<const uint4 *>(a.xres + vox * a.cres + cc);
-#pragma unroll
-                            for (int k4 = 0; k4 < 4; ++k4) {
-                                const uint4 t4 = src[k4];
-                                const __nv_bfloat162 *hp = reinterpret_cast<const __nv_bfloat162 *>(&t4);
-#pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    const float2 f = __bfloat1622float2(hp[e]);
-                                    v[k4 * 8 + 2 * e] = __float_as_uint(__uint_as_float(v[k4 * 8 + 2 * e]) + f.x);
-                                    v[k4 * 8 + 2 * e + 1] = __float_as_uint(__uint_as_float(v[k4 * 8 + 2 * e + 1]) + f.y);
-                                }
-                            }
-                        }
-                        uint4 *dst = reinterpret_cast<uint4 *>(a.y + vox * N + cc);
+                    if (a.residual) {
+                        // the input is read-only for the whole launch (the output is another buffer)
+                        // 8-channel blocks k4 = 0..3: contiguous (NDHWC) or n_out voxels apart (blocked)
+                        const __nv_bfloat16 *rsrc = a.xres + rbase + zz * zstep_r + (size_t)cc * rcc;
+                        const int rstep = 8 * rcc;
 #pragma unroll
                         for (int k4 = 0; k4 < 4; ++k4) {
-                            uint4 t4;
-                            __nv_bfloat162 *hp = reinterpret_cast<__nv_bfloat162 *>(&t4);
+                            const uint4 t4 = __ldg(reinterpret_cast<const uint4 *>(rsrc + k4 * rstep));
+                            const __nv_bfloat162 *hp = reinterpret_cast<const __nv_bfloat162 *>(&t4);
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
-                                hp[e] = __floats2bfloat162_rn(__uint_as_float(v[k4 * 8 + 2 * e]),
-                                                              __uint_as_float(v[k4 * 8 + 2 * e + 1]));
-                                if constexpr (F8) {
-                                    const float2 rr = __bfloat1622float2(hp[e]);
-                                    vmax = fmaxf(vmax, fmaxf(fabsf(rr.x), fabsf(rr.y)));
-                                }
+                                const float2 f = __bfloat1622float2(hp[e]);
+                                v[k4 * 8 + 2 * e] = __float_as_uint(__uint_as_float(v[k4 * 8 + 2 * e]) + f.x);
+                                v[k4 * 8 + 2 * e + 1] = __float_as_uint(__uint_as_float(v[k4 * 8 + 2 * e + 1]) + f.y);
                             }
-                            dst[k4] = t4;
                         }
+                    }
+                    __nv_bfloat16 *const ydst = a.y + ybase + zz * zstep_y + (size_t)cc * ycc;
+                    const int ystep = 8 * ycc;
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        uint4 t4;
+                        __nv_bfloat162 *hp = reinterpret_cast<__nv_bfloat162 *>(&t4);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            hp[e] = __floats2bfloat162_rn(__uint_as_float(v[k4 * 8 + 2 * e]),
+                                                          __uint_as_float(v[k4 * 8 + 2 * e + 1]));
+                            if constexpr (F8) {
+                                const float2 rr = __bfloat1622float2(hp[e]);
+                                vmax = fmaxf(vmax, fmaxf(fabsf(rr.x), fabsf(rr.y)));
+                            }
+                        }
+                        *reinterpret_cast<uint4 *>(ydst + k4 * ystep) = t4;
                     }
                 }
             }
@@ -656,7 +718,22 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     g.hd = T + ntmax - 1;
     g.hh = 16 + ntmax - 1;
     g.hw = 8 + ntmax - 1;
+    if (sp.blocked && stride != 1) {
+        snprintf(why, why_len, "a channel-blocked input needs stride 1");
+        return -1;
+    }
     g.plane_bytes = ((uint32_t)(g.hd * g.hh * g.hw) * 16 + 127) / 128 * 128;
+    if (sp.blocked) {
+        // [z][y][K half][x][16 bytes]: K halves hw rows apart, y rows 2 hw apart
+        g.a_bytes = ((uint32_t)(g.hd * g.hh * g.hw) * 32 + 127) / 128 * 128;
+        g.lbo_a = (uint32_t)g.hw * 16;
+        g.ystep = 2 * g.hw;
+    } else {
+        // [K half][z][y][x][16 bytes]
+        g.a_bytes = 2 * g.plane_bytes;
+        g.lbo_a = g.plane_bytes;
+        g.ystep = g.hw;
+    }
     // about 48 KB of weights per stage in a ring of two: each stage hand-off costs a fixed few
     // hundred cycles, and fewer, larger stages measured faster than deeper rings of smaller ones
     const uint32_t gbytes_max = (uint32_t)ntmax * c_out * 32;
@@ -688,14 +765,14 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     const size_t bar_bytes = (size_t)(4 + 2 * g.nbs + 2 * (T / group) + 1) * 8 + 16;
     const size_t limit = 227 * 1024;
     const size_t b_total = (size_t)g.nbs * g.stage_bytes;
-    const size_t a1 = 2 * (size_t)g.plane_bytes;
+    const size_t a1 = g.a_bytes;
     g.na = (2 * a1 + b_total + bar_bytes <= limit) ? 2 : 1;
     P.smem = g.na * a1 + b_total + bar_bytes;
     if (P.smem > limit) {
         snprintf(why, why_len, "tensor-core conv tile needs %zu bytes of shared memory", P.smem);
         return -1;
     }
-    if (g.hw * stride > 256 || g.hh * stride > 256 || g.hd * stride > 256) {
+    if (g.hw * stride > 256 || g.hh * stride > 256 || g.hd * stride > 256 || (sp.blocked && g.hw * 16 / sp.elem > 256)) {
         snprintf(why, why_len, "halo box too large for a TMA load");
         return -1;
     }
@@ -707,11 +784,19 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     const cuuint64_t rowb = (cuuint64_t)sp.cin_pad * sp.elem;   // bytes per voxel
     const cuuint64_t n = (cuuint64_t)sp.n_in;
     const cuuint64_t nx_in = n + (sp.fold == 2 ? 1 : 0);          // FP8-folded input is stored from x = -1
+    const cuuint64_t cpr = (cuuint64_t)(16 / sp.elem);              // elements per 16-byte channel block
     cuuint64_t dims[5] = {(cuuint64_t)sp.cin_pad, nx_in, n, n, (cuuint64_t)sp.max_poses};
     cuuint64_t strides[4] = {rowb, rowb * nx_in, rowb * nx_in * n, rowb * nx_in * n * n};
-    cuuint32_t box[5] = {(cuuint32_t)(16 / sp.elem), (cuuint32_t)(g.hw * stride), (cuuint32_t)(g.hh * stride),
+    cuuint32_t box[5] = {(cuuint32_t)cpr, (cuuint32_t)(g.hw * stride), (cuuint32_t)(g.hh * stride),
                          (cuuint32_t)(g.hd * stride), 1};
     cuuint32_t estr[5] = {1, (cuuint32_t)stride, (cuuint32_t)stride, (cuuint32_t)stride, 1};
+    if (sp.blocked) {
+        // dims (x * cpr + channel in block, block, y, z, pose); a box row is hw voxels x 16 bytes
+        const cuuint64_t blocks = (cuuint64_t)sp.cin_pad / cpr;
+        dims[0] = nx_in * cpr; dims[1] = blocks; dims[2] = n; dims[3] = n; dims[4] = (cuuint64_t)sp.max_poses;
+        strides[0] = nx_in * 16; strides[1] = blocks * nx_in * 16; strides[2] = strides[1] * n; strides[3] = strides[2] * n;
+        box[0] = (cuuint32_t)(g.hw * cpr); box[1] = 2; box[2] = (cuuint32_t)g.hh; box[3] = (cuuint32_t)g.hd; box[4] = 1;
+    }
     CUresult r = enc(&P.tmap, sp.elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 5,
                      const_cast<void *>(sp.x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -738,6 +823,9 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     A.xpat = sp.fold ? 1 : 0;
     A.x_shift = sp.fold == 2 ? 1 : 0;
     if (sp.fold) fold_pattern(sp.fold, k, A.xt_n, A.xt_step, A.xt_start);
+    A.blocked = sp.blocked;
+    A.out_blocked = sp.out_blocked;
+    A.res_blocked = sp.res_blocked;
     A.g = g;
     A.err = sp.err;
     P.N = c_out;
@@ -762,7 +850,7 @@ static void launch_t(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
     P.args.B = B;
     const unsigned tiles = P.grid * (unsigned)B;
     const unsigned grid = tiles < (unsigned)P.sms ? tiles : (unsigned)P.sms;
-    conv3d_tc_kernel<N, T, F8, G><<<grid, kThreads, P.smem, s>>>(P.tmap, P.args);
+    conv3d_tc_kernel<N, T, F8, G><<<grid, Roles<N, T, G>::THREADS, P.smem, s>>>(P.tmap, P.args);
 }
 
 template <int N, int T, bool F8>

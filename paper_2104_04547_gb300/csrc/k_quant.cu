@@ -1,5 +1,6 @@
 // Per-pose FP8 (E4M3) quantization of NDHWC bf16 activations for the FP8
-// convolution path.  Each pose gets its own scale s = max|x| / 448 (the
+// convolution path (stored NDHWC, or channel-blocked for the stride-1 layers,
+// whose halos are then loaded in rows of hw x 16 contiguous bytes).  Each pose gets its own scale s = max|x| / 448 (the
 // largest finite E4M3 value), so a pose's result does not depend on the other
 // poses of its batch.  amax_per_pose_kernel reduces max|x| per pose;
 // quantize_per_pose_kernel writes code = E4M3(x / s) (round to nearest even,
@@ -56,6 +57,43 @@ __global__ void quantize_per_pose_kernel(const __nv_bfloat16 *x, uint8_t *q, siz
     }
 }
 
+// Channel-blocked output: item (voxel v, 16-channel block cb) reads 16 bf16 (32 bytes) and writes 16 codes
+// to [b][z][y][cb][x][16]; cb varies fastest across threads, so the reads are contiguous and each
+// block's writes form runs of consecutive x.
+__global__ void quantize_blocked_kernel(const __nv_bfloat16 *x, uint8_t *q, int n, int C, const float *amax,
+                                        float *scale) {
+    const int b = blockIdx.y;
+    const float am = amax[b];
+    const float s = am > 0.f ? am / kE4M3Max : 1.f;
+    const float inv = 1.f / s;
+    if (blockIdx.x == 0 && threadIdx.x == 0) scale[b] = s;
+    const int ncb = C / 16;
+    const size_t nv = (size_t)n * n * n;
+    const size_t items = nv * ncb;
+    const __nv_bfloat16 *xb = x + (size_t)b * nv * C;
+    uint8_t *qb = q + (size_t)b * nv * C;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < items; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = i / ncb;
+        const int cb = (int)(i - v * ncb);
+        const size_t row = v / n;                 // (z, y)
+        const int xx = (int)(v - row * n);
+        const uint4 *src = reinterpret_cast<const uint4 *>(xb + v * C + cb * 16);
+        uint4 out;
+        uint16_t *o16 = reinterpret_cast<uint16_t *>(&out);
+#pragma unroll
+        for (int hlf = 0; hlf < 2; ++hlf) {
+            const uint4 t = src[hlf];
+            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&t);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(h[e]);
+                o16[hlf * 4 + e] = __nv_cvt_float2_to_fp8x2(make_float2(f.x * inv, f.y * inv), __NV_SATFINITE, __NV_E4M3);
+            }
+        }
+        *reinterpret_cast<uint4 *>(qb + ((row * ncb + cb) * n + xx) * 16) = out;
+    }
+}
+
 // One CTA per 4 grid rows (b, z, y): the rows' channels 0..18 are loaded with 16-byte reads and
 // quantized into shared memory (codes are the same E4M3(x / s) as quantize_per_pose_kernel gives),
 // then each stored voxel j = 0 .. n of a row is assembled from them, as described at
@@ -63,7 +101,7 @@ __global__ void quantize_per_pose_kernel(const __nv_bfloat16 *x, uint8_t *q, siz
 constexpr int kFoldRows = 4;
 
 __global__ void __launch_bounds__(256) quantize_fold_fp8_kernel(const __nv_bfloat16 *g, uint8_t *q, int B, int n,
-                                                                 int p, const float *amax, float *scale) {
+                                                                 int p, const float *amax, float *scale, int blocked) {
     extern __shared__ __align__(16) uint8_t s_code[];     // [kFoldRows][n][20] (19 channels + pad)
     const int rows = B * n * n;
     const int r0 = blockIdx.x * kFoldRows;
@@ -112,20 +150,35 @@ __global__ void __launch_bounds__(256) quantize_fold_fp8_kernel(const __nv_bfloa
 #pragma unroll
             for (int f = 0; f < 3; ++f) out[32 + 3 * sl + f] = cr[x * 20 + 16 + f];
         }
-        uint4 *dst = reinterpret_cast<uint4 *>(q + ((size_t)(r0 + r) * nx + j) * 64);
+        if (blocked) {
+            // [row][16-byte block u][x = j][16]
 #pragma unroll
-        for (int u = 0; u < 4; ++u) dst[u] = reinterpret_cast<const uint4 *>(out)[u];
+            for (int u = 0; u < 4; ++u)
+                *reinterpret_cast<uint4 *>(q + (((size_t)(r0 + r) * 4 + u) * nx + j) * 16) = reinterpret_cast<const uint4 *>(out)[u];
+        } else {
+            uint4 *dst = reinterpret_cast<uint4 *>(q + ((size_t)(r0 + r) * nx + j) * 64);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dst[u] = reinterpret_cast<const uint4 *>(out)[u];
+        }
     }
 }
 
 }  // namespace
 
 void launch_quantize_fold_fp8(const void *grid_bf16, void *q_fp8, int B, int n, int p, const float *amax,
-                              float *scale, cudaStream_t s) {
+                              float *scale, int blocked, cudaStream_t s) {
     const int rows = B * n * n;
     const size_t sm = (size_t)kFoldRows * n * 20;
     quantize_fold_fp8_kernel<<<(unsigned)((rows + kFoldRows - 1) / kFoldRows), 256, sm, s>>>(
-        static_cast<const __nv_bfloat16 *>(grid_bf16), static_cast<uint8_t *>(q_fp8), B, n, p, amax, scale);
+        static_cast<const __nv_bfloat16 *>(grid_bf16), static_cast<uint8_t *>(q_fp8), B, n, p, amax, scale, blocked);
+}
+
+void launch_quantize_blocked(const void *x_bf16, void *q_fp8, int B, int n, int C, const float *amax, float *scale,
+                             cudaStream_t s) {
+    const size_t items = (size_t)n * n * n * (C / 16);
+    const unsigned gx = (unsigned)((items + 255) / 256 < 128 ? (items + 255) / 256 : 128);
+    quantize_blocked_kernel<<<dim3(gx > 0 ? gx : 1, B), 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(x_bf16),
+                                                                    static_cast<uint8_t *>(q_fp8), n, C, amax, scale);
 }
 
 void launch_amax_per_pose(const void *x_bf16, int B, size_t per_pose, float *amax, cudaStream_t s) {

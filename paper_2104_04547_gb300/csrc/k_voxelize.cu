@@ -205,14 +205,17 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
     if (vx < n && vy < n && vz < n) {
         const size_t vox = (((size_t)p * n + vz) * n + vy) * n + vx;
         if constexpr (BF16) {
-            __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(a.out) + vox * CX;
+            // 8-channel block c0 / 8 of the voxel: NDHWC, or channel-blocked [row][CX / 8][x][8]
+            const size_t row = ((size_t)p * n + vz) * n + vy;
+            __nv_bfloat16 *const base = reinterpret_cast<__nv_bfloat16 *>(a.out);
+            auto blk = [&](int c0) { return a.blocked ? base + ((row * (CX / 8) + c0 / 8) * n + vx) * 8 : base + vox * CX + c0; };
             if (a.fold_pad < 0) {
 #pragma unroll
                 for (int c0 = 0; c0 < CX; c0 += 8) {
                     __align__(16) __nv_bfloat16 v8[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) v8[j] = __float2bfloat16_rn(c0 + j < kFeat ? acc[c0 + j] : 0.f);
-                    *reinterpret_cast<uint4 *>(out + c0) = *reinterpret_cast<const uint4 *>(v8);
+                    *reinterpret_cast<uint4 *>(blk(c0)) = *reinterpret_cast<const uint4 *>(v8);
                 }
             } else {
                 // folded layout, first pass: features 16..18 at slot s = p of the voxel's own second chunk
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
                                                : d == 0 ? acc[16] : d == 1 ? acc[17] : d == 2 ? acc[18] : 0.f;
                         v8[j] = __float2bfloat16_rn(v);
                     }
-                    *reinterpret_cast<uint4 *>(out + c0) = *reinterpret_cast<const uint4 *>(v8);
+                    *reinterpret_cast<uint4 *>(blk(c0)) = *reinterpret_cast<const uint4 *>(v8);
                 }
             }
         } else {
@@ -249,19 +252,25 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
 }
 
 
+// Channels 16 + 8 j .. 23 + 8 j (j = 0, 1) of voxel x of grid row `row` (pose, z, y), 32 channels per voxel.
+__device__ __forceinline__ __nv_bfloat16 *hi_block(__nv_bfloat16 *grid, int row, int x, int j, int n, int blocked) {
+    return blocked ? grid + (((size_t)row * 4 + 2 + j) * n + x) * 8 : grid + ((size_t)row * n + x) * 32 + 16 + 8 * j;
+}
+
 // Second pass of the folded layout: one CTA per 8 x-rows (all poses, z, y); each row's features
 // 16..18 (at slot 16 + 3p) are staged in shared memory first, then every voxel's second chunk is
 // rewritten as slot 16 + 3 s + f = feature 16 + f of voxel x - p + s (zero outside the grid) with
 // 16-byte stores.  Rows are independent, and a row is read completely before any of it is written.
-__global__ void __launch_bounds__(256) fold_grid_kernel(__nv_bfloat16 *grid, int rows, int n, int p) {
+__global__ void __launch_bounds__(256) fold_grid_kernel(__nv_bfloat16 *grid, int rows, int n, int p, int blocked) {
     extern __shared__ __align__(16) __nv_bfloat16 s_r[];     // [8][n][3]
     const int r0 = blockIdx.x * 8;
     const int nr = min(8, rows - r0);
     const int sp = 16 + 3 * p;
     for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
         // the voxel's channels 16..31 in two 16-byte loads (one 32-byte sector), then the 3 at slot sp
-        const uint4 *src = reinterpret_cast<const uint4 *>(grid + ((size_t)r0 * n + e) * 32 + 16);
-        const uint4 a0 = src[0], a1 = src[1];
+        const int r = e / n, x = e - r * n;
+        const uint4 a0 = *reinterpret_cast<const uint4 *>(hi_block(grid, r0 + r, x, 0, n, blocked));
+        const uint4 a1 = *reinterpret_cast<const uint4 *>(hi_block(grid, r0 + r, x, 1, n, blocked));
         const uint32_t wd[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
         // select with constant indices (sp is a runtime value; a runtime index would go to local memory)
         const int o = sp - 16;
@@ -289,9 +298,8 @@ __global__ void __launch_bounds__(256) fold_grid_kernel(__nv_bfloat16 *grid, int
             for (int f = 0; f < 3; ++f) v16[3 * sl + f] = in ? s_r[(r * n + xs) * 3 + f] : __float2bfloat16_rn(0.f);
         }
         v16[15] = __float2bfloat16_rn(0.f);
-        uint4 *dst = reinterpret_cast<uint4 *>(grid + ((size_t)r0 * n + e) * 32 + 16);
-        dst[0] = reinterpret_cast<const uint4 *>(v16)[0];
-        dst[1] = reinterpret_cast<const uint4 *>(v16)[1];
+        *reinterpret_cast<uint4 *>(hi_block(grid, r0 + r, x, 0, n, blocked)) = reinterpret_cast<const uint4 *>(v16)[0];
+        *reinterpret_cast<uint4 *>(hi_block(grid, r0 + r, x, 1, n, blocked)) = reinterpret_cast<const uint4 *>(v16)[1];
     }
 }
 
@@ -322,7 +330,7 @@ void launch_voxelize(const VoxArgs &a, cudaStream_t s) {
         if (a.fold_pad >= 0) {
             const int rows = a.n_poses * a.grid_n * a.grid_n;
             fold_grid_kernel<<<(rows + 7) / 8, 256, (size_t)8 * a.grid_n * 3 * sizeof(__nv_bfloat16), s>>>(
-                static_cast<__nv_bfloat16 *>(a.out), rows, a.grid_n, a.fold_pad);
+                static_cast<__nv_bfloat16 *>(a.out), rows, a.grid_n, a.fold_pad, a.blocked);
         }
     } else if (a.cx == 24) {
         launch_vox_t<false, 24>(a, s);
