@@ -78,17 +78,21 @@ def run(args):
             "batches": len(batches), "max_batch": args.max_batch,
             "atoms_per_pose_mean": float(np.mean(sizes))}
 
-    def timed(label):
-        # one untimed pass over every batch: each batch size's graph is captured here, not in the timed loop
+    def timed(label, passes=5):
+        # one untimed pass over every batch: each batch size's graph is captured here, not in the timed loop;
+        # then `passes` timed passes over the pool, reported as the median (and the range)
         for pb, db in zip(packed, dev):
             m.score(db, n_poses=len(pb["n_lig"]), out=out, on_device=True)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for pb, db in zip(packed, dev):
-            m.score(db, n_poses=len(pb["n_lig"]), out=out, on_device=True)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        print(json.dumps({**base, "mode": label, "poses_per_s": len(pool) / dt, "seconds": dt}), flush=True)
+        rates = []
+        for _ in range(passes):
+            t0 = time.perf_counter()
+            for pb, db in zip(packed, dev):
+                m.score(db, n_poses=len(pb["n_lig"]), out=out, on_device=True)
+            torch.cuda.synchronize()
+            rates.append(len(pool) / (time.perf_counter() - t0))
+        print(json.dumps({**base, "mode": label, "poses_per_s": float(np.median(rates)),
+                          "poses_per_s_range": [float(min(rates)), float(max(rates))], "passes": passes}), flush=True)
 
     timed("plain launches")
     m.use_cuda_graphs(True)

@@ -9,7 +9,8 @@
 //   ligand gather:       sum over ligand atoms of sigmoid(W_g [h_i, x_i] + b_g) * (W_o h_i + b_o)
 //                        (x_i = input of the last stage), or sum of (W h_i + b)
 //
-// Node work is warp-per-node: lane l owns features l and l + 32.  The
+// Node work is warp-per-node (the step kernel: a few nodes per warp sharing the
+// weight loads): lane l owns features l and l + 32.  The
 // per-edge-type transforms W_e h_j + b_e are computed once per node and step
 // (sg_transform_kernel at a stage start, then by the previous step), so a step
 // is a segment sum over the sorted CSR row in a fixed order followed by the
@@ -76,78 +77,114 @@ __global__ void __launch_bounds__(kWarps * 32) sg_transform_kernel(SgTransformAr
     }
 }
 
+// A warp takes kNodesPerWarp consecutive nodes: the matrix-vector products of the GRU and of the next
+// step's transforms load each weight once for all of them (the weights, 128 KB at H = 64, are read from
+// L1 and that read bounds the kernel), while every node's sums keep the order of a warp per node.
+constexpr int kNodesPerWarp = 4;
+
 template <int H>
 __global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
     constexpr int HJ = H / 32;
-    __shared__ float sv[kWarps][2 * H];
+    constexpr int NP = kNodesPerWarp;
+    __shared__ float sv[kWarps][NP][2 * H];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kWarps + warp;
-    if (i >= (a.A_dev ? *a.A_dev : a.A)) return;
-    float *v = sv[warp];
+    const int A = a.A_dev ? *a.A_dev : a.A;
+    const int i0 = (blockIdx.x * kWarps + warp) * NP;
+    if (i0 >= A) return;
+    const int np = min(NP, A - i0);          // nodes of this warp (the rest of the NP slots are zero)
+    float (*v)[2 * H] = sv[warp];
 
     // message: segment sum of the neighbours' transforms, edge type by edge type, row order
-    float m[HJ];
+    float hv[NP][HJ];
 #pragma unroll
-    for (int j = 0; j < HJ; ++j) m[j] = 0.f;
-    for (int e = 0; e < 2; ++e) {
-        if (!a.T_in[e]) continue;
-        const int beg = a.beg[e][i], d = a.deg[e][i];
-        const float *T = a.T_in[e];
-        for (int q0 = 0; q0 < d; q0 += 32) {
-            const int jl = (q0 + lane < d) ? a.col[e][beg + q0 + lane] : 0;
-            const int nq = min(32, d - q0);
-            for (int q = 0; q < nq; ++q) {
-                const int jn = __shfl_sync(0xffffffffu, jl, q);
+    for (int n = 0; n < NP; ++n) {
+        float m[HJ];
 #pragma unroll
-                for (int j = 0; j < HJ; ++j) m[j] += T[(size_t)jn * H + lane + 32 * j];
+        for (int j = 0; j < HJ; ++j) m[j] = 0.f;
+        if (n < np) {
+            const int i = i0 + n;
+            for (int e = 0; e < 2; ++e) {
+                if (!a.T_in[e]) continue;
+                const int beg = a.beg[e][i], d = a.deg[e][i];
+                const float *T = a.T_in[e];
+                for (int q0 = 0; q0 < d; q0 += 32) {
+                    const int jl = (q0 + lane < d) ? a.col[e][beg + q0 + lane] : 0;
+                    const int nq = min(32, d - q0);
+                    for (int q = 0; q < nq; ++q) {
+                        const int jn = __shfl_sync(0xffffffffu, jl, q);
+#pragma unroll
+                        for (int j = 0; j < HJ; ++j) m[j] += T[(size_t)jn * H + lane + 32 * j];
+                    }
+                }
             }
         }
-    }
-    float hv[HJ];
 #pragma unroll
-    for (int j = 0; j < HJ; ++j) {
-        const int o = lane + 32 * j;
-        hv[j] = a.h_in[(size_t)i * H + o];
-        v[o] = m[j];
-        v[H + o] = hv[j];
+        for (int j = 0; j < HJ; ++j) {
+            const int o = lane + 32 * j;
+            hv[n][j] = n < np ? a.h_in[(size_t)(i0 + n) * H + o] : 0.f;
+            v[n][o] = m[j];
+            v[n][H + o] = hv[n][j];
+        }
     }
     __syncwarp();
-    float hn[HJ];
+    float hn[NP][HJ];
 #pragma unroll
     for (int j = 0; j < HJ; ++j) {
         const int o = lane + 32 * j;
-        float ir = a.bih[o], iz = a.bih[H + o], in_ = a.bih[2 * H + o];
-        float hr = a.bhh[o], hz = a.bhh[H + o], hn_ = a.bhh[2 * H + o];
+        float ir[NP], iz[NP], in_[NP], hr[NP], hz[NP], hn_[NP];
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+            ir[n] = a.bih[o]; iz[n] = a.bih[H + o]; in_[n] = a.bih[2 * H + o];
+            hr[n] = a.bhh[o]; hz[n] = a.bhh[H + o]; hn_[n] = a.bhh[2 * H + o];
+        }
         for (int k = 0; k < H; ++k) {
-            const float mk = v[k], hk = v[H + k];
             const float *wi = a.wih_t + (size_t)k * 3 * H;
             const float *wh = a.whh_t + (size_t)k * 3 * H;
-            ir = fmaf(wi[o], mk, ir);
-            iz = fmaf(wi[H + o], mk, iz);
-            in_ = fmaf(wi[2 * H + o], mk, in_);
-            hr = fmaf(wh[o], hk, hr);
-            hz = fmaf(wh[H + o], hk, hz);
-            hn_ = fmaf(wh[2 * H + o], hk, hn_);
+            const float w0 = wi[o], w1 = wi[H + o], w2 = wi[2 * H + o];
+            const float u0 = wh[o], u1 = wh[H + o], u2 = wh[2 * H + o];
+#pragma unroll
+            for (int n = 0; n < NP; ++n) {
+                const float mk = v[n][k], hk = v[n][H + k];
+                ir[n] = fmaf(w0, mk, ir[n]);
+                iz[n] = fmaf(w1, mk, iz[n]);
+                in_[n] = fmaf(w2, mk, in_[n]);
+                hr[n] = fmaf(u0, hk, hr[n]);
+                hz[n] = fmaf(u1, hk, hz[n]);
+                hn_[n] = fmaf(u2, hk, hn_[n]);
+            }
         }
-        const float r = sigm(ir + hr);
-        const float z = sigm(iz + hz);
-        const float nn = tanhf(in_ + r * hn_);
-        hn[j] = (1.f - z) * nn + z * hv[j];
-        a.h_out[(size_t)i * H + o] = hn[j];
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+            const float r = sigm(ir[n] + hr[n]);
+            const float z = sigm(iz[n] + hz[n]);
+            const float nn = tanhf(in_[n] + r * hn_[n]);
+            hn[n][j] = (1.f - z) * nn + z * hv[n][j];
+            if (n < np) a.h_out[(size_t)(i0 + n) * H + o] = hn[n][j];
+        }
     }
     if (!a.T_out[0] && !a.T_out[1]) return;
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < HJ; ++j) v[lane + 32 * j] = hn[j];
+    for (int n = 0; n < NP; ++n)
+#pragma unroll
+        for (int j = 0; j < HJ; ++j) v[n][lane + 32 * j] = hn[n][j];
     __syncwarp();
     for (int e = 0; e < 2; ++e) {
         if (!a.T_out[e]) continue;
 #pragma unroll
         for (int j = 0; j < HJ; ++j) {
             const int o = lane + 32 * j;
-            float t = a.be[e][o];
-            for (int k = 0; k < H; ++k) t = fmaf(a.we_t[e][k * H + o], v[k], t);
-            a.T_out[e][(size_t)i * H + o] = t;
+            float t[NP];
+#pragma unroll
+            for (int n = 0; n < NP; ++n) t[n] = a.be[e][o];
+            for (int k = 0; k < H; ++k) {
+                const float w = a.we_t[e][k * H + o];
+#pragma unroll
+                for (int n = 0; n < NP; ++n) t[n] = fmaf(w, v[n][k], t[n]);
+            }
+#pragma unroll
+            for (int n = 0; n < NP; ++n)
+                if (n < np) a.T_out[e][(size_t)(i0 + n) * H + o] = t[n];
         }
     }
 }
@@ -212,7 +249,7 @@ void launch_sg_transform(const SgTransformArgs &a, cudaStream_t s) {
 }
 
 void launch_sg_step(const SgStepArgs &a, cudaStream_t s) {
-    const int blocks = (a.A + kWarps - 1) / kWarps;
+    const int blocks = (a.A + kWarps * kNodesPerWarp - 1) / (kWarps * kNodesPerWarp);
     if (a.H == 64) sg_step_kernel<64><<<blocks, kWarps * 32, 0, s>>>(a);
     else sg_step_kernel<32><<<blocks, kWarps * 32, 0, s>>>(a);
 }
