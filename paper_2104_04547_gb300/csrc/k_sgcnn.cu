@@ -9,12 +9,12 @@
 //   ligand gather:       sum over ligand atoms of sigmoid(W_g [h_i, x_i] + b_g) * (W_o h_i + b_o)
 //                        (x_i = input of the last stage), or sum of (W h_i + b)
 //
-// Node work is warp-per-node (the step kernel: a few nodes per warp sharing the
-// weight loads): lane l owns features l and l + 32.  The
-// per-edge-type transforms W_e h_j + b_e are computed once per node and step
-// (sg_transform_kernel at a stage start, then by the previous step), so a step
-// is a segment sum over the sorted CSR row in a fixed order followed by the
-// GRU matrix-vector products, all deterministic.  The gather is one CTA per
+// A warp takes a few consecutive nodes (sharing each weight load); lane l owns
+// features l and l + 32 of each.  The per-edge-type transforms W_e h_j + b_e
+// are computed once per node and step (sg_transform_kernel at a stage start,
+// then by the previous step), so a step is a segment sum over the sorted CSR
+// row in a fixed order followed by the GRU matrix-vector products, all
+// deterministic.  The gather is one CTA per
 // pose: warps take ligand atoms round robin and the warp partials are added in
 // warp order.
 #include "fusion_internal.cuh"
@@ -27,60 +27,89 @@ constexpr int kWarps = 8;
 
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
 
+// A warp takes kNodesPerWarp consecutive nodes: the matrix-vector products load each weight once for all
+// of them (weights are read from L1, and that read bounds these kernels), while every node's sums keep the
+// order of a warp per node.
+constexpr int kNodesPerWarp = 4;
+
 template <int H>
 __global__ void __launch_bounds__(kWarps * 32) sg_transform_kernel(SgTransformArgs a) {
     constexpr int HJ = H / 32;
-    __shared__ float sv[kWarps][2 * H];
+    constexpr int NP = kNodesPerWarp;
+    __shared__ float sv[kWarps][NP][2 * H];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kWarps + warp;
-    if (i >= (a.A_dev ? *a.A_dev : a.A)) return;
-    float *v = sv[warp];
+    const int A = a.A_dev ? *a.A_dev : a.A;
+    const int i0 = (blockIdx.x * kWarps + warp) * NP;
+    if (i0 >= A) return;
+    const int np = min(NP, A - i0);          // nodes of this warp (the rest of the NP slots are zero)
+    float (*v)[2 * H] = sv[warp];
 #pragma unroll
-    for (int j = 0; j < HJ; ++j) {
-        const int o = lane + 32 * j;
-        v[H + o] = o < kFeat ? a.feat[(size_t)i * kFeat + o] : 0.f;
-        if (!a.init) v[o] = a.h_in[(size_t)i * H + o];
-    }
+    for (int n = 0; n < NP; ++n)
+#pragma unroll
+        for (int j = 0; j < HJ; ++j) {
+            const int o = lane + 32 * j;
+            const size_t i = (size_t)(i0 + n);
+            v[n][H + o] = (n < np && o < kFeat) ? a.feat[i * kFeat + o] : 0.f;
+            v[n][o] = (n < np && !a.init) ? a.h_in[i * H + o] : 0.f;
+        }
     __syncwarp();
-    float x[HJ];
+    float x[NP][HJ];
 #pragma unroll
     for (int j = 0; j < HJ; ++j) {
         const int o = lane + 32 * j;
         if (a.init) {
-            x[j] = v[H + o];
+#pragma unroll
+            for (int n = 0; n < NP; ++n) x[n][j] = v[n][H + o];
         } else if (a.gi_t) {
-            float u = a.gbi[o], w = a.gbj[o];
-            for (int k = 0; k < 2 * H; ++k) u = fmaf(a.gi_t[k * H + o], v[k], u);
-            for (int k = 0; k < H; ++k) w = fmaf(a.gj_t[k * H + o], v[k], w);
-            x[j] = sigm(u) * w;
+            float u[NP], w[NP];
+#pragma unroll
+            for (int n = 0; n < NP; ++n) { u[n] = a.gbi[o]; w[n] = a.gbj[o]; }
+            for (int k = 0; k < 2 * H; ++k) {
+                const float g = a.gi_t[k * H + o];
+#pragma unroll
+                for (int n = 0; n < NP; ++n) u[n] = fmaf(g, v[n][k], u[n]);
+            }
+            for (int k = 0; k < H; ++k) {
+                const float g = a.gj_t[k * H + o];
+#pragma unroll
+                for (int n = 0; n < NP; ++n) w[n] = fmaf(g, v[n][k], w[n]);
+            }
+#pragma unroll
+            for (int n = 0; n < NP; ++n) x[n][j] = sigm(u[n]) * w[n];
         } else {
-            x[j] = v[o];
+#pragma unroll
+            for (int n = 0; n < NP; ++n) x[n][j] = v[n][o];
         }
     }
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < HJ; ++j) {
-        const int o = lane + 32 * j;
-        v[o] = x[j];
-        a.h_out[(size_t)i * H + o] = x[j];
-    }
+    for (int n = 0; n < NP; ++n)
+#pragma unroll
+        for (int j = 0; j < HJ; ++j) {
+            const int o = lane + 32 * j;
+            v[n][o] = x[n][j];
+            if (n < np) a.h_out[(size_t)(i0 + n) * H + o] = x[n][j];
+        }
     __syncwarp();
     for (int e = 0; e < 2; ++e) {
         if (!a.we_t[e]) continue;
 #pragma unroll
         for (int j = 0; j < HJ; ++j) {
             const int o = lane + 32 * j;
-            float t = a.be[e][o];
-            for (int k = 0; k < H; ++k) t = fmaf(a.we_t[e][k * H + o], v[k], t);
-            a.T[e][(size_t)i * H + o] = t;
+            float t[NP];
+#pragma unroll
+            for (int n = 0; n < NP; ++n) t[n] = a.be[e][o];
+            for (int k = 0; k < H; ++k) {
+                const float w = a.we_t[e][k * H + o];
+#pragma unroll
+                for (int n = 0; n < NP; ++n) t[n] = fmaf(w, v[n][k], t[n]);
+            }
+#pragma unroll
+            for (int n = 0; n < NP; ++n)
+                if (n < np) a.T[e][(size_t)(i0 + n) * H + o] = t[n];
         }
     }
 }
-
-// A warp takes kNodesPerWarp consecutive nodes: the matrix-vector products of the GRU and of the next
-// step's transforms load each weight once for all of them (the weights, 128 KB at H = 64, are read from
-// L1 and that read bounds the kernel), while every node's sums keep the order of a warp per node.
-constexpr int kNodesPerWarp = 4;
 
 template <int H>
 __global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
@@ -243,7 +272,7 @@ __global__ void __launch_bounds__(kWarps * 32) sg_gather_kernel(SgGatherArgs a) 
 }  // namespace
 
 void launch_sg_transform(const SgTransformArgs &a, cudaStream_t s) {
-    const int blocks = (a.A + kWarps - 1) / kWarps;
+    const int blocks = (a.A + kWarps * kNodesPerWarp - 1) / (kWarps * kNodesPerWarp);
     if (a.H == 64) sg_transform_kernel<64><<<blocks, kWarps * 32, 0, s>>>(a);
     else sg_transform_kernel<32><<<blocks, kWarps * 32, 0, s>>>(a);
 }
