@@ -246,6 +246,7 @@ struct fusion_model {
     float *in_xyz = nullptr, *in_feat = nullptr;
     float *origin = nullptr;
     int4 *atom_vox = nullptr;
+    uint32_t *tile_mask = nullptr;    // [B][kTileMaskWords]: voxelize tiles some atom's support meets
     float *atom_w = nullptr;
     void *grid = nullptr;
     int grid_cx = kGridCxF32;
@@ -501,6 +502,7 @@ int alloc_workspace(fusion_model *m) {
     RC(dalloc(m, &m->in_feat, A * kFeat));
     RC(dalloc(m, &m->origin, B * 3));
     RC(dalloc(m, &m->atom_vox, A));
+    RC(dalloc(m, &m->tile_mask, B * kTileMaskWords));
     RC(dalloc(m, &m->atom_w, A * 3 * KW));
     const size_t n3 = (size_t)d.grid_n * d.grid_n * d.grid_n;
     RC(dalloc_bytes(m, &m->grid, B * n3 * m->grid_cx * m->esz));
@@ -783,7 +785,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
 
     // pose prep + voxelize
     PrepArgs pa{off_d, nlig_d, xyz_d, B, d.max_atoms, d.grid_n, d.grid_h, d.sigma, d.support,
-                m->origin, m->atom_vox, m->atom_w, m->err};
+                m->origin, m->atom_vox, m->atom_w, m->err, m->tile_mask};
     launch_prep(pa, ms);
     RC(check_launch("prep"));
     map[0] = ei; mark(ms);
@@ -872,7 +874,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     RC(check_launch("sg_gather"));
     sg_mark(3);
     VoxArgs va{off_d, feat_d, m->atom_vox, m->atom_w, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx,
-               m->bf16 ? 1 : 0, m->grid_fold, bf16_blocked_in(m, 0) ? 1 : 0};
+               m->bf16 ? 1 : 0, m->grid_fold, bf16_blocked_in(m, 0) ? 1 : 0, m->tile_mask};
     launch_voxelize(va, st);
     RC(check_launch("voxelize"));
     map[1] = ei; mark(st);

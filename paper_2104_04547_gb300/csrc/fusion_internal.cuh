@@ -37,7 +37,10 @@ struct PrepArgs {
     int4 *atom_vox;       // [A]: (cz, cy, cx, pose)
     float *atom_w;        // [A][3][2k+1]: z, y, x axis weights
     unsigned *err;
+    uint32_t *tile_mask;  // [B][kTileMaskWords]: bit t set iff some atom's support cube meets 8^3 tile t
 };
+// Grid tiles of 8^3 voxels per pose are at most 12^3 (grid_n <= 96): one bit each.
+constexpr int kTileMaskWords = (12 * 12 * 12 + 31) / 32;
 void launch_prep(const PrepArgs &a, cudaStream_t s);
 
 struct VoxArgs {
@@ -56,6 +59,7 @@ struct VoxArgs {
                           // channel 16 + 3 s + f of voxel x holds feature 16 + f of voxel x - p + s
                           // (s = 0..4, zero outside the grid), channel 31 zero
     int blocked;          // bf16 only: store channel-blocked, [B][n][n][cx / 8][n][8]
+    const uint32_t *tile_mask;   // PrepArgs::tile_mask: a tile whose bit is clear stores zeros at once
 };
 void launch_voxelize(const VoxArgs &a, cudaStream_t s);
 

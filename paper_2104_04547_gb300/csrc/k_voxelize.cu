@@ -8,7 +8,10 @@
 // and, per atom, its containing voxel and the 3 x (2k+1) per-axis weights
 //   w_d(i) = 1/2 [erf((u_i + h - x_d)/(sigma sqrt 2)) - erf((u_i - x_d)/(sigma sqrt 2))].
 //
-// voxelize_kernel (one CTA per 8^3 voxel tile of a pose): compacts, in atom
+// prep_kernel also marks, per pose, the 8^3 tiles that some atom's support cube
+// meets.  voxelize_kernel (one CTA per 8^3 voxel tile of a pose) stores zeros at
+// once for an unmarked tile (on docked poses about 70% of a 48^3 grid's tiles
+// hold no atom); otherwise it compacts, in atom
 // order, the atoms whose support cube meets the tile, stages them in shared
 // memory and accumulates all channels of each voxel in registers in atom-index
 // order (deterministic, no atomics), then stores the voxel's channels as one
@@ -27,6 +30,8 @@ namespace fusion {
 
 namespace {
 
+constexpr int kTile = 8;      // voxelize tiles are kTile^3 voxels
+
 // erf(b) - erf(a) for a < b, through erfc in the tails to keep relative accuracy.
 __device__ __forceinline__ float erf_diff(float a, float b) {
     if (a >= 0.f) return erfcf(a) - erfcf(b);
@@ -40,10 +45,12 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a) {
     const int N = a.atom_off[p + 1] - a0;
     const int nl = a.n_lig[p];
     __shared__ float s_org[3];
+    __shared__ uint32_t s_mask[kTileMaskWords];
     if (N < 1 || N > a.max_atoms || nl < 1 || nl > N || a0 < 0) {
         if (threadIdx.x == 0) atomicOr(a.err, FUSION_ERR_INPUT);
         return;
     }
+    for (int w = threadIdx.x; w < kTileMaskWords; w += blockDim.x) s_mask[w] = 0u;
     if (threadIdx.x < 3) {
         const int d = threadIdx.x;
         float s = 0.f;
@@ -79,11 +86,30 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a) {
             }
         }
         a.atom_vox[ai] = make_int4(c3[2], c3[1], c3[0], p);
+        // the 8^3 tiles (of the tiles^3 that cover the grid) that the support cube c +- K meets: the same
+        // test voxelize_kernel's compaction makes, so a tile with a clear bit has no candidate atom
+        const int tiles = (a.grid_n + kTile - 1) / kTile, last = tiles * kTile - 1;
+        int lo[3], hi[3];
+        bool meets = true;
+        for (int d = 0; d < 3; ++d) {
+            const int c = c3[2 - d];                     // z, y, x
+            if (c + K < 0 || c - K > last) meets = false;
+            lo[d] = max(c - K, 0) / kTile;
+            hi[d] = min(c + K, last) / kTile;
+        }
+        if (meets)
+            for (int tz = lo[0]; tz <= hi[0]; ++tz)
+                for (int ty = lo[1]; ty <= hi[1]; ++ty)
+                    for (int tx = lo[2]; tx <= hi[2]; ++tx) {
+                        const int t = (tz * tiles + ty) * tiles + tx;
+                        atomicOr(&s_mask[t >> 5], 1u << (t & 31));
+                    }
     }
     if (bad) atomicOr(a.err, FUSION_ERR_INPUT);
+    __syncthreads();
+    for (int w = threadIdx.x; w < kTileMaskWords; w += blockDim.x) a.tile_mask[(size_t)p * kTileMaskWords + w] = s_mask[w];
 }
 
-constexpr int kTile = 8;
 constexpr int kStage = 256;
 constexpr int kFeatPad = 20;   // staged features per atom: 19 + 1 zero, so a thread reads them as 5 float4
 
@@ -102,6 +128,9 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
     const int N = a.atom_off[p + 1] - a0;
     if (N < 1 || N > a.max_atoms) return;
 
+    // 0. a tile that no atom's support meets holds zeros: store them without scanning the atoms
+    const bool empty = !((a.tile_mask[(size_t)p * kTileMaskWords + (t >> 5)] >> (t & 31)) & 1u);
+
     int4 *s_v = reinterpret_cast<int4 *>(smem);                  // [kStage]
     float *s_w = reinterpret_cast<float *>(s_v + kStage);        // [kStage][3*KW]
     float *s_f = s_w + kStage * 3 * KW;                          // [kStage][20], 16-byte aligned rows
@@ -113,7 +142,7 @@ __global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
 
     // 1. ordered compaction of the atoms whose support cube meets this tile
     int count = 0;
-    for (int base = 0; base < N; base += 512) {
+    for (int base = 0; base < (empty ? 0 : N); base += 512) {
         const int i = base + tid;
         bool hit = false;
         if (i < N) {
