@@ -113,7 +113,9 @@ def conv_flops_per_pose(desc):
 
 
 def launches_per_step(desc):
-    return (2 + len(desc["conv"]) + (1 if desc["pool"] > 1 else 0) + 2 + 1 +
+    # prep + voxelize, the convs, the pool, dense + its reduction, the radius graph (count, scan, fill),
+    # a transform per stage, the steps, the gather, the head
+    return (2 + len(desc["conv"]) + (1 if desc["pool"] > 1 else 0) + 2 + 3 +
             len(desc["sg_stages"]) + sum(s["steps"] for s in desc["sg_stages"]) + 1 + 1)
 
 

@@ -1,11 +1,17 @@
 // Radius graph with two edge types (Section 1: edge types at distinct distance
 // thresholds for covalent and non-covalent interactions; Table II cutoffs).
 //
-// One CTA per pose.  The pose's coordinates go to shared memory, atoms are
-// counting-sorted into a cell list with cells no smaller than the
-// non-covalent cutoff (so every neighbour lies in the 27 surrounding cells),
-// then a count pass, a block-wide exclusive scan and a fill pass write CSR
-// rows, and each row is sorted by neighbour index so the output is canonical.
+// Three launches: a count pass and a fill pass with kGraphSplit CTAs per pose,
+// and between them one CTA per pose that scans the degrees into row offsets.
+// Every CTA of the count and fill passes puts its pose's coordinates in shared
+// memory and counting-sorts them into a cell list with cells no smaller than
+// the non-covalent cutoff (so every neighbour lies in the 27 surrounding cells;
+// the three x-adjacent cells of each of the 9 neighbour rows are contiguous in
+// cell order).  A warp takes one query atom of the CTA's share at a time, its
+// lanes testing the candidates in parallel; the fill pass packs the hits into
+// the row by ballot and then sorts the row by neighbour index, so the output is
+// canonical.  CTAs stay short (tens of microseconds), so on the low-priority
+// stream they never hold an SM for long from the persistent convolutions.
 //
 // Edge test, exact IEEE float32 with no contraction:
 //   s = ((dx*dx + dy*dy) + dz*dz), dx = x_i - x_j (and y, z);
@@ -20,7 +26,8 @@ namespace fusion {
 namespace {
 
 constexpr int kCells = kGridCellsMax * kGridCellsMax * kGridCellsMax;
-constexpr int kThreads = 512;
+constexpr int kThreads = 256;
+constexpr int kGraphSplit = 4;      // CTAs per pose in the count and fill passes
 
 // In-place exclusive scan of d[0..n) by the whole block; returns the total.
 __device__ int block_exscan(int *d, int n, int *s_tmp /* [33] */) {
@@ -64,33 +71,30 @@ __device__ __forceinline__ float dist2_rn(float xi, float yi, float zi, float xj
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
-__global__ void __launch_bounds__(kThreads) radius_graph_kernel(GraphArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int p = blockIdx.x;
-    const int a0 = a.atom_off[p];
-    const int N = a.atom_off[p + 1] - a0;
-    const int MA = a.max_atoms;
-    const int tid = threadIdx.x;
-    if (N < 1 || N > MA || a0 < 0) return;   // flagged by the prep kernel
+// The pose's coordinates and cell list in shared memory, built by every CTA of the pose (linear in N).
+struct CellList {
+    float *sx, *sy, *sz;
+    int *cell, *sorted, *start;
+    int dim[3];
+};
 
-    float *sx = reinterpret_cast<float *>(smem);
-    float *sy = sx + MA;
-    float *sz = sy + MA;
-    int *s_cell = reinterpret_cast<int *>(sz + MA);   // [MA]
-    int *s_sorted = s_cell + MA;                      // [MA] atoms in cell order
-    int *s_d0 = s_sorted + MA;                        // [MA + 1] covalent degree -> offset
-    int *s_d1 = s_d0 + MA + 1;                        // [MA + 1] non-covalent degree -> offset
-    int *s_start = s_d1 + MA + 1;                     // [kCells + 1]
-    int *s_cur = s_start + kCells + 1;                // [kCells]
+__device__ void build_cells(const GraphArgs &a, int a0, int N, unsigned char *smem, CellList &cl) {
+    const int MA = a.max_atoms, tid = threadIdx.x, nt = blockDim.x;
+    cl.sx = reinterpret_cast<float *>(smem);
+    cl.sy = cl.sx + MA;
+    cl.sz = cl.sy + MA;
+    cl.cell = reinterpret_cast<int *>(cl.sz + MA);    // [MA]
+    cl.sorted = cl.cell + MA;                         // [MA] atoms in cell order
+    cl.start = cl.sorted + MA;                        // [kCells + 1]
+    int *cur = cl.start + kCells + 1;                 // [kCells]
     __shared__ float s_red[6][kThreads / 32];
     __shared__ float s_lo[3], s_L[3];
     __shared__ int s_dim[3];
     __shared__ int s_tmp[33];
-
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int i = tid; i < N; i += kThreads) {
+    for (int i = tid; i < N; i += nt) {
         const float x = a.xyz[(size_t)(a0 + i) * 3], y = a.xyz[(size_t)(a0 + i) * 3 + 1], z = a.xyz[(size_t)(a0 + i) * 3 + 2];
-        sx[i] = x; sy[i] = y; sz[i] = z;
+        cl.sx[i] = x; cl.sy[i] = y; cl.sz[i] = z;
         lo[0] = fminf(lo[0], x); lo[1] = fminf(lo[1], y); lo[2] = fminf(lo[2], z);
         hi[0] = fmaxf(hi[0], x); hi[1] = fmaxf(hi[1], y); hi[2] = fmaxf(hi[2], z);
     }
@@ -101,11 +105,11 @@ __global__ void __launch_bounds__(kThreads) radius_graph_kernel(GraphArgs a) {
         }
     if ((tid & 31) == 0)
         for (int d = 0; d < 3; ++d) { s_red[d][tid >> 5] = lo[d]; s_red[3 + d][tid >> 5] = hi[d]; }
-    for (int c = tid; c <= kCells; c += kThreads) s_start[c] = 0;
+    for (int c = tid; c <= kCells; c += nt) cl.start[c] = 0;
     __syncthreads();
     if (tid < 3) {
         float l = INFINITY, h = -INFINITY;
-        for (int w = 0; w < kThreads / 32; ++w) { l = fminf(l, s_red[tid][w]); h = fmaxf(h, s_red[3 + tid][w]); }
+        for (int w = 0; w < nt / 32; ++w) { l = fminf(l, s_red[tid][w]); h = fmaxf(h, s_red[3 + tid][w]); }
         const float ext = h - l;
         float L = a.cut_nc * 1.001f + 1e-4f;
         if (ext / L > (float)(kGridCellsMax - 1)) L = ext / (float)(kGridCellsMax - 1) * 1.001f;
@@ -114,129 +118,210 @@ __global__ void __launch_bounds__(kThreads) radius_graph_kernel(GraphArgs a) {
         s_lo[tid] = l; s_L[tid] = L; s_dim[tid] = dim;
     }
     __syncthreads();
-    for (int i = tid; i < N; i += kThreads) {
-        const int cx = max(0, min((int)((sx[i] - s_lo[0]) / s_L[0]), s_dim[0] - 1));
-        const int cy = max(0, min((int)((sy[i] - s_lo[1]) / s_L[1]), s_dim[1] - 1));
-        const int cz = max(0, min((int)((sz[i] - s_lo[2]) / s_L[2]), s_dim[2] - 1));
+    for (int i = tid; i < N; i += nt) {
+        const int cx = max(0, min((int)((cl.sx[i] - s_lo[0]) / s_L[0]), s_dim[0] - 1));
+        const int cy = max(0, min((int)((cl.sy[i] - s_lo[1]) / s_L[1]), s_dim[1] - 1));
+        const int cz = max(0, min((int)((cl.sz[i] - s_lo[2]) / s_L[2]), s_dim[2] - 1));
         const int c = (cz * s_dim[1] + cy) * s_dim[0] + cx;
-        s_cell[i] = c;
-        atomicAdd(&s_start[c], 1);
+        cl.cell[i] = c;
+        atomicAdd(&cl.start[c], 1);
     }
     __syncthreads();
-    const int ncell = s_dim[0] * s_dim[1] * s_dim[2];
-    block_exscan(s_start, ncell + 1, s_tmp);
-    for (int c = tid; c < ncell; c += kThreads) s_cur[c] = s_start[c];
+    for (int d = 0; d < 3; ++d) cl.dim[d] = s_dim[d];
+    const int ncell = cl.dim[0] * cl.dim[1] * cl.dim[2];
+    block_exscan(cl.start, ncell + 1, s_tmp);
+    for (int c = tid; c < ncell; c += nt) cur[c] = cl.start[c];
     __syncthreads();
-    for (int i = tid; i < N; i += kThreads) {
-        const int pos = atomicAdd(&s_cur[s_cell[i]], 1);
-        s_sorted[pos] = i;
+    for (int i = tid; i < N; i += nt) {
+        const int pos = atomicAdd(&cur[cl.cell[i]], 1);   // order within a cell is arbitrary: rows are sorted later
+        cl.sorted[pos] = i;
     }
     __syncthreads();
+}
 
+// The query atoms of CTA `part` of a pose: a contiguous share of the pose's atoms.
+__device__ __forceinline__ void part_range(int N, int part, int &i0, int &i1) {
+    const int per = (N + kGraphSplit - 1) / kGraphSplit;
+    i0 = min(part * per, N);
+    i1 = min(i0 + per, N);
+}
+
+// Candidate run r (0..8) of atom i: the atoms of the three x-adjacent cells of neighbour row (oz, oy) = (r / 3 - 1,
+// r % 3 - 1), which are contiguous in cell order.  Returns false if the row lies outside the cell grid.
+__device__ __forceinline__ bool cand_run(const CellList &cl, int c, int r, int &q0, int &q1) {
+    const int cx = c % cl.dim[0], cy = (c / cl.dim[0]) % cl.dim[1], cz = c / (cl.dim[0] * cl.dim[1]);
+    const int zz = cz + r / 3 - 1, yy = cy + r % 3 - 1;
+    if (zz < 0 || zz >= cl.dim[2] || yy < 0 || yy >= cl.dim[1]) return false;
+    const int row = (zz * cl.dim[1] + yy) * cl.dim[0];
+    q0 = cl.start[row + max(cx - 1, 0)];
+    q1 = cl.start[row + min(cx + 1, cl.dim[0] - 1) + 1];
+    return true;
+}
+
+// Count pass: a warp per query atom, its lanes over the candidates of the 27 neighbouring cells.
+__global__ void __launch_bounds__(kThreads) radius_count_kernel(GraphArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int p = blockIdx.x / kGraphSplit, part = blockIdx.x % kGraphSplit;
+    const int a0 = a.atom_off[p];
+    const int N = a.atom_off[p + 1] - a0;
+    if (N < 1 || N > a.max_atoms || a0 < 0) return;   // flagged by the prep kernel
+    CellList cl;
+    build_cells(a, a0, N, smem, cl);
     const float c2 = __fmul_rn(a.cut_cov, a.cut_cov);
     const float n2 = __fmul_rn(a.cut_nc, a.cut_nc);
-
-    // count pass
-    for (int i = tid; i < N; i += kThreads) {
-        const int c = s_cell[i];
-        const int cx = c % s_dim[0], cy = (c / s_dim[0]) % s_dim[1], cz = c / (s_dim[0] * s_dim[1]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int i0, i1;
+    part_range(N, part, i0, i1);
+    for (int i = i0 + warp; i < i1; i += kThreads / 32) {
+        const float xi = cl.sx[i], yi = cl.sy[i], zi = cl.sz[i];
         int d0 = 0, d1 = 0;
-        for (int oz = -1; oz <= 1; ++oz) {
-            const int zz = cz + oz;
-            if (zz < 0 || zz >= s_dim[2]) continue;
-            for (int oy = -1; oy <= 1; ++oy) {
-                const int yy = cy + oy;
-                if (yy < 0 || yy >= s_dim[1]) continue;
-                for (int ox = -1; ox <= 1; ++ox) {
-                    const int xx = cx + ox;
-                    if (xx < 0 || xx >= s_dim[0]) continue;
-                    const int cc = (zz * s_dim[1] + yy) * s_dim[0] + xx;
-                    for (int q = s_start[cc]; q < s_start[cc + 1]; ++q) {
-                        const int j = s_sorted[q];
-                        if (j == i) continue;
-                        const float s = dist2_rn(sx[i], sy[i], sz[i], sx[j], sy[j], sz[j]);
-                        if (s < c2) ++d0;
-                        else if (s < n2) ++d1;
-                    }
-                }
+        for (int r = 0; r < 9; ++r) {
+            int q0, q1;
+            if (!cand_run(cl, cl.cell[i], r, q0, q1)) continue;
+            for (int q = q0 + lane; q < q1; q += 32) {
+                const int j = cl.sorted[q];
+                if (j == i) continue;
+                const float s = dist2_rn(xi, yi, zi, cl.sx[j], cl.sy[j], cl.sz[j]);
+                if (s < c2) ++d0;
+                else if (s < n2) ++d1;
             }
         }
-        s_d0[i] = d0;
-        s_d1[i] = d1;
+        for (int o = 16; o > 0; o >>= 1) {
+            d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        }
+        if (lane == 0) { a.deg[0][a0 + i] = d0; a.deg[1][a0 + i] = d1; }
     }
-    if (tid == 0) { s_d0[N] = 0; s_d1[N] = 0; }
-    __syncthreads();
-    const int tot0 = block_exscan(s_d0, N + 1, s_tmp);
-    const int tot1 = block_exscan(s_d1, N + 1, s_tmp);
+}
+
+// Row offsets: one CTA per pose scans the degrees; a pose whose edges of a type exceed N * max_degree raises the
+// capacity flag and gets no edges.
+__global__ void __launch_bounds__(kThreads) radius_scan_kernel(GraphArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int p = blockIdx.x;
+    const int a0 = a.atom_off[p];
+    const int N = a.atom_off[p + 1] - a0;
+    if (N < 1 || N > a.max_atoms || a0 < 0) return;
+    int *s_d = reinterpret_cast<int *>(smem);          // [max_atoms + 1]
+    __shared__ int s_tmp[33];
     const long long cap = (long long)N * a.max_degree;
     const size_t base = (size_t)a0 * a.max_degree;
-    if (tot0 > cap || tot1 > cap) {
-        if (tid == 0) atomicOr(a.err, FUSION_ERR_EDGES);
-        for (int i = tid; i < N; i += kThreads) {
-            a.beg[0][a0 + i] = (int)base; a.deg[0][a0 + i] = 0;
-            a.beg[1][a0 + i] = (int)base; a.deg[1][a0 + i] = 0;
+    for (int e = 0; e < 2; ++e) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) s_d[i] = a.deg[e][a0 + i];
+        if (threadIdx.x == 0) s_d[N] = 0;
+        __syncthreads();
+        const int tot = block_exscan(s_d, N + 1, s_tmp);
+        if (tot > cap) {
+            if (threadIdx.x == 0) atomicOr(a.err, FUSION_ERR_EDGES);
+            for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                for (int f = 0; f < 2; ++f) { a.beg[f][a0 + i] = (int)base; a.deg[f][a0 + i] = 0; }
+            }
+            return;
         }
+        for (int i = threadIdx.x; i < N; i += blockDim.x) a.beg[e][a0 + i] = (int)(base + s_d[i]);
+        __syncthreads();
+    }
+}
+
+// Sort row[0..n) (distinct atom indices) ascending by the warp: each lane ranks up to kRankPerLane elements
+// against the whole row, then all write after all have read; longer rows fall back to one lane's insertion
+// sort.
+constexpr int kRankPerLane = 4;
+__device__ void warp_sort_row(int32_t *row, int n, int lane) {
+    if (n <= 1) return;
+    if (n > 32 * kRankPerLane) {
+        if (lane == 0)
+            for (int u = 1; u < n; ++u) {
+                const int v = row[u];
+                int w = u - 1;
+                while (w >= 0 && row[w] > v) { row[w + 1] = row[w]; --w; }
+                row[w + 1] = v;
+            }
+        __syncwarp();
         return;
     }
+    int val[kRankPerLane], rank[kRankPerLane];
+#pragma unroll
+    for (int t = 0; t < kRankPerLane; ++t) {
+        const int e = lane + 32 * t;
+        val[t] = e < n ? row[e] : 0;
+        rank[t] = 0;
+    }
+    for (int f = 0; f < n; ++f) {
+        const int u = row[f];
+#pragma unroll
+        for (int t = 0; t < kRankPerLane; ++t) rank[t] += (u < val[t]) ? 1 : 0;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < kRankPerLane; ++t)
+        if (lane + 32 * t < n) row[rank[t]] = val[t];
+    __syncwarp();
+}
 
-    // fill pass, then sort each row by neighbour index
-    for (int i = tid; i < N; i += kThreads) {
-        const int c = s_cell[i];
-        const int cx = c % s_dim[0], cy = (c / s_dim[0]) % s_dim[1], cz = c / (s_dim[0] * s_dim[1]);
-        int32_t *r0 = a.col[0] + base + s_d0[i];
-        int32_t *r1 = a.col[1] + base + s_d1[i];
-        const int n0 = s_d0[i + 1] - s_d0[i], n1 = s_d1[i + 1] - s_d1[i];
+// Fill pass: a warp per query atom writes its neighbours into the row the scan placed (hits in candidate order,
+// packed by ballot), then sorts each row by neighbour index so the output is canonical.
+__global__ void __launch_bounds__(kThreads) radius_fill_kernel(GraphArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int p = blockIdx.x / kGraphSplit, part = blockIdx.x % kGraphSplit;
+    const int a0 = a.atom_off[p];
+    const int N = a.atom_off[p + 1] - a0;
+    if (N < 1 || N > a.max_atoms || a0 < 0) return;
+    CellList cl;
+    build_cells(a, a0, N, smem, cl);
+    const float c2 = __fmul_rn(a.cut_cov, a.cut_cov);
+    const float n2 = __fmul_rn(a.cut_nc, a.cut_nc);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int i0, i1;
+    part_range(N, part, i0, i1);
+    for (int i = i0 + warp; i < i1; i += kThreads / 32) {
+        const int n0 = a.deg[0][a0 + i], n1 = a.deg[1][a0 + i];   // 0 for a pose over capacity
+        int32_t *r0 = a.col[0] + a.beg[0][a0 + i];
+        int32_t *r1 = a.col[1] + a.beg[1][a0 + i];
+        const float xi = cl.sx[i], yi = cl.sy[i], zi = cl.sz[i];
         int k0 = 0, k1 = 0;
-        for (int oz = -1; oz <= 1; ++oz) {
-            const int zz = cz + oz;
-            if (zz < 0 || zz >= s_dim[2]) continue;
-            for (int oy = -1; oy <= 1; ++oy) {
-                const int yy = cy + oy;
-                if (yy < 0 || yy >= s_dim[1]) continue;
-                for (int ox = -1; ox <= 1; ++ox) {
-                    const int xx = cx + ox;
-                    if (xx < 0 || xx >= s_dim[0]) continue;
-                    const int cc = (zz * s_dim[1] + yy) * s_dim[0] + xx;
-                    for (int q = s_start[cc]; q < s_start[cc + 1]; ++q) {
-                        const int j = s_sorted[q];
-                        if (j == i) continue;
-                        const float s = dist2_rn(sx[i], sy[i], sz[i], sx[j], sy[j], sz[j]);
-                        if (s < c2) { if (k0 < n0) r0[k0++] = a0 + j; }
-                        else if (s < n2) { if (k1 < n1) r1[k1++] = a0 + j; }
+        for (int r = 0; r < 9; ++r) {
+            int q0, q1;
+            if (!cand_run(cl, cl.cell[i], r, q0, q1)) continue;
+            for (int qb = q0; qb < q1; qb += 32) {
+                const int q = qb + lane;
+                bool h0 = false, h1 = false;
+                int j = 0;
+                if (q < q1) {
+                    j = cl.sorted[q];
+                    if (j != i) {
+                        const float s = dist2_rn(xi, yi, zi, cl.sx[j], cl.sy[j], cl.sz[j]);
+                        h0 = s < c2;
+                        h1 = !h0 && s < n2;
                     }
                 }
+                const unsigned b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
+                if (h0 && k0 + __popc(b0 & below) < n0) r0[k0 + __popc(b0 & below)] = a0 + j;
+                if (h1 && k1 + __popc(b1 & below) < n1) r1[k1 + __popc(b1 & below)] = a0 + j;
+                k0 += __popc(b0);
+                k1 += __popc(b1);
             }
         }
-        for (int u = 1; u < n0; ++u) {
-            const int v = r0[u];
-            int w = u - 1;
-            while (w >= 0 && r0[w] > v) { r0[w + 1] = r0[w]; --w; }
-            r0[w + 1] = v;
-        }
-        for (int u = 1; u < n1; ++u) {
-            const int v = r1[u];
-            int w = u - 1;
-            while (w >= 0 && r1[w] > v) { r1[w + 1] = r1[w]; --w; }
-            r1[w + 1] = v;
-        }
-        a.beg[0][a0 + i] = (int)(base + s_d0[i]);
-        a.deg[0][a0 + i] = n0;
-        a.beg[1][a0 + i] = (int)(base + s_d1[i]);
-        a.deg[1][a0 + i] = n1;
+        __syncwarp();
+        warp_sort_row(r0, n0, lane);
+        warp_sort_row(r1, n1, lane);
     }
 }
 
 }  // namespace
 
 size_t radius_graph_smem(int max_atoms) {
-    return (size_t)max_atoms * 3 * 4 + (size_t)max_atoms * 2 * 4 + (size_t)(max_atoms + 1) * 2 * 4 +
-           (size_t)(kCells + 1) * 4 + (size_t)kCells * 4;
+    return (size_t)max_atoms * 3 * 4 + (size_t)max_atoms * 2 * 4 + (size_t)(kCells + 1) * 4 + (size_t)kCells * 4;
 }
 
 void launch_radius_graph(const GraphArgs &a, cudaStream_t s) {
     const size_t sm = radius_graph_smem(a.max_atoms);
-    cudaFuncSetAttribute(radius_graph_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    radius_graph_kernel<<<a.n_poses, kThreads, sm, s>>>(a);
+    cudaFuncSetAttribute(radius_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(radius_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    radius_count_kernel<<<a.n_poses * kGraphSplit, kThreads, sm, s>>>(a);
+    radius_scan_kernel<<<a.n_poses, kThreads, (size_t)(a.max_atoms + 1) * 4, s>>>(a);
+    radius_fill_kernel<<<a.n_poses * kGraphSplit, kThreads, sm, s>>>(a);
 }
 
 }  // namespace fusion
