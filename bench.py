@@ -377,7 +377,7 @@ def run_ours(args):
         "stage_ms": {k: round(v, 4) for k, v in stage_mean.items() if v > 0},
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": (launches_per_step(desc) + (1 + len(desc["conv"]) if args.dtype == "fp8" else 0) +
+        "gpu_launches": (launches_per_step(desc) + (len(desc["conv"]) if args.dtype == "fp8" else 0) +
                          (1 if args.dtype == "bf16" and grid_folded(desc) else 0)) * args.steps,
         "clocks": clk,
         "affinity_std": float(out.float().std().item()),

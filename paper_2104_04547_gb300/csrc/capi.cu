@@ -874,7 +874,10 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     RC(check_launch("sg_gather"));
     sg_mark(3);
     VoxArgs va{off_d, feat_d, m->atom_vox, m->atom_w, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx,
-               m->bf16 ? 1 : 0, m->grid_fold, bf16_blocked_in(m, 0) ? 1 : 0, m->tile_mask};
+               m->bf16 ? 1 : 0, m->grid_fold, bf16_blocked_in(m, 0) ? 1 : 0, m->tile_mask,
+               m->fp8 ? m->amax : nullptr};
+    // FP8: voxelize also reduces each pose's max |grid value| (the first layer's input scale)
+    if (m->fp8) CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
     launch_voxelize(va, st);
     RC(check_launch("voxelize"));
     map[1] = ei; mark(st);
@@ -884,13 +887,8 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     for (int i = 0; i < d.n_conv; ++i) {
         const fusion_conv_desc &c = d.conv[i];
         if (m->fp8) {
-            // quantize this layer's bf16 input per pose, then run the FP8 conv
-            const Shape si = conv_out(d, i);
-            const size_t per_pose = (size_t)si.n * si.n * si.n * m->conv[i].cx_in;
-            if (i == 0) {
-                CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
-                launch_amax_per_pose(m->grid, B, per_pose, m->amax, st);
-            }
+            // quantize this layer's bf16 input per pose (its per-pose max comes from voxelize or from the
+            // previous layer's epilogue), then run the FP8 conv
             quantize_conv_input(m, i, x, B, st);
             CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
             conv_tc_launch(m->tcplan[i], B, st);

@@ -60,6 +60,7 @@ struct VoxArgs {
                           // (s = 0..4, zero outside the grid), channel 31 zero
     int blocked;          // bf16 only: store channel-blocked, [B][n][n][cx / 8][n][8]
     const uint32_t *tile_mask;   // PrepArgs::tile_mask: a tile whose bit is clear stores zeros at once
+    float *amax;          // bf16 only, may be null: per-pose max |stored value| (atomic max; zeroed by the caller)
 };
 void launch_voxelize(const VoxArgs &a, cudaStream_t s);
 

@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(512, 3) voxelize_kernel(VoxArgs a) {
     }
 
     // 3. store the voxel's channel vector (channels >= 19 are zero padding)
+    float vmax = 0.f;                                   // max |stored bf16 value| of this voxel
     if (vx < n && vy < n && vz < n) {
         const size_t vox = (((size_t)p * n + vz) * n + vy) * n + vx;
         if constexpr (BF16) {
@@ -243,7 +244,10 @@ __global__ void __launch_bounds__(512, 3) voxelize_kernel(VoxArgs a) {
                 for (int c0 = 0; c0 < CX; c0 += 8) {
                     __align__(16) __nv_bfloat16 v8[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) v8[j] = __float2bfloat16_rn(c0 + j < kFeat ? acc[c0 + j] : 0.f);
+                    for (int j = 0; j < 8; ++j) {
+                        v8[j] = __float2bfloat16_rn(c0 + j < kFeat ? acc[c0 + j] : 0.f);
+                        vmax = fmaxf(vmax, fabsf(__bfloat162float(v8[j])));
+                    }
                     *reinterpret_cast<uint4 *>(blk(c0)) = *reinterpret_cast<const uint4 *>(v8);
                 }
             } else {
@@ -261,6 +265,7 @@ __global__ void __launch_bounds__(512, 3) voxelize_kernel(VoxArgs a) {
                         const float v = c < 16 ? acc[c < 16 ? c : 0]
                                                : d == 0 ? acc[16] : d == 1 ? acc[17] : d == 2 ? acc[18] : 0.f;
                         v8[j] = __float2bfloat16_rn(v);
+                        vmax = fmaxf(vmax, fabsf(__bfloat162float(v8[j])));
                     }
                     *reinterpret_cast<uint4 *>(blk(c0)) = *reinterpret_cast<const uint4 *>(v8);
                 }
@@ -276,6 +281,18 @@ __global__ void __launch_bounds__(512, 3) voxelize_kernel(VoxArgs a) {
                 v4.w = c0 + 3 < kFeat ? acc[c0 + 3] : 0.f;
                 *reinterpret_cast<float4 *>(out + c0) = v4;
             }
+        }
+    }
+    if (a.amax) {
+        // the pose's max |grid value| for the FP8 input scale: warps, then one atomic per CTA
+        __shared__ float s_wmax[16];
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if (lane == 0) s_wmax[warp] = vmax;
+        __syncthreads();
+        if (tid == 0) {
+            float m = 0.f;
+            for (int w = 0; w < 16; ++w) m = fmaxf(m, s_wmax[w]);
+            if (m > 0.f) atomicMax(reinterpret_cast<unsigned *>(a.amax + p), __float_as_uint(m));
         }
     }
 }
