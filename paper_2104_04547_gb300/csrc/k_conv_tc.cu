@@ -93,6 +93,7 @@ namespace fusion {
 namespace {
 
 constexpr int kIssReq = 4;
+constexpr int kRing = 4;     // tile indices the producer publishes ahead of the issuers and the epilogue
 
 // Warp roles of one kernel instance: warp 0 loads, warps 1..NI issue MMAs, then 4 x EPW epilogue warps
 // (EPW per tensor-memory lane quarter, each holding PART columns of a slice group).
@@ -145,6 +146,7 @@ struct Args {
     int res_blocked;            // xres is channel-blocked: [pose][z][y][cres / 8][x][8]
     Geo g;
     unsigned *err;
+    int *tile_counter;          // tiles handed out beyond each CTA's first (zeroed before every launch)
 };
 
 __device__ __forceinline__ void phase_taps(const Args &a, int ph, int &pz, int &py, int &px, int &nz, int &ny,
@@ -186,7 +188,10 @@ __global__ void __launch_bounds__(Roles<N, T, G>::THREADS, 1) conv3d_tc_kernel(c
     uint64_t *acc_full = b_empty + g.nbs;   // [UNITS]: the tile's MMAs of the group are complete
     uint64_t *acc_empty = acc_full + UNITS; // [UNITS]: the epilogue has read and re-zeroed the group
     uint64_t *mma_done = acc_empty + UNITS;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
+    uint64_t *tile_full = mma_done + 1;        // [kRing]: ring slot holds the next tile index (or -1: done)
+    uint64_t *tile_empty = tile_full + kRing;  // [kRing]: every issuer and epilogue warp has read the slot
+    int *tile_ring = reinterpret_cast<int *>(tile_empty + kRing);   // [kRing]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tile_ring + kRing);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -203,6 +208,7 @@ __global__ void __launch_bounds__(Roles<N, T, G>::THREADS, 1) conv3d_tc_kernel(c
         for (int i = 0; i < g.nbs; ++i) { tc::mbar_init(&b_full[i], 1); tc::mbar_init(&b_empty[i], NI); }
         for (int u = 0; u < UNITS; ++u) { tc::mbar_init(&acc_full[u], 1); tc::mbar_init(&acc_empty[u], 4 * EPW); }
         tc::mbar_init(mma_done, NI);
+        for (int i = 0; i < kRing; ++i) { tc::mbar_init(&tile_full[i], 1); tc::mbar_init(&tile_empty[i], NI + 4 * EPW); }
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -227,15 +233,24 @@ __global__ void __launch_bounds__(Roles<N, T, G>::THREADS, 1) conv3d_tc_kernel(c
         atomicOr(a.err, FUSION_ERR_TIMEOUT);
     };
 
-    // Tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...  Every wait's deadline is re-armed per tile.
+    // Tiles: a CTA's first is blockIdx.x; the producer takes each further one from a global counter (so a CTA
+    // that started late, its SM still busy with another kernel, takes fewer) and publishes every tile index,
+    // then -1, through the ring to the issuers and the epilogue.  Every wait's deadline is re-armed per tile.
     int prod_ai = 0, prod_bi = 0;
     if (warp == 0 && lane == 0) {
         // ---------------- producer ----------------
         int &ai = prod_ai, &bi = prod_bi;
-        for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag && !a.stall; tile += gridDim.x) {
+        int tile = blockIdx.x;
+        for (int k = 0;; ++k) {
+            const uint64_t deadline = tc::globaltimer() + kWaitNs;
+            const int slot = k % kRing;
+            if (!tc::mbar_wait(&tile_empty[slot], ((k / kRing) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
+            const bool done = tile >= n_tiles || *abort_flag;
+            tile_ring[slot] = done ? -1 : tile;
+            tc::mbar_arrive(&tile_full[slot]);           // release: the ring entry is visible to the waiters
+            if (done || a.stall) break;                  // stall test: publish the first tile, load nothing
             int x0, y0, z0, b;
             decode(tile, x0, y0, z0, b);
-            const uint64_t deadline = tc::globaltimer() + kWaitNs;
             const uint8_t *wc = a.w;     // weights are consumed in storage order: chunk, phase, (ty, tx) group
             for (int c = 0; c < g.chunks && !*abort_flag; ++c) {
                 for (int ph = 0; ph < g.nphase && !*abort_flag; ++ph) {
@@ -271,15 +286,21 @@ __global__ void __launch_bounds__(Roles<N, T, G>::THREADS, 1) conv3d_tc_kernel(c
                     wc += (size_t)ngr * gbytes;
                 }
             }
+            tile = atomicAdd(a.tile_counter, 1) + (int)gridDim.x;
         }
     } else if (warp >= 1 && warp <= NI && lane == 0) {
         const int d0 = (warp - 1) * DPI;
         // ---------------- MMA issuer ----------------
-        int ai = 0, bi = 0, it = 0;
+        int ai = 0, bi = 0;
         const uint32_t sbo_a = (uint32_t)g.ystep * 16;
         const uint32_t row_zy = (uint32_t)g.hh * g.ystep;
-        for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x, ++it) {
+        for (int it = 0;; ++it) {
             const uint64_t deadline = tc::globaltimer() + kWaitNs;
+            const int slot = it % kRing;
+            if (!tc::mbar_wait(&tile_full[slot], (it / kRing) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
+            const int tile = tile_ring[slot];
+            tc::mbar_arrive(&tile_empty[slot]);
+            if (tile < 0 || *abort_flag) break;
             // this warp's slice groups must have been read (and re-zeroed) by the previous tile's epilogue
             bool ok = true;
             for (int dd = 0; dd < DPI && ok; ++dd)
@@ -347,11 +368,23 @@ __global__ void __launch_bounds__(Roles<N, T, G>::THREADS, 1) conv3d_tc_kernel(c
         const int r = q * 32 + lane;            // M row = voxel of the slice
         const int h = r >> 3, w = r & 7;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        int it = 0;
-        for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x, ++it) {
+        for (int it = 0;; ++it) {
+            const uint64_t deadline = tc::globaltimer() + kWaitNs;
+            // lane 0 takes the tile index from the ring; the warp follows its answer
+            const int slot = it % kRing;
+            int tile = -1;
+            if (lane == 0) {
+                if (tc::mbar_wait(&tile_full[slot], (it / kRing) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) {
+                    tile = tile_ring[slot];
+                    tc::mbar_arrive(&tile_empty[slot]);
+                } else {
+                    fail();
+                }
+            }
+            tile = __shfl_sync(0xffffffffu, tile, 0);
+            if (tile < 0 || __any_sync(0xffffffffu, *abort_flag != 0)) break;
             int x0, y0, z0, b;
             decode(tile, x0, y0, z0, b);
-            const uint64_t deadline = tc::globaltimer() + kWaitNs;
             const int yy = y0 + h, xx = x0 + w;
             const float sx = F8 ? a.s_in[b] : 1.f;
             // element offset of channel c of this thread's voxel in slice zz, NDHWC or channel-blocked
@@ -383,9 +416,11 @@ __global__ void __launch_bounds__(Roles<N, T, G>::THREADS, 1) conv3d_tc_kernel(c
             float vmax = 0.f;
             bool ok = true;
             for (int u = 0; u < UNITS && ok; ++u) {
+                // every lane waits (each acquires), and the warp goes on only if all succeeded and nobody gave up:
+                // the tensor-memory loads below must be executed by all 32 lanes or by none
                 ok = tc::mbar_wait(&acc_full[u], it & 1, deadline, a.err, FUSION_ERR_TIMEOUT);
-                if (!ok) { fail(); break; }
-                if (*abort_flag) { ok = false; break; }   // the issuers gave up: nothing valid to store
+                ok = __all_sync(0xffffffffu, ok) && !__any_sync(0xffffffffu, *abort_flag != 0);
+                if (!ok) { if (lane == 0) fail(); break; }
                 tc::tc_fence_after();
                 // read this warp's columns of the group, zero them for the next tile and hand them back
                 // before any arithmetic, so the next tile's MMAs into the group wait only for the reads
@@ -499,6 +534,8 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 struct ConvTcPlan::Impl {
     CUtensorMap tmap;
     Args args;
+    int *counter = nullptr;     // device: the launch's tile counter
+    ~Impl() { if (counter) cudaFree(counter); }
     int N = 0, T = 0;
     bool f8 = false;
     int group = 1;          // output slices per MMA
@@ -761,8 +798,8 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     }
     g.chunks = sp.cin_pad / chunk_ch;
     // a_full/a_empty [2] each, b_full/b_empty [nbs] each, acc_full/acc_empty [T / group] each, mma_done,
-    // then the tensor-memory slot and the abort flag
-    const size_t bar_bytes = (size_t)(4 + 2 * g.nbs + 2 * (T / group) + 1) * 8 + 16;
+    // tile_full/tile_empty [kRing] each, the tile ring, then the tensor-memory slot and the abort flag
+    const size_t bar_bytes = (size_t)(4 + 2 * g.nbs + 2 * (T / group) + 1 + 2 * kRing) * 8 + kRing * 4 + 16;
     const size_t limit = 227 * 1024;
     const size_t b_total = (size_t)g.nbs * g.stage_bytes;
     const size_t a1 = g.a_bytes;
@@ -840,6 +877,12 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
         return -2;
     }
     P.sms = sms;
+    if (!P.counter && cudaMalloc(&P.counter, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(why, why_len, "cannot allocate the tile counter");
+        return -2;
+    }
+    A.tile_counter = P.counter;
     return 0;
 }
 
@@ -850,6 +893,7 @@ static void launch_t(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
     P.args.B = B;
     const unsigned tiles = P.grid * (unsigned)B;
     const unsigned grid = tiles < (unsigned)P.sms ? tiles : (unsigned)P.sms;
+    cudaMemsetAsync(P.counter, 0, sizeof(int), s);
     conv3d_tc_kernel<N, T, F8, G><<<grid, Roles<N, T, G>::THREADS, P.smem, s>>>(P.tmap, P.args);
 }
 
