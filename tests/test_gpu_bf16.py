@@ -12,9 +12,8 @@
 
 import numpy as np
 import pytest
-import torch
 
-from gpu_common import golden, require_gpu, split_csr
+from gpu_common import check_layer_bf16, golden, layers_in_isolation, require_gpu, split_csr
 from oracle import fusion_oracle as O
 from synth import configs, poses, weights
 
@@ -28,33 +27,8 @@ def F():
     return require_gpu()
 
 
-def _bf16(a):
-    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64)
-
-
-def _check_layer(x_in, W, b, cv, y_gpu):
-    """x_in: [n][n][n][C] float (exact bf16 values); y_gpu: [m][m][m][Co]."""
-    x = np.asarray(x_in, dtype=np.float64)
-    wb = _bf16(W).numpy()
-    ref = np.maximum(O.conv3d(x, wb, b.astype(np.float64), cv["stride"]), 0.0)
-    if cv["residual"]:
-        ref = ref + x
-    scale = float(np.abs(ref).max()) + 1e-12
-    err = np.abs(y_gpu - ref)
-    assert np.all(err <= 8e-3 * np.abs(ref) + 2e-3 * scale), (float(err.max()), scale)
-
-
 def _layers_in_isolation(F, m, desc, W, p, layers=None):
-    grid = m.fetch(F.STAGE_GRID, p)
-    n = desc["grid_n"]
-    x = grid.reshape(n, n, n, 19)
-    for i, cv in enumerate(desc["conv"]):
-        y = m.fetch(F.STAGE_CONV, (i << 16) | p)
-        side = round((y.size // cv["c_out"]) ** (1 / 3))
-        y = y.reshape(side, side, side, cv["c_out"])
-        if layers is None or i in layers:
-            _check_layer(x, W[f"conv{i}.w"], W[f"conv{i}.b"], cv, y)
-        x = y
+    layers_in_isolation(F, m, desc, W, p, check_layer_bf16, layers)
 
 
 def test_tiny_bf16(F):

@@ -12,9 +12,8 @@ weight scales and per-pose activation scales, through the C ABI.
 
 import numpy as np
 import pytest
-import torch
 
-from gpu_common import golden, require_gpu
+from gpu_common import check_layer_fp8, golden, require_gpu
 from oracle import fusion_oracle as O
 from synth import configs, poses, weights
 
@@ -28,25 +27,6 @@ def F():
     return require_gpu()
 
 
-def _e4m3(a):
-    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
-
-
-def _check_layer_fp8(x_bf16, W, b, cv, y_gpu):
-    x = np.asarray(x_bf16, dtype=np.float64)
-    s_in = np.abs(x).max() / 448.0
-    xq = _e4m3(x / s_in) * s_in
-    co = W.shape[0]
-    sw = np.abs(W.reshape(co, -1)).max(axis=1) / 448.0
-    wq = _e4m3(W / sw[:, None, None, None, None]) * sw[:, None, None, None, None]
-    ref = np.maximum(O.conv3d(xq, wq, b.astype(np.float64), cv["stride"]), 0.0)
-    if cv["residual"]:
-        ref = ref + x
-    scale = float(np.abs(ref).max()) + 1e-12
-    err = float(np.abs(y_gpu - ref).max())
-    assert err <= 2e-2 * scale, (err, scale)
-
-
 def test_tiny_fp8(F):
     desc = configs.model("fusion-24grid-c32", dtype="fp8")
     W = weights.init_weights(desc, 0)
@@ -58,7 +38,7 @@ def test_tiny_fp8(F):
     n = desc["grid_n"]
     x = m.fetch(F.STAGE_GRID, 0).reshape(n, n, n, 19)
     y = m.fetch(F.STAGE_CONV, 0).reshape(n, n, n, 32)
-    _check_layer_fp8(x, W["conv0.w"], W["conv0.b"], desc["conv"][0], y)
+    check_layer_fp8(x, W["conv0.w"], W["conv0.b"], desc["conv"][0], y)
     assert abs(float(got[0]) - exp) <= FP8_AFFINITY_TOL, (got[0], exp)
 
 
@@ -90,7 +70,7 @@ def test_full_size_fp8(F):
     # the first residual layer of pose 7 in isolation
     x = m.fetch(F.STAGE_CONV, (0 << 16) | 7).reshape(48, 48, 48, 64)
     y = m.fetch(F.STAGE_CONV, (1 << 16) | 7).reshape(48, 48, 48, 64)
-    _check_layer_fp8(x, W["conv1.w"], W["conv1.b"], desc["conv"][1], y)
+    check_layer_fp8(x, W["conv1.w"], W["conv1.b"], desc["conv"][1], y)
     d32 = configs.model("fusion-48grid-c64", dtype="f32")
     m32 = F.Model(d32, weights.to_blob(d32, W), max_poses=64, max_atoms=1200)
     ref32 = m32.score(batch)
