@@ -61,13 +61,16 @@
 // |output| so the next layer's input can be quantized with its own scale.
 //
 // Persistent schedule: one CTA per multiprocessor (the tile's shared memory
-// allows one), tiles taken round robin.  Roles: warp 0 lane 0 issues the TMA
+// allows one); a CTA's first tile is its block index and the producer takes
+// each further one from a global counter, passing the index on to the other
+// roles through a small ring in shared memory.  Roles: warp 0 lane 0 issues the TMA
 // loads, running ahead into the next tile while the current one finishes;
 // warp 1 owns tensor memory; lane 0 of warps 1..NI issues the MMAs of its share
 // of the slice groups (one issuing thread was measured to limit the MMA rate,
 // so several warps issue; each commits its own MMAs and the empty barriers
 // count NI arrivals); the remaining 4 x EPW warps run the epilogue (tensor
-// memory -> registers, bias, ReLU, residual add, bf16 NDHWC stores), EPW per
+// memory -> registers, bias, ReLU, residual add, bf16 stores in NDHWC or
+// channel-blocked order), EPW per
 // tensor-memory lane quarter (a warp reaches only the lanes of quarter
 // warp % 4), each holding up to 128 columns of a slice group: two per quarter
 // when a group spans 256 columns, so a group is read in one pass.  Each
@@ -889,7 +892,7 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
 template <int N, int T, bool F8, int G>
 static void launch_t(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
     cudaFuncSetAttribute(conv3d_tc_kernel<N, T, F8, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
-    // persistent: one CTA per multiprocessor (one fits at this shared-memory size), tiles round robin
+    // persistent: one CTA per multiprocessor (one fits at this shared-memory size); tiles from the counter
     P.args.B = B;
     const unsigned tiles = P.grid * (unsigned)B;
     const unsigned grid = tiles < (unsigned)P.sms ? tiles : (unsigned)P.sms;
