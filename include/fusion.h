@@ -206,6 +206,12 @@ int fusion_last_timings(fusion_model *m, float *out, int32_t n);
                                             normal.  Nothing faults or hangs.  FUSION_EUNSUPPORTED on the
                                             FP32 path or with CUDA graphs on */
 
+#define FUSION_OPT_GRAPH_NODES_PER_WARP 4   /* graph convolution (gated graph steps and stage transforms):
+                                               value 1, 2, 4 or 8 nodes per warp, each weight load serving
+                                               them all; -1 = the default, 4.  Every node's sums keep their
+                                               order, so scores are the same for every value.  Drops
+                                               captured graphs.  Any dtype */
+
 /* Set a runtime option of a model (FUSION_OPT_*). */
 int fusion_set_option(fusion_model *m, int32_t option, int64_t value);
 
@@ -213,10 +219,16 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value);
  * fastest tile configuration (output slices per CTA, output slices per MMA,
  * kernel-offset groups per weight stage, weight stages) by timing
  * every configuration that fits shared memory on the given batch (scored once
- * first).  Every configuration sums each output in the same order, so the
- * scores do not change.  Replaces the layer plans;
+ * first), then the graph convolution's nodes per warp (1, 2, 4, 8) by timing
+ * whole scoring calls of the batch, since that branch runs beside the
+ * convolutions.  Every configuration sums each output in the same order, so
+ * the scores do not change.  Replaces the layer plans and the graph schedule;
  * captured graphs are dropped.  FUSION_EUNSUPPORTED on the FP32 path. */
 int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses);
+
+/* The graph convolution's current nodes per warp (FUSION_OPT_GRAPH_NODES_PER_WARP, or the autotuner's
+ * choice) into *nodes_per_warp.  FUSION_EINVAL on NULL arguments. */
+int fusion_graph_schedule(fusion_model *m, int32_t *nodes_per_warp);
 
 /* Tile configuration of conv `layer`: out5 = {output slices per CTA, (ty, tx)
  * kernel-offset groups per weight stage, weight stages, shared-memory bytes,

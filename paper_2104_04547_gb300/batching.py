@@ -98,7 +98,8 @@ def run(args):
     m.use_cuda_graphs(True)
     timed("cuda graphs")
     m.autotune(packed[len(packed) // 2])
-    print(json.dumps({**base, "autotuned_tiles": m.conv_tiles()}), flush=True)
+    print(json.dumps({**base, "autotuned_tiles": m.conv_tiles(), "graph_nodes_per_warp": m.graph_nodes_per_warp()}),
+          flush=True)
     timed("cuda graphs + autotuned tiles")
     # per-compound ranking as the paper does it: each ligand's strongest affinity over its 10 poses
     aff = np.empty(len(pool), dtype=np.float32)

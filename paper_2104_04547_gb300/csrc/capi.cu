@@ -273,6 +273,7 @@ struct fusion_model {
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr, cnn_join_ev = nullptr, ev_sg[4] = {};
     bool use_graph = false;                       // replay captured CUDA graphs, one per batch size
     int group_mode = -1;                          // conv output slices per MMA: -1 default per layer, or 1, 2, 4
+    int sg_npw = 4;                               // graph convolution: nodes per warp (1, 2, 4, 8)
     std::map<int, cudaGraphExec_t> graph_exec;
     std::map<int, cudaGraph_t> graph;
 
@@ -825,6 +826,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
         ta.H = H;
         ta.init = (s == 0);
         ta.A_dev = A_dev;
+        ta.nodes_per_warp = m->sg_npw;
         ta.h_in = h;            // read row by row before the same row of xin is written
         ta.h_out = m->xin;
         if (s > 0 && d.sg_gate) {
@@ -859,6 +861,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
             sa.A = A;
             sa.H = H;
             sa.A_dev = A_dev;
+            sa.nodes_per_warp = m->sg_npw;
             launch_sg_step(sa, sgs);
             RC(check_launch("sg_step"));
             h = hout;
@@ -1248,6 +1251,12 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
         conv_tc_stall_next(m->tcplan[0]);
         return FUSION_OK;
     }
+    case FUSION_OPT_GRAPH_NODES_PER_WARP:
+        if (value != -1 && value != 1 && value != 2 && value != 4 && value != 8)
+            return fail(FUSION_EINVAL, "graph nodes per warp must be -1 (default), 1, 2, 4 or 8");
+        m->sg_npw = value == -1 ? 4 : (int)value;
+        drop_graphs(m);
+        return FUSION_OK;
     case FUSION_OPT_CONV_SLICES_PER_MMA: {
         if (value != -1 && value != 1 && value != 2 && value != 4)
             return fail(FUSION_EINVAL, "slices per MMA must be -1 (default), 1, 2 or 4");
@@ -1313,9 +1322,12 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
     if (poses->on_device) {
         CU(cudaMalloc(&dout, sizeof(float) * std::max(1, n_poses)));
     }
-    const int rc = fusion_score(m, poses, n_poses, poses->on_device ? dout : out.data());
-    if (dout) cudaFree(dout);
-    if (rc) return rc;
+    struct Free {
+        float *p;
+        ~Free() { if (p) cudaFree(p); }
+    } free_dout{dout};
+    float *const score_out = poses->on_device ? dout : out.data();
+    RC(fusion_score(m, poses, n_poses, score_out));
     const fusion_model_desc &d = m->d;
     const int B = n_poses;
     cudaStream_t st = m->stream;
@@ -1374,6 +1386,36 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
         if (conv_tc_plan(m->tcplan[i], sp, why, sizeof(why))) return fail(FUSION_ECUDA, why);
     }
     drop_graphs(m);
+
+    // graph convolution: nodes per warp, by the whole call's device time (the branch runs beside the
+    // convolutions, so its own kernel time is not what counts); median of 5 calls after one untimed
+    const bool graphs = m->use_graph;
+    m->use_graph = false;
+    float best_total = 1e30f;
+    int best_npw = 4;
+    for (int npw : {4, 8, 2, 1}) {
+        m->sg_npw = npw;
+        RC(fusion_score(m, poses, n_poses, score_out));
+        std::vector<float> tot;
+        for (int r = 0; r < 5; ++r) {
+            RC(fusion_score(m, poses, n_poses, score_out));
+            tot.push_back(m->last_ms[16]);
+        }
+        std::sort(tot.begin(), tot.end());
+        if (tot[2] < best_total) {
+            best_total = tot[2];
+            best_npw = npw;
+        }
+    }
+    m->sg_npw = best_npw;
+    m->use_graph = graphs;
+    drop_graphs(m);
+    return FUSION_OK;
+}
+
+int fusion_graph_schedule(fusion_model *m, int32_t *nodes_per_warp) {
+    if (!m || !nodes_per_warp) return fail(FUSION_EINVAL, "NULL argument");
+    *nodes_per_warp = m->sg_npw;
     return FUSION_OK;
 }
 

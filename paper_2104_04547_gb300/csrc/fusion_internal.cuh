@@ -212,6 +212,7 @@ struct SgTransformArgs {
     int A, H;
     int init;              // 1: stage input = h0 (features zero-padded to H)
     const int32_t *A_dev;  // non-null: the atom count is *A_dev (A is then the launch capacity)
+    int nodes_per_warp;    // 1, 2, 4 or 8 (anything else: 4); the results do not depend on it
 };
 void launch_sg_transform(const SgTransformArgs &a, cudaStream_t s);
 
@@ -225,6 +226,7 @@ struct SgStepArgs {
     const float *we_t[2], *be[2];               // for T_out
     int A, H;
     const int32_t *A_dev;  // non-null: the atom count is *A_dev (A is then the launch capacity)
+    int nodes_per_warp;    // 1, 2, 4 or 8 (anything else: 4); the results do not depend on it
 };
 void launch_sg_step(const SgStepArgs &a, cudaStream_t s);
 

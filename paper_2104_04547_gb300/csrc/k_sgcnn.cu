@@ -27,15 +27,13 @@ constexpr int kWarps = 8;
 
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
 
-// A warp takes kNodesPerWarp consecutive nodes: the matrix-vector products load each weight once for all
-// of them (weights are read from L1, and that read bounds these kernels), while every node's sums keep the
-// order of a warp per node.
-constexpr int kNodesPerWarp = 4;
+// A warp takes NP consecutive nodes (1, 2, 4 or 8; SgStepArgs::nodes_per_warp): the matrix-vector products
+// load each weight once for all of them (weights are read from L1, and that read bounds these kernels),
+// while every node's sums keep the order of a warp per node, so the results do not depend on NP.
 
-template <int H>
+template <int H, int NP>
 __global__ void __launch_bounds__(kWarps * 32) sg_transform_kernel(SgTransformArgs a) {
     constexpr int HJ = H / 32;
-    constexpr int NP = kNodesPerWarp;
     __shared__ float sv[kWarps][NP][2 * H];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int A = a.A_dev ? *a.A_dev : a.A;
@@ -111,10 +109,9 @@ __global__ void __launch_bounds__(kWarps * 32) sg_transform_kernel(SgTransformAr
     }
 }
 
-template <int H>
+template <int H, int NP>
 __global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
     constexpr int HJ = H / 32;
-    constexpr int NP = kNodesPerWarp;
     __shared__ float sv[kWarps][NP][2 * H];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int A = a.A_dev ? *a.A_dev : a.A;
@@ -271,16 +268,46 @@ __global__ void __launch_bounds__(kWarps * 32) sg_gather_kernel(SgGatherArgs a) 
 
 }  // namespace
 
+template <int H, int NP>
+void launch_transform_np(const SgTransformArgs &a, cudaStream_t s) {
+    const int blocks = (a.A + kWarps * NP - 1) / (kWarps * NP);
+    sg_transform_kernel<H, NP><<<blocks, kWarps * 32, 0, s>>>(a);
+}
+
+template <int H, int NP>
+void launch_step_np(const SgStepArgs &a, cudaStream_t s) {
+    const int blocks = (a.A + kWarps * NP - 1) / (kWarps * NP);
+    sg_step_kernel<H, NP><<<blocks, kWarps * 32, 0, s>>>(a);
+}
+
+template <int H>
+void launch_transform_h(const SgTransformArgs &a, cudaStream_t s) {
+    switch (a.nodes_per_warp) {
+    case 1: launch_transform_np<H, 1>(a, s); break;
+    case 2: launch_transform_np<H, 2>(a, s); break;
+    case 8: launch_transform_np<H, 8>(a, s); break;
+    default: launch_transform_np<H, 4>(a, s); break;
+    }
+}
+
+template <int H>
+void launch_step_h(const SgStepArgs &a, cudaStream_t s) {
+    switch (a.nodes_per_warp) {
+    case 1: launch_step_np<H, 1>(a, s); break;
+    case 2: launch_step_np<H, 2>(a, s); break;
+    case 8: launch_step_np<H, 8>(a, s); break;
+    default: launch_step_np<H, 4>(a, s); break;
+    }
+}
+
 void launch_sg_transform(const SgTransformArgs &a, cudaStream_t s) {
-    const int blocks = (a.A + kWarps * kNodesPerWarp - 1) / (kWarps * kNodesPerWarp);
-    if (a.H == 64) sg_transform_kernel<64><<<blocks, kWarps * 32, 0, s>>>(a);
-    else sg_transform_kernel<32><<<blocks, kWarps * 32, 0, s>>>(a);
+    if (a.H == 64) launch_transform_h<64>(a, s);
+    else launch_transform_h<32>(a, s);
 }
 
 void launch_sg_step(const SgStepArgs &a, cudaStream_t s) {
-    const int blocks = (a.A + kWarps * kNodesPerWarp - 1) / (kWarps * kNodesPerWarp);
-    if (a.H == 64) sg_step_kernel<64><<<blocks, kWarps * 32, 0, s>>>(a);
-    else sg_step_kernel<32><<<blocks, kWarps * 32, 0, s>>>(a);
+    if (a.H == 64) launch_step_h<64>(a, s);
+    else launch_step_h<32>(a, s);
 }
 
 void launch_sg_gather(const SgGatherArgs &a, cudaStream_t s) {

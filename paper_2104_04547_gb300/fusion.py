@@ -42,12 +42,13 @@ FUSION_FORMS = {"coherent": FUSION_COHERENT, "mid": FUSION_MID, "late": FUSION_L
 FUSION_OPT_CUDA_GRAPH = 1
 FUSION_OPT_CONV_SLICES_PER_MMA = 2
 FUSION_OPT_TEST_WAIT_TIMEOUT = 3
+FUSION_OPT_GRAPH_NODES_PER_WARP = 4
 
 EXPORTED = ["fusion_weights_bytes", "fusion_create", "fusion_score", "fusion_destroy", "fusion_last_error",
             "fusion_stage_bytes", "fusion_fetch_stage", "fusion_last_timings", "fusion_cnn_dense_noalloc",
             "fusion_server_create", "fusion_server_submit", "fusion_server_poll", "fusion_server_drain",
             "fusion_server_get_stats", "fusion_server_destroy", "fusion_set_option", "fusion_autotune",
-            "fusion_describe_conv", "fusion_best_per_compound"]
+            "fusion_describe_conv", "fusion_best_per_compound", "fusion_graph_schedule"]
 
 FUSION_NOALLOC_MAX_PARTIALS = 1 << 21
 
@@ -139,6 +140,8 @@ def _load():
     lib.fusion_best_per_compound.argtypes = [P(C.c_float), P(C.c_int32), C.c_int32, C.c_int32, P(C.c_float),
                                              P(C.c_int32)]
     lib.fusion_best_per_compound.restype = C.c_int
+    lib.fusion_graph_schedule.argtypes = [C.c_void_p, P(C.c_int32)]
+    lib.fusion_graph_schedule.restype = C.c_int
     return lib
 
 
@@ -276,6 +279,12 @@ def fusion_describe_conv(model, layer: int) -> dict:
             "slices_per_mma": out[4]}
 
 
+def fusion_graph_schedule(model) -> int:
+    npw = C.c_int32(0)
+    _check(lib.fusion_graph_schedule(model, C.byref(npw)))
+    return int(npw.value)
+
+
 def fusion_score(model, poses: dict, n_poses: int, out, on_device: bool = False) -> None:
     """Score a packed batch.
 
@@ -369,6 +378,12 @@ class Model:
 
     def conv_tiles(self):
         return [fusion_describe_conv(self.handle, i) for i in range(self.desc.n_conv)]
+
+    def graph_nodes_per_warp(self, value=None):
+        """Set (1, 2, 4, 8; -1 default) and/or return the graph convolution's nodes per warp."""
+        if value is not None:
+            fusion_set_option(self.handle, FUSION_OPT_GRAPH_NODES_PER_WARP, int(value))
+        return fusion_graph_schedule(self.handle)
 
     def close(self):
         if self.handle:
