@@ -1389,6 +1389,18 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
 
     // graph convolution: nodes per warp, by the whole call's device time (the branch runs beside the
     // convolutions, so its own kernel time is not what counts); median of 5 calls after one untimed
+    // on an early return (a failed call) the model gets its graph mode and schedule back
+    struct Restore {
+        fusion_model *m;
+        bool graphs;
+        int npw;
+        bool armed = true;
+        ~Restore() {
+            if (!armed) return;
+            m->use_graph = graphs;
+            m->sg_npw = npw;
+        }
+    } restore{m, m->use_graph, m->sg_npw};
     const bool graphs = m->use_graph;
     m->use_graph = false;
     float best_total = 1e30f;
@@ -1407,6 +1419,7 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
             best_npw = npw;
         }
     }
+    restore.armed = false;
     m->sg_npw = best_npw;
     m->use_graph = graphs;
     drop_graphs(m);
