@@ -11,6 +11,7 @@ import inspect
 import pytest
 
 import test_oracle_cnn as cnn_pins
+import test_oracle_fusion_forms as forms_pins
 import test_oracle_graph as graph_pins
 import test_oracle_sgcnn as sg_pins
 import test_oracle_voxelize as vox_pins
@@ -75,6 +76,20 @@ MUTATIONS = [
     ("SELU alpha of another activation",
      [("SELU_ALPHA = 1.6732632423543772848170429916717", "SELU_ALPHA = 1.0")],
      [sg_pins.test_activations_match_torch, sg_pins.test_head_matches_torch]),
+    ("Late Fusion summing the two affinities instead of averaging",
+     [("return 0.5 * (out[0] + out[1])", "return out[0] + out[1]")],
+     [lambda: forms_pins.test_late_fusion_is_mean_of_torch_stacks("fusion-24grid-c32-late"),
+      forms_pins.test_late_fusion_constant_branch_pins_the_mean]),
+    ("Late Fusion stacks without their ReLU",
+     [("                if l + 1 < n:\n                    v = relu(v)", "                pass")],
+     [lambda: forms_pins.test_late_fusion_is_mean_of_torch_stacks("fusion-24grid-c32-late")]),
+    ("Mid-level branch outputs in front of the latents",
+     [("parts = [cnn, sg]", "parts = []"), ("        v = np.concatenate(parts)", "        v = np.concatenate(parts + [cnn, sg])")],
+     [lambda: forms_pins.test_mid_fusion_zero_branches_equal_coherent_head_on_leading_columns("fusion-24grid-c32-mid"),
+      forms_pins.test_mid_fusion_matches_torch_restatement]),
+    ("residual fusion layer without its add",
+     [("u = v + u", "u = u")],
+     [forms_pins.test_residual_zero_layer_is_identity, forms_pins.test_mid_fusion_matches_torch_restatement]),
     ("latents concatenated in the other order",
      [("    v = np.concatenate([cnn, sg])\n", "    v = np.concatenate([sg, cnn])\n")],
      [sg_pins.test_head_matches_torch, sg_pins.test_tiny_network_end_to_end_matches_torch_restatement]),
