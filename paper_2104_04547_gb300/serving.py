@@ -94,11 +94,18 @@ def run(args):
         srv.drain()
         elapsed = time.perf_counter() - t0
         _aff, lat = _collect(srv, tickets)
+        lat = np.asarray(lat)
+        slow = np.nonzero(lat > 0.010)[0]
         print(json.dumps({**base, "offered": load, "offered_poses_per_s": rate, "poses_per_s": n / elapsed,
                           "requests": n,
                           "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
                                          "p99": 1e3 * float(np.percentile(lat, 99)),
-                                         "p99.9": 1e3 * float(np.percentile(lat, 99.9))}}), flush=True)
+                                         "p99.9": 1e3 * float(np.percentile(lat, 99.9)),
+                                         "max": 1e3 * float(lat.max())},
+                          # requests slower than 10 ms: how many, and when they arrived (s after the start)
+                          "over_10ms": {"count": int(len(slow)),
+                                        "arrivals_s": [round(float(arrivals[i]), 3) for i in slow[:20]]}}),
+              flush=True)
     print(json.dumps({**base, "stats": srv.stats()}), flush=True)
     srv.close()
 
