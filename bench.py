@@ -8,7 +8,7 @@ heavy atoms, pockets 300-600 atoms, seeds 1..64) with the full-size model
 gated ligand pooling to 128; head 384->256->64->1): voxelize, 3D-CNN, radius
 graph, graph convolution, gather and head, all in the CUDA library.
 
-    python bench.py [--steps K] [--warmup W] [--dtype f32|bf16] [--impl ours|reference]
+    python bench.py [--steps K] [--warmup W] [--dtype f32|bf16|fp8] [--impl ours|reference]
 
 Multi-GPU (torchrun, one rank per GPU): every rank scores its own copy of the
 batch with no data-path collective (replicas; weak scaling).  Rank 0 prints
