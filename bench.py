@@ -64,9 +64,10 @@ def conv_source_hash():
     return h.hexdigest()[:16]
 
 
-def conv_traffic(dtype, n_poses):
+def conv_traffic(dtype, n_poses, model=MODEL):
     """Measured DRAM bytes per conv launch (mean of the step's launches), or None."""
-    if dtype not in CONV_TRAFFIC or n_poses != CONV_TRAFFIC["poses"] or conv_source_hash() != CONV_TRAFFIC["src"]:
+    if (model != MODEL or dtype not in CONV_TRAFFIC or n_poses != CONV_TRAFFIC["poses"] or
+            conv_source_hash() != CONV_TRAFFIC["src"]):
         return None
     v = CONV_TRAFFIC[dtype]
     return sum(v) / len(v)
@@ -196,7 +197,7 @@ def run_reference(args):
     if rank != 0:
         return
     from synth import configs, poses, weights
-    desc = configs.model(MODEL)
+    desc = configs.model(args.model)
     W = weights.init_weights(desc, WEIGHTS_SEED)
     batch = poses.make_batch(configs.WORKLOADS[WORKLOAD])
     from oracle import fusion_oracle as O
@@ -215,7 +216,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"{MODEL} scoring, {WORKLOAD}", "sample_per_step": "1 pose"},
+            "config": {"workload": f"{args.model} scoring, {WORKLOAD}", "sample_per_step": "1 pose"},
             "cpu_baseline": {"value": v, "unit": "poses/s", "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} poses of the workload, one per step"},
             "e2e": {"value": v, "unit": "poses/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -241,7 +242,7 @@ def run_ours(args):
     from paper_2104_04547_gb300 import fusion as F
     from synth import configs, poses, weights
 
-    desc = configs.model(MODEL, dtype=args.dtype)
+    desc = configs.model(args.model, dtype=args.dtype)
     W = weights.init_weights(desc, WEIGHTS_SEED)
     blob = weights.to_blob(desc, W)
     batch = poses.make_batch(configs.WORKLOADS[WORKLOAD])
@@ -314,7 +315,7 @@ def run_ours(args):
     fp32_path = None
     if args.dtype != "f32" and not args.no_f32_compare:
         got = out.float().cpu().numpy().copy()
-        d32 = configs.model(MODEL, dtype="f32")
+        d32 = configs.model(args.model, dtype="f32")
         m32 = F.Model(d32, weights.to_blob(d32, W), max_poses=B, max_atoms=1200, max_degree=64,
                       stream=stream.cuda_stream)
         ref = m32.score(batch).copy()
@@ -344,11 +345,11 @@ def run_ours(args):
     conv_flops = conv_flops_per_pose(desc) * B
     achieved = conv_flops / (conv_ms / 1000.0) / 1e12
     pk, pk_src = peaks()
-    traffic = conv_traffic(args.dtype, B)
+    traffic = conv_traffic(args.dtype, B, args.model)
     if args.dtype == "f32":
         roof = {"bound": "alu", "achieved": achieved, "peak": F32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / F32_ALU_PEAK_TFLOPS, "traffic": None,
-                "kernel": "conv3d_f32_kernel (4 launches per step)",
+                "kernel": f"conv3d_f32_kernel ({len(conv_names)} launches per step)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     else:
         # The burst peak: the step keeps the SM clock at its maximum (see `clocks`), while the sustained
@@ -358,18 +359,19 @@ def run_ours(args):
         p = pk["bf16_tflops"] * ratio
         ps = pk["bf16_tflops_sustained"] * ratio
         roof = {"bound": "tensor", "achieved": achieved, "peak": p, "unit": "TFLOP/s", "frac": achieved / p,
-                "traffic": traffic, "kernel": f"conv3d_tc_kernel {args.dtype} (4 launches per step)",
+                "traffic": traffic, "kernel": f"conv3d_tc_kernel {args.dtype} ({len(conv_names)} launches per step)",
                 "peak_source": f"bf16_tflops burst ({pk_src})" + (" x 2 (nominal fp8/bf16 ratio)" if ratio != 1 else ""),
                 "frac_of_sustained": achieved / ps}
     if args.dtype != "f32":
-        roof["traffic_unit"] = "DRAM bytes per conv launch (mean of the step's 4), ncu"
+        roof["traffic_unit"] = f"DRAM bytes per conv launch (mean of the step's {len(conv_names)}), ncu"
         roof["algorithmic_bytes"] = conv_algorithmic_bytes(desc, args.dtype, B)
     stage_mean = {n: statistics.mean(s[n] for s in stage_ms) for n in stage_ms[0]}
     line = {
         "metric": METRIC, "value": value, "unit": "poses/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-        "config": {"workload": f"{MODEL} scoring, {WORKLOAD}", "batch": B, "grid": "48^3x19 at 1 A",
+        "config": {"workload": f"{args.model} scoring, {WORKLOAD}", "batch": B,
+                   "grid": f"{desc['grid_n']}^3x19 at {desc['grid_h']:g} A",
                    "l2": "256 MiB written between timed steps; step working set (activations) > L2",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -404,6 +406,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f32-compare", action="store_true")
     ap.add_argument("--poses", type=int, default=64, help="first N poses of the batch (small profiling captures)")
+    ap.add_argument("--model", default=MODEL,
+                    help="model preset (synth.configs); the benchmark model by default, others for comparison")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
