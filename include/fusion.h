@@ -192,12 +192,13 @@ int fusion_last_timings(fusion_model *m, float *out, int32_t n);
 #define FUSION_OPT_CUDA_GRAPH 1   /* value 1: fusion_score replays a CUDA graph of the whole device-side
                                      forward pass, captured on first use for each batch size (inputs are
                                      copied into the model's own buffers first); 0: plain launches */
-#define FUSION_OPT_CONV_SLICES_PER_MMA 2   /* tensor-core convs: value 1, 2 or 4 = every layer has each MMA
+#define FUSION_OPT_CONV_SLICES_PER_MMA 2   /* tensor-core convs: value 1, 2, 4 or 8 = every layer has each MMA
                                               serve that many adjacent output slices (N = value x output
-                                              channels; FUSION_EUNSUPPORTED where a layer cannot), -1 = the
-                                              default per layer (for stride-1 layers 4 where it fits,
-                                              else 2, else 1; 1 for stride 2).  Re-plans the layers and drops captured graphs; scores
-                                              are the same in every mode */
+                                              channels; 8 only for 32-channel layers at 16 slices per CTA;
+                                              FUSION_EUNSUPPORTED where a layer cannot), -1 = the default per
+                                              layer (for stride-1 layers 8 at 16 slices per CTA, else 4 where
+                                              it fits, else 2, else 1; 1 for stride 2).  Re-plans the layers
+                                              and drops captured graphs; scores are the same in every mode */
 
 #define FUSION_OPT_TEST_WAIT_TIMEOUT 3   /* value 1: test of failure detection.  In the next fusion_score
                                             call the first tensor-core conv launch loads nothing, so its

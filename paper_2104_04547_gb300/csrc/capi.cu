@@ -1258,8 +1258,8 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
         drop_graphs(m);
         return FUSION_OK;
     case FUSION_OPT_CONV_SLICES_PER_MMA: {
-        if (value != -1 && value != 1 && value != 2 && value != 4)
-            return fail(FUSION_EINVAL, "slices per MMA must be -1 (default), 1, 2 or 4");
+        if (value != -1 && value != 1 && value != 2 && value != 4 && value != 8)
+            return fail(FUSION_EINVAL, "slices per MMA must be -1 (default), 1, 2, 4 or 8");
         if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "the FP32 path has no tensor-core tiles");
         const int old = m->group_mode;
         m->group_mode = (int)value;
@@ -1334,7 +1334,9 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
     cudaEvent_t e0 = m->ev[16], e1 = m->ev[17];
     for (int i = 0; i < d.n_conv; ++i) {
         const int co = d.conv[i].c_out;
-        std::vector<int> Ts = co <= 64 ? std::vector<int>{8, 4} : co == 128 ? std::vector<int>{4, 2} : std::vector<int>{2};
+        std::vector<int> Ts = co <= 32   ? std::vector<int>{16, 8, 4}
+                              : co <= 64 ? std::vector<int>{8, 4}
+                              : co == 128 ? std::vector<int>{4, 2} : std::vector<int>{2};
         float best_ms = 1e30f;
         int best[4] = {0, 0, 0, 0};
         auto prepare_input = [&]() {
@@ -1348,7 +1350,7 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
             quantize_conv_input(m, i, xb, B, st);
         };
         for (int T : Ts)
-            for (int group : {4, 2, 1})
+            for (int group : {8, 4, 2, 1})
             for (int groups : {1, 2, 3, 4, 6})
                 for (int nbs : {2, 3, 4}) {
                     ConvTcPlan trial;

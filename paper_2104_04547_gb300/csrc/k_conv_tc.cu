@@ -552,6 +552,15 @@ ConvTcPlan::~ConvTcPlan() { delete impl; }
 
 int conv_tc_tile_slices(int c_out) { return c_out >= 256 ? 2 : c_out >= 128 ? 4 : 8; }
 
+// 32-output-channel layers can take 16 slices per CTA (16 x 32 = 512 tensor-memory columns) and serve 8 of
+// them per MMA (N = 256, the width that keeps the MMA above the operand path's rate) with two slice groups,
+// hence two issuers.  Chosen by default where the halo fits and the z extent wastes no more slices than 8
+// per CTA would.
+static bool wide_tiles_ok(int c_out, int n_out) {
+    const int w16 = (n_out + 15) / 16 * 16, w8 = (n_out + 7) / 8 * 8;
+    return c_out <= 32 && w16 <= w8;
+}
+
 // Taps per dimension of parity phase ph: k at stride 1; (k + 1) / 2 and k / 2 for parities 0 / 1 at stride 2.
 static void phase_ntaps(int k, int stride, int ph, int &nz, int &ny, int &nx) {
     if (stride == 1) {
@@ -724,9 +733,15 @@ void conv_tc_arrange_weights(const float *w, int c_out, int c_in, int cin_pad, i
 int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_len) {
     ConvTcPlan::Impl &P = *plan.impl;
     const int c_out = sp.c_out, k = sp.k, stride = sp.stride;
+    if (sp.T <= 0 && stride == 1 && wide_tiles_ok(c_out, sp.n_out)) {
+        ConvTcSpec wide = sp;
+        wide.T = 16;
+        if (conv_tc_plan(plan, wide, why, why_len) == 0) return 0;   // else the default below
+    }
     const int T = sp.T > 0 ? sp.T : conv_tc_tile_slices(c_out);
     const int chunk_ch = sp.elem == 2 ? 16 : 32;
-    const bool t_ok = (c_out <= 64 && (T == 4 || T == 8)) || (c_out == 128 && (T == 2 || T == 4)) ||
+    const bool t_ok = (c_out <= 64 && (T == 4 || T == 8)) || (c_out <= 32 && T == 16) ||
+                      (c_out == 128 && (T == 2 || T == 4)) ||
                       (c_out == 256 && T == 2);
     if (!t_ok) {
         snprintf(why, why_len, "unsupported output slices per CTA (%d) for %d output channels", T, c_out);
@@ -786,12 +801,14 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     // about every 80-100 clocks, and 4 slices per MMA leave two accumulator sets, hence two issuers, whose
     // warps also ran the epilogue.)  At stride 2 each phase has only 2-3 z offsets, so a slice group
     // shares little: 1.
-    auto group_ok = [&](int G) { return (G == 1 || G == 2 || G == 4) && T % G == 0 && G * c_out <= 256; };
+    auto group_ok = [&](int G) {
+        return (G == 1 || G == 2 || G == 4 || G == 8) && T % G == 0 && G * c_out <= 256 && T / G >= (G == 8 ? 2 : 1);
+    };
     int group = sp.group;
-    if (group <= 0) group = stride != 1 ? 1 : group_ok(4) ? 4 : group_ok(2) ? 2 : 1;
+    if (group <= 0) group = stride != 1 ? 1 : (T == 16 && group_ok(8)) ? 8 : group_ok(4) ? 4 : group_ok(2) ? 2 : 1;
     if (!group_ok(group)) {
-        snprintf(why, why_len, "%d slices per MMA: must be 1, 2 or 4, divide the %d slices per CTA and span <= 256 "
-                 "columns", group, T);
+        snprintf(why, why_len, "%d slices per MMA: must be 1, 2, 4 or 8 (8: with 16 slices per CTA), divide the %d "
+                 "slices per CTA and span <= 256 columns", group, T);
         return -1;
     }
     g.nbs = sp.nbs > 0 ? sp.nbs : 2;
@@ -804,8 +821,14 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     // tile_full/tile_empty [kRing] each, the tile ring, then the tensor-memory slot and the abort flag
     const size_t bar_bytes = (size_t)(4 + 2 * g.nbs + 2 * (T / group) + 1 + 2 * kRing) * 8 + kRing * 4 + 16;
     const size_t limit = 227 * 1024;
-    const size_t b_total = (size_t)g.nbs * g.stage_bytes;
     const size_t a1 = g.a_bytes;
+    // a larger halo (16 slices per CTA) leaves less room for weights: shrink the default stages to fit
+    while (sp.groups_per_stage <= 0 && g.groups_per_stage > 1 &&
+           a1 + (size_t)g.nbs * g.stage_bytes + bar_bytes > limit) {
+        --g.groups_per_stage;
+        g.stage_bytes = ((uint32_t)g.groups_per_stage * gbytes_max + 127) / 128 * 128;
+    }
+    const size_t b_total = (size_t)g.nbs * g.stage_bytes;
     g.na = (2 * a1 + b_total + bar_bytes <= limit) ? 2 : 1;
     P.smem = g.na * a1 + b_total + bar_bytes;
     if (P.smem > limit) {
@@ -902,6 +925,9 @@ static void launch_t(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
 
 template <int N, int T, bool F8>
 static void launch_g(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
+    if constexpr (T == 16 && 8 * N <= 256) {
+        if (P.group == 8) return launch_t<N, T, F8, 8>(P, B, s);
+    }
     if constexpr (T % 4 == 0 && 4 * N <= 256) {
         if (P.group == 4) return launch_t<N, T, F8, 4>(P, B, s);
     }
@@ -916,6 +942,7 @@ static void launch_n(ConvTcPlan::Impl &P, int B, cudaStream_t s) {
     switch (P.N * 16 + P.T) {
     case 32 * 16 + 4: launch_g<32, 4, F8>(P, B, s); break;
     case 32 * 16 + 8: launch_g<32, 8, F8>(P, B, s); break;
+    case 32 * 16 + 16: launch_g<32, 16, F8>(P, B, s); break;
     case 64 * 16 + 4: launch_g<64, 4, F8>(P, B, s); break;
     case 64 * 16 + 8: launch_g<64, 8, F8>(P, B, s); break;
     case 128 * 16 + 2: launch_g<128, 2, F8>(P, B, s); break;
