@@ -234,8 +234,8 @@ struct fusion_model {
     DenseTcPlan dense_tc;                         // tensor-core CNN dense (bf16 / FP8 models)
     int dense_tc_splits = 0;
     int pool_n = 0, pool_c = 0, flat = 0, splits = 1;
-    float *we_t[FUSION_MAX_STAGES][2] = {}, *be[FUSION_MAX_STAGES][2] = {};
-    float *wih_t[FUSION_MAX_STAGES] = {}, *whh_t[FUSION_MAX_STAGES] = {}, *bih[FUSION_MAX_STAGES] = {}, *bhh[FUSION_MAX_STAGES] = {};
+    float *we_p[FUSION_MAX_STAGES][2] = {}, *be[FUSION_MAX_STAGES][2] = {};
+    float *gru_p[FUSION_MAX_STAGES] = {}, *bih[FUSION_MAX_STAGES] = {}, *bhh[FUSION_MAX_STAGES] = {};
     float *gi_t = nullptr, *gbi = nullptr, *gj_t = nullptr, *gbj = nullptr;
     float *gat_wg_t = nullptr, *gat_bg = nullptr, *gat_wo_t = nullptr, *gat_bo = nullptr;
     float *head_wt[FUSION_MAX_HEAD] = {}, *head_b[FUSION_MAX_HEAD] = {};
@@ -357,6 +357,35 @@ std::vector<float> transpose(const float *w, int rows, int cols) {   // [rows][c
     return t;
 }
 
+// Graph-kernel weights in the order a warp reads them: lane l owns outputs o = l + 32 j (j < H / 32).
+// Edge transform W [H][H] (out x in) -> [k][l][j] = W[l + 32 j][k].
+std::vector<float> pack_edge(const float *w, int H) {
+    const int HJ = H / 32;
+    std::vector<float> t((size_t)H * H);
+    for (int k = 0; k < H; ++k)
+        for (int l = 0; l < 32; ++l)
+            for (int j = 0; j < HJ; ++j) t[((size_t)k * 32 + l) * HJ + j] = w[(size_t)(l + 32 * j) * H + k];
+    return t;
+}
+
+// GRU W_ih, W_hh [3H][H] (gate rows reset, update, new) -> [k][l][P]: for each j the six floats
+// W_ih[gH + o][k] (g = 0, 1, 2) then W_hh[gH + o][k], o = l + 32 j; P = 6 H / 32 rounded up to a
+// multiple of 4 (zero padding), so a lane's weights for one k are P / 4 aligned 16-byte loads.
+std::vector<float> pack_gru(const float *wih, const float *whh, int H) {
+    const int HJ = H / 32, P = (6 * HJ + 3) / 4 * 4;
+    std::vector<float> t((size_t)H * 32 * P, 0.f);
+    for (int k = 0; k < H; ++k)
+        for (int l = 0; l < 32; ++l)
+            for (int j = 0; j < HJ; ++j)
+                for (int g = 0; g < 3; ++g) {
+                    const size_t row = (size_t)g * H + l + 32 * j;
+                    float *q = &t[((size_t)k * 32 + l) * P + 6 * j];
+                    q[g] = wih[row * H + k];
+                    q[3 + g] = whh[row * H + k];
+                }
+    return t;
+}
+
 #define RC(x)                 \
     do {                      \
         int rc_ = (x);        \
@@ -430,15 +459,14 @@ int load_weights(fusion_model *m, const float *blob) {
             if (!(d.sg_edges[s] & (1 << e))) continue;
             const float *w = take();
             const float *b = take();
-            RC(upload(m, &m->we_t[s][e], transpose(w, H, H)));
+            RC(upload(m, &m->we_p[s][e], pack_edge(w, H)));
             RC(upload(m, &m->be[s][e], std::vector<float>(b, b + H)));
         }
         const float *wih = take();
         const float *whh = take();
         const float *bih = take();
         const float *bhh = take();
-        RC(upload(m, &m->wih_t[s], transpose(wih, 3 * H, H)));
-        RC(upload(m, &m->whh_t[s], transpose(whh, 3 * H, H)));
+        RC(upload(m, &m->gru_p[s], pack_gru(wih, whh, H)));
         RC(upload(m, &m->bih[s], std::vector<float>(bih, bih + 3 * H)));
         RC(upload(m, &m->bhh[s], std::vector<float>(bhh, bhh + 3 * H)));
         if (d.sg_gate && s + 1 < d.sg_n_stages) {
@@ -834,7 +862,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
         }
         for (int e = 0; e < 2; ++e) {
             const bool use = (d.sg_edges[s] & (1 << e)) && d.sg_steps[s] > 0;
-            ta.we_t[e] = use ? m->we_t[s][e] : nullptr;
+            ta.we_p[e] = use ? m->we_p[s][e] : nullptr;
             ta.be[e] = use ? m->be[s][e] : nullptr;
             ta.T[e] = m->Tbuf[e][tcur];
         }
@@ -854,10 +882,10 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
                 sa.beg[e] = m->e_beg[e];
                 sa.deg[e] = m->e_deg[e];
                 sa.col[e] = m->e_col[e];
-                sa.we_t[e] = use ? m->we_t[s][e] : nullptr;
+                sa.we_p[e] = use ? m->we_p[s][e] : nullptr;
                 sa.be[e] = use ? m->be[s][e] : nullptr;
             }
-            sa.wih_t = m->wih_t[s]; sa.whh_t = m->whh_t[s]; sa.bih = m->bih[s]; sa.bhh = m->bhh[s];
+            sa.gru_p = m->gru_p[s]; sa.bih = m->bih[s]; sa.bhh = m->bhh[s];
             sa.A = A;
             sa.H = H;
             sa.A_dev = A_dev;

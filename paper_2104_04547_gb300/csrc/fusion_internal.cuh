@@ -206,7 +206,7 @@ struct SgTransformArgs {
     const float *h_in;     // [A][H] (unused in init mode)
     float *h_out;          // [A][H]: the stage input written here
     float *T[2];           // [A][H] per edge type slot
-    const float *we_t[2];  // [H][H] transposed edge transforms (nullptr: slot unused)
+    const float *we_p[2];  // edge transforms, [k][lane][H/32]: W_e[lane + 32 j][k] (nullptr: slot unused)
     const float *be[2];
     const float *gi_t, *gbi, *gj_t, *gbj;   // gate ([2H][H], [H], [H][H], [H]); nullptr: no gate
     int A, H;
@@ -222,8 +222,10 @@ struct SgStepArgs {
     const float *T_in[2];  // neighbour transforms of this step (nullptr: slot unused)
     float *T_out[2];       // transforms of h_out for the next step (nullptr: not needed)
     const int32_t *beg[2], *deg[2], *col[2];   // edges of each slot
-    const float *wih_t, *whh_t, *bih, *bhh;     // GRU: [H][3H], [H][3H], [3H], [3H]
-    const float *we_t[2], *be[2];               // for T_out
+    const float *gru_p;    // GRU weights, [k][lane][P]: per j, W_ih[gH + o][k] then W_hh[gH + o][k] (g = 0..2,
+                           // o = lane + 32 j), zero-padded to P = 6H/32 rounded up to a multiple of 4
+    const float *bih, *bhh;                     // GRU biases [3H], [3H]
+    const float *we_p[2], *be[2];               // for T_out (layout as SgTransformArgs::we_p)
     int A, H;
     const int32_t *A_dev;  // non-null: the atom count is *A_dev (A is then the launch capacity)
     int nodes_per_warp;    // 1, 2, 4 or 8 (anything else: 4); the results do not depend on it

@@ -27,14 +27,62 @@ constexpr int kWarps = 8;
 
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
 
+__device__ __forceinline__ float f4(const float4 &x, int i) { return i == 0 ? x.x : i == 1 ? x.y : i == 2 ? x.z : x.w; }
+
+// T = W_e x + b_e for the warp's NP nodes, x = v[n][0..H).  Lane l computes outputs o = l + 32 j; its weights
+// for input k are the H/32 floats at we_p[(k * 32 + l) * H/32] (one 8- or 4-byte load), and the node vectors
+// are read four inputs at a time from shared memory.  Every sum runs from the bias over k ascending.
+template <int H, int NP>
+__device__ __forceinline__ void edge_transform(const float (*v)[2 * H], const float *we_p, const float *be, int lane,
+                                               int np, int i0, float *T) {
+    constexpr int HJ = H / 32;
+    float t[NP][HJ];
+#pragma unroll
+    for (int j = 0; j < HJ; ++j) {
+        const float b = be[lane + 32 * j];
+#pragma unroll
+        for (int n = 0; n < NP; ++n) t[n][j] = b;
+    }
+    const float *wl = we_p + lane * HJ;
+    for (int k0 = 0; k0 < H; k0 += 4) {
+        float4 x[NP];
+#pragma unroll
+        for (int n = 0; n < NP; ++n) x[n] = *reinterpret_cast<const float4 *>(&v[n][k0]);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            float w[HJ];
+            if constexpr (HJ == 2) {
+                const float2 q = __ldg(reinterpret_cast<const float2 *>(wl + (size_t)(k0 + kk) * 32 * HJ));
+                w[0] = q.x;
+                w[1] = q.y;
+            } else {
+                w[0] = __ldg(wl + (size_t)(k0 + kk) * 32 * HJ);
+            }
+#pragma unroll
+            for (int n = 0; n < NP; ++n) {
+                const float xk = f4(x[n], kk);
+#pragma unroll
+                for (int j = 0; j < HJ; ++j) t[n][j] = fmaf(w[j], xk, t[n][j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NP; ++n)
+#pragma unroll
+        for (int j = 0; j < HJ; ++j)
+            if (n < np) T[(size_t)(i0 + n) * H + lane + 32 * j] = t[n][j];
+}
+
 // A warp takes NP consecutive nodes (1, 2, 4 or 8; SgStepArgs::nodes_per_warp): the matrix-vector products
-// load each weight once for all of them (weights are read from L1, and that read bounds these kernels),
-// while every node's sums keep the order of a warp per node, so the results do not depend on NP.
+// load each weight once for all of them, while every node's sums keep the order of a warp per node, so the
+// results do not depend on NP.  The weights are packed in the order a lane reads them (its GRU weights for
+// one input in 16-byte loads, its edge-transform weights in one 8-byte load), so the L1 weight reads that
+// bounded these kernels take a quarter of the load instructions.
 
 template <int H, int NP>
 __global__ void __launch_bounds__(kWarps * 32) sg_transform_kernel(SgTransformArgs a) {
     constexpr int HJ = H / 32;
-    __shared__ float sv[kWarps][NP][2 * H];
+    __shared__ __align__(16) float sv[kWarps][NP][2 * H];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int A = a.A_dev ? *a.A_dev : a.A;
     const int i0 = (blockIdx.x * kWarps + warp) * NP;
@@ -89,30 +137,14 @@ __global__ void __launch_bounds__(kWarps * 32) sg_transform_kernel(SgTransformAr
             if (n < np) a.h_out[(size_t)(i0 + n) * H + o] = x[n][j];
         }
     __syncwarp();
-    for (int e = 0; e < 2; ++e) {
-        if (!a.we_t[e]) continue;
-#pragma unroll
-        for (int j = 0; j < HJ; ++j) {
-            const int o = lane + 32 * j;
-            float t[NP];
-#pragma unroll
-            for (int n = 0; n < NP; ++n) t[n] = a.be[e][o];
-            for (int k = 0; k < H; ++k) {
-                const float w = a.we_t[e][k * H + o];
-#pragma unroll
-                for (int n = 0; n < NP; ++n) t[n] = fmaf(w, v[n][k], t[n]);
-            }
-#pragma unroll
-            for (int n = 0; n < NP; ++n)
-                if (n < np) a.T[e][(size_t)(i0 + n) * H + o] = t[n];
-        }
-    }
+    for (int e = 0; e < 2; ++e)
+        if (a.we_p[e]) edge_transform<H, NP>(v, a.we_p[e], a.be[e], lane, np, i0, a.T[e]);
 }
 
 template <int H, int NP>
 __global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
     constexpr int HJ = H / 32;
-    __shared__ float sv[kWarps][NP][2 * H];
+    __shared__ __align__(16) float sv[kWarps][NP][2 * H];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int A = a.A_dev ? *a.A_dev : a.A;
     const int i0 = (blockIdx.x * kWarps + warp) * NP;
@@ -121,7 +153,6 @@ __global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
     float (*v)[2 * H] = sv[warp];
 
     // message: segment sum of the neighbours' transforms, edge type by edge type, row order
-    float hv[NP][HJ];
 #pragma unroll
     for (int n = 0; n < NP; ++n) {
         float m[HJ];
@@ -136,10 +167,11 @@ __global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
                 for (int q0 = 0; q0 < d; q0 += 32) {
                     const int jl = (q0 + lane < d) ? a.col[e][beg + q0 + lane] : 0;
                     const int nq = min(32, d - q0);
+#pragma unroll 4
                     for (int q = 0; q < nq; ++q) {
                         const int jn = __shfl_sync(0xffffffffu, jl, q);
 #pragma unroll
-                        for (int j = 0; j < HJ; ++j) m[j] += T[(size_t)jn * H + lane + 32 * j];
+                        for (int j = 0; j < HJ; ++j) m[j] += __ldg(T + (size_t)jn * H + lane + 32 * j);
                     }
                 }
             }
@@ -147,44 +179,67 @@ __global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
 #pragma unroll
         for (int j = 0; j < HJ; ++j) {
             const int o = lane + 32 * j;
-            hv[n][j] = n < np ? a.h_in[(size_t)(i0 + n) * H + o] : 0.f;
             v[n][o] = m[j];
-            v[n][H + o] = hv[n][j];
+            v[n][H + o] = n < np ? a.h_in[(size_t)(i0 + n) * H + o] : 0.f;
         }
     }
     __syncwarp();
+    // GRU.  Lane l owns outputs o = l + 32 j of each gate.  Its weights for input k are P floats (per j:
+    // W_ih rows r, z, n, then W_hh rows r, z, n, at row o), read as P / 4 16-byte loads; the node vectors
+    // [m, h] are read four inputs at a time.  Every sum runs from the bias over k ascending.
+    constexpr int P = (6 * HJ + 3) / 4 * 4;
+    float acc[NP][HJ][6];
+#pragma unroll
+    for (int j = 0; j < HJ; ++j) {
+        const int o = lane + 32 * j;
+        float b[6];
+#pragma unroll
+        for (int g = 0; g < 3; ++g) { b[g] = a.bih[g * H + o]; b[3 + g] = a.bhh[g * H + o]; }
+#pragma unroll
+        for (int n = 0; n < NP; ++n)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc[n][j][q] = b[q];
+    }
+    const float4 *wl = reinterpret_cast<const float4 *>(a.gru_p) + lane * (P / 4);
+    for (int k0 = 0; k0 < H; k0 += 4) {
+        float4 xm[NP], xh[NP];
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+            xm[n] = *reinterpret_cast<const float4 *>(&v[n][k0]);
+            xh[n] = *reinterpret_cast<const float4 *>(&v[n][H + k0]);
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            float w[P];
+            const float4 *wk = wl + (size_t)(k0 + kk) * 32 * (P / 4);
+#pragma unroll
+            for (int q = 0; q < P / 4; ++q) {
+                const float4 t = __ldg(wk + q);
+                w[4 * q] = t.x; w[4 * q + 1] = t.y; w[4 * q + 2] = t.z; w[4 * q + 3] = t.w;
+            }
+#pragma unroll
+            for (int n = 0; n < NP; ++n) {
+                const float mk = f4(xm[n], kk), hk = f4(xh[n], kk);
+#pragma unroll
+                for (int j = 0; j < HJ; ++j)
+#pragma unroll
+                    for (int g = 0; g < 3; ++g) {
+                        acc[n][j][g] = fmaf(w[6 * j + g], mk, acc[n][j][g]);
+                        acc[n][j][3 + g] = fmaf(w[6 * j + 3 + g], hk, acc[n][j][3 + g]);
+                    }
+            }
+        }
+    }
     float hn[NP][HJ];
 #pragma unroll
     for (int j = 0; j < HJ; ++j) {
         const int o = lane + 32 * j;
-        float ir[NP], iz[NP], in_[NP], hr[NP], hz[NP], hn_[NP];
 #pragma unroll
         for (int n = 0; n < NP; ++n) {
-            ir[n] = a.bih[o]; iz[n] = a.bih[H + o]; in_[n] = a.bih[2 * H + o];
-            hr[n] = a.bhh[o]; hz[n] = a.bhh[H + o]; hn_[n] = a.bhh[2 * H + o];
-        }
-        for (int k = 0; k < H; ++k) {
-            const float *wi = a.wih_t + (size_t)k * 3 * H;
-            const float *wh = a.whh_t + (size_t)k * 3 * H;
-            const float w0 = wi[o], w1 = wi[H + o], w2 = wi[2 * H + o];
-            const float u0 = wh[o], u1 = wh[H + o], u2 = wh[2 * H + o];
-#pragma unroll
-            for (int n = 0; n < NP; ++n) {
-                const float mk = v[n][k], hk = v[n][H + k];
-                ir[n] = fmaf(w0, mk, ir[n]);
-                iz[n] = fmaf(w1, mk, iz[n]);
-                in_[n] = fmaf(w2, mk, in_[n]);
-                hr[n] = fmaf(u0, hk, hr[n]);
-                hz[n] = fmaf(u1, hk, hz[n]);
-                hn_[n] = fmaf(u2, hk, hn_[n]);
-            }
-        }
-#pragma unroll
-        for (int n = 0; n < NP; ++n) {
-            const float r = sigm(ir[n] + hr[n]);
-            const float z = sigm(iz[n] + hz[n]);
-            const float nn = tanhf(in_[n] + r * hn_[n]);
-            hn[n][j] = (1.f - z) * nn + z * hv[n][j];
+            const float r = sigm(acc[n][j][0] + acc[n][j][3]);
+            const float z = sigm(acc[n][j][1] + acc[n][j][4]);
+            const float nn = tanhf(acc[n][j][2] + r * acc[n][j][5]);
+            hn[n][j] = (1.f - z) * nn + z * v[n][H + o];
             if (n < np) a.h_out[(size_t)(i0 + n) * H + o] = hn[n][j];
         }
     }
@@ -195,24 +250,8 @@ __global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
 #pragma unroll
         for (int j = 0; j < HJ; ++j) v[n][lane + 32 * j] = hn[n][j];
     __syncwarp();
-    for (int e = 0; e < 2; ++e) {
-        if (!a.T_out[e]) continue;
-#pragma unroll
-        for (int j = 0; j < HJ; ++j) {
-            const int o = lane + 32 * j;
-            float t[NP];
-#pragma unroll
-            for (int n = 0; n < NP; ++n) t[n] = a.be[e][o];
-            for (int k = 0; k < H; ++k) {
-                const float w = a.we_t[e][k * H + o];
-#pragma unroll
-                for (int n = 0; n < NP; ++n) t[n] = fmaf(w, v[n][k], t[n]);
-            }
-#pragma unroll
-            for (int n = 0; n < NP; ++n)
-                if (n < np) a.T_out[e][(size_t)(i0 + n) * H + o] = t[n];
-        }
-    }
+    for (int e = 0; e < 2; ++e)
+        if (a.T_out[e]) edge_transform<H, NP>(v, a.we_p[e], a.be[e], lane, np, i0, a.T_out[e]);
 }
 
 template <int H>
