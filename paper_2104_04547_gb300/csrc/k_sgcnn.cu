@@ -141,8 +141,15 @@ __global__ void __launch_bounds__(kWarps * 32) sg_transform_kernel(SgTransformAr
         if (a.we_p[e]) edge_transform<H, NP>(v, a.we_p[e], a.be[e], lane, np, i0, a.T[e]);
 }
 
+// Blocks per SM the step kernel is compiled for: four at H = 64 and up to four nodes per warp (64 registers),
+// since the message sums are latency-bound and need the warps (at 80 registers, three blocks, the
+// paper-final model's calls took 3% longer); the other shapes state no minimum (0) and keep the registers
+// the compiler gives them.
 template <int H, int NP>
-__global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
+constexpr int step_min_blocks() { return (H == 64 && NP <= 4) ? 4 : 0; }
+
+template <int H, int NP>
+__global__ void __launch_bounds__(kWarps * 32, step_min_blocks<H, NP>()) sg_step_kernel(SgStepArgs a) {
     constexpr int HJ = H / 32;
     __shared__ __align__(16) float sv[kWarps][NP][2 * H];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -184,61 +191,63 @@ __global__ void __launch_bounds__(kWarps * 32) sg_step_kernel(SgStepArgs a) {
         }
     }
     __syncwarp();
-    // GRU.  Lane l owns outputs o = l + 32 j of each gate.  Its weights for input k are P floats (per j:
-    // W_ih rows r, z, n, then W_hh rows r, z, n, at row o), read as P / 4 16-byte loads; the node vectors
-    // [m, h] are read four inputs at a time.  Every sum runs from the bias over k ascending.
+    // GRU.  Lane l owns outputs o = l + 32 j of each gate, one j at a time (24 accumulators at NP = 4, so
+    // four blocks fit an SM and the latency-bound message sums keep their warps).  Its weights for input k
+    // and output o are six consecutive floats of its P (W_ih rows r, z, n, then W_hh rows r, z, n, at row
+    // o), read as one 16-byte and one 8-byte load; the node vectors [m, h] are read four inputs at a time.
+    // Every sum runs from the bias over k ascending.
     constexpr int P = (6 * HJ + 3) / 4 * 4;
-    float acc[NP][HJ][6];
-#pragma unroll
-    for (int j = 0; j < HJ; ++j) {
-        const int o = lane + 32 * j;
-        float b[6];
-#pragma unroll
-        for (int g = 0; g < 3; ++g) { b[g] = a.bih[g * H + o]; b[3 + g] = a.bhh[g * H + o]; }
-#pragma unroll
-        for (int n = 0; n < NP; ++n)
-#pragma unroll
-            for (int q = 0; q < 6; ++q) acc[n][j][q] = b[q];
-    }
-    const float4 *wl = reinterpret_cast<const float4 *>(a.gru_p) + lane * (P / 4);
-    for (int k0 = 0; k0 < H; k0 += 4) {
-        float4 xm[NP], xh[NP];
-#pragma unroll
-        for (int n = 0; n < NP; ++n) {
-            xm[n] = *reinterpret_cast<const float4 *>(&v[n][k0]);
-            xh[n] = *reinterpret_cast<const float4 *>(&v[n][H + k0]);
-        }
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            float w[P];
-            const float4 *wk = wl + (size_t)(k0 + kk) * 32 * (P / 4);
-#pragma unroll
-            for (int q = 0; q < P / 4; ++q) {
-                const float4 t = __ldg(wk + q);
-                w[4 * q] = t.x; w[4 * q + 1] = t.y; w[4 * q + 2] = t.z; w[4 * q + 3] = t.w;
-            }
-#pragma unroll
-            for (int n = 0; n < NP; ++n) {
-                const float mk = f4(xm[n], kk), hk = f4(xh[n], kk);
-#pragma unroll
-                for (int j = 0; j < HJ; ++j)
-#pragma unroll
-                    for (int g = 0; g < 3; ++g) {
-                        acc[n][j][g] = fmaf(w[6 * j + g], mk, acc[n][j][g]);
-                        acc[n][j][3 + g] = fmaf(w[6 * j + 3 + g], hk, acc[n][j][3 + g]);
-                    }
-            }
-        }
-    }
+    const float *wl = a.gru_p + lane * P;
     float hn[NP][HJ];
 #pragma unroll
     for (int j = 0; j < HJ; ++j) {
         const int o = lane + 32 * j;
+        float acc[NP][6];
+        {
+            float b[6];
+#pragma unroll
+            for (int g = 0; g < 3; ++g) { b[g] = a.bih[g * H + o]; b[3 + g] = a.bhh[g * H + o]; }
+#pragma unroll
+            for (int n = 0; n < NP; ++n)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) acc[n][q] = b[q];
+        }
+        for (int k0 = 0; k0 < H; k0 += 4) {
+            float4 xm[NP], xh[NP];
+#pragma unroll
+            for (int n = 0; n < NP; ++n) {
+                xm[n] = *reinterpret_cast<const float4 *>(&v[n][k0]);
+                xh[n] = *reinterpret_cast<const float4 *>(&v[n][H + k0]);
+            }
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const float *wk = wl + (size_t)(k0 + kk) * 32 * P + 6 * j;   // 16-byte aligned at even j
+                float w[6];
+                if (j % 2 == 0) {
+                    const float4 t = __ldg(reinterpret_cast<const float4 *>(wk));
+                    const float2 u = __ldg(reinterpret_cast<const float2 *>(wk + 4));
+                    w[0] = t.x; w[1] = t.y; w[2] = t.z; w[3] = t.w; w[4] = u.x; w[5] = u.y;
+                } else {
+                    const float2 t = __ldg(reinterpret_cast<const float2 *>(wk));
+                    const float4 u = __ldg(reinterpret_cast<const float4 *>(wk + 2));
+                    w[0] = t.x; w[1] = t.y; w[2] = u.x; w[3] = u.y; w[4] = u.z; w[5] = u.w;
+                }
+#pragma unroll
+                for (int n = 0; n < NP; ++n) {
+                    const float mk = f4(xm[n], kk), hk = f4(xh[n], kk);
+#pragma unroll
+                    for (int g = 0; g < 3; ++g) {
+                        acc[n][g] = fmaf(w[g], mk, acc[n][g]);
+                        acc[n][3 + g] = fmaf(w[3 + g], hk, acc[n][3 + g]);
+                    }
+                }
+            }
+        }
 #pragma unroll
         for (int n = 0; n < NP; ++n) {
-            const float r = sigm(acc[n][j][0] + acc[n][j][3]);
-            const float z = sigm(acc[n][j][1] + acc[n][j][4]);
-            const float nn = tanhf(acc[n][j][2] + r * acc[n][j][5]);
+            const float r = sigm(acc[n][0] + acc[n][3]);
+            const float z = sigm(acc[n][1] + acc[n][4]);
+            const float nn = tanhf(acc[n][2] + r * acc[n][5]);
             hn[n][j] = (1.f - z) * nn + z * v[n][H + o];
             if (n < np) a.h_out[(size_t)(i0 + n) * H + o] = hn[n][j];
         }
