@@ -93,6 +93,42 @@ MUTATIONS = [
     ("latents concatenated in the other order",
      [("    v = np.concatenate([cnn, sg])\n", "    v = np.concatenate([sg, cnn])\n")],
      [sg_pins.test_head_matches_torch, sg_pins.test_tiny_network_end_to_end_matches_torch_restatement]),
+    ("convolution without its bias",
+     [("y = np.zeros((Do, Ho, Wo, Co)) + np.asarray(b, dtype=np.float64)", "y = np.zeros((Do, Ho, Wo, Co))")],
+     [lambda: cnn_pins.test_conv3d_matches_torch_float64(6, 2, 3, 3, 1),
+      cnn_pins.test_cnn_branch_matches_torch_restatement]),
+    ("flatten in (D, H, W, C) order instead of (C, D, H, W)",
+     [("v = x.transpose(3, 0, 1, 2).reshape(-1)", "v = x.reshape(-1)")],
+     [cnn_pins.test_cnn_branch_matches_torch_restatement]),
+    ("stage gate reading h twice instead of [h, h0]",
+     [("hh = np.concatenate([h, h0], axis=1)", "hh = np.concatenate([h, h], axis=1)")],
+     [lambda: sg_pins.test_sg_branch_matches_dense_adjacency_torch("fusion-20grid-ragged")]),
+    ("messages without the edge-transform bias",
+     [("T = h @ W[f\"sg{s}.{e}.w\"].T + W[f\"sg{s}.{e}.b\"]", "T = h @ W[f\"sg{s}.{e}.w\"].T")],
+     [lambda: sg_pins.test_sg_branch_matches_dense_adjacency_torch("fusion-24grid-c32"),
+      sg_pins.test_tiny_network_end_to_end_matches_torch_restatement]),
+    ("gather over every atom, not only the ligand's",
+     [("hl = h[:n_lig]", "hl = h"), ("xl = x_in[:n_lig]", "xl = x_in")],
+     [sg_pins.test_zero_steps_linear_gather_closed_form,
+      lambda: sg_pins.test_sg_branch_matches_dense_adjacency_torch("fusion-20grid-ragged")]),
+    ("gated gather reading the first stage's input instead of the last",
+     [("        x_in = h\n        for step in range(st[\"steps\"]):", "        for step in range(st[\"steps\"]):")],
+     [lambda: sg_pins.test_sg_branch_matches_dense_adjacency_torch("fusion-20grid-ragged")]),
+    ("GRU blend with z and 1 - z swapped",
+     [("return (1.0 - z) * nn + z * h", "return z * nn + (1.0 - z) * h")],
+     [sg_pins.test_gru_matches_torch_grucell]),
+    ("SELU without its scale",
+     [("return SELU_SCALE * np.where(x > 0, x,", "return np.where(x > 0, x,")],
+     [sg_pins.test_activations_match_torch, sg_pins.test_head_matches_torch]),
+    ("non-covalent set also holding the covalent pairs",
+     [("nc = (~cov) & (s < n2) & off", "nc = (s < n2) & off")],
+     [graph_pins.test_graph_structure, lambda: graph_pins.test_edges_match_kdtree(0)]),
+    ("grid centred on the origin instead of on the ligand centroid",
+     [("return (c - half).astype(np.float32)", "return c.astype(np.float32)")],
+     [vox_pins.test_containing_voxel_on_boundary_and_centroid_rule]),
+    ("max-pool window of the first voxel only",
+     [(".max(axis=(1, 3, 5))", "[:, 0, :, 0, :, 0]")],
+     [cnn_pins.test_maxpool_matches_torch, cnn_pins.test_cnn_branch_matches_torch_restatement]),
 ]
 
 
