@@ -42,7 +42,7 @@ L2_FLUSH_BYTES = 256 << 20
 # tensor but the weights scales with the pose count).  Valid only for the kernel source they were taken
 # on: the sha256 prefix of the conv kernel's source code (comments removed); other code reports null.
 CONV_TRAFFIC = {
-    "src": "71b02756495df8e1",
+    "src": "bee8dc0556ebdbad",
     "poses": 64,
     "bf16": [1135.8e6, 1680.9e6, 1647.2e6, 1080.4e6],
     "fp8": [1148.8e6, 2113.4e6, 2113.5e6, 554.4e6],

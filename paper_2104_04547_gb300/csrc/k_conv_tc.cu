@@ -740,11 +740,13 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     }
     const int T = sp.T > 0 ? sp.T : conv_tc_tile_slices(c_out);
     const int chunk_ch = sp.elem == 2 ? 16 : 32;
-    const bool t_ok = (c_out <= 64 && (T == 4 || T == 8)) || (c_out <= 32 && T == 16) ||
+    // 16 slices per CTA only at stride 1 (the strided phases are built and checked for at most 8)
+    const bool t_ok = (c_out <= 64 && (T == 4 || T == 8)) || (c_out <= 32 && T == 16 && stride == 1) ||
                       (c_out == 128 && (T == 2 || T == 4)) ||
                       (c_out == 256 && T == 2);
     if (!t_ok) {
-        snprintf(why, why_len, "unsupported output slices per CTA (%d) for %d output channels", T, c_out);
+        snprintf(why, why_len, "unsupported output slices per CTA (%d) for %d output channels at stride %d", T, c_out,
+                 stride);
         return -1;
     }
     if (c_out != 32 && c_out != 64 && c_out != 128 && c_out != 256) {
