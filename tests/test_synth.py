@@ -1,5 +1,7 @@
 """The seeded generators: deterministic, within the stated ranges, and free of
-atom pairs within 1e-5 A^2 of a squared edge cutoff."""
+atom pairs within 1e-5 A^2 of a squared edge cutoff; the uneven pools' pose
+groups are one ligand moved rigidly (plus jitter) in one pocket, with ligand
+and pocket sizes distributed as stated."""
 
 import numpy as np
 
@@ -46,3 +48,47 @@ def test_blob_layout_size_and_order():
     first = np.frombuffer(blob[:4 * W["conv0.w"].size], dtype="<f4")
     assert np.array_equal(first, W["conv0.w"].reshape(-1))
     assert weights.cnn_out_shape(configs.model("fusion-48grid-c64")) == (128, 12)
+
+
+def _kabsch_rmsd(a, b):
+    """RMSD of b onto a after the best rigid superposition (Kabsch: SVD of the covariance)."""
+    a = a - a.mean(axis=0)
+    b = b - b.mean(axis=0)
+    u, _, vt = np.linalg.svd(b.T @ a)
+    d = np.sign(np.linalg.det(u @ vt))
+    r = u @ np.diag([1.0, 1.0, d]) @ vt
+    return float(np.sqrt(((b @ r - a) ** 2).sum(axis=1).mean()))
+
+
+def test_pose_group_is_one_ligand_rigidly_moved_in_one_pocket():
+    """The uneven pools' recipe: the n_rot poses of a group share the ligand size, the features and the pocket;
+    each ligand is the same rigid body up to the per-atom jitter (about 0.5 A per axis: the RMSD between two
+    poses after superposition is about 0.5 sqrt(3) sqrt(2) = 1.2 A), turned by a different rotation."""
+    group = poses.make_pose_group(500123, 4)
+    again = poses.make_pose_group(500123, 4)
+    assert all(np.array_equal(p[0], q[0]) and np.array_equal(p[1], q[1]) for p, q in zip(group, again))
+    n_lig = group[0][2]
+    assert 8 <= n_lig <= 90 and 150 <= len(group[0][0]) - n_lig <= 1000
+    lig0 = group[0][0][:n_lig].astype(np.float64)
+    for xyz, feat, nl in group[1:]:
+        assert nl == n_lig and np.array_equal(feat, group[0][1])
+        # the pocket stays put (up to the 0.01 A nudges that clear near-cutoff pairs)
+        assert np.abs(xyz[n_lig:] - group[0][0][n_lig:]).max() < 0.1
+        lig = xyz[:n_lig].astype(np.float64)
+        assert 0.6 < _kabsch_rmsd(lig0, lig) < 1.8
+        # a different orientation: without superposition the ligands are far apart
+        c = lig0.mean(axis=0) - lig.mean(axis=0)
+        assert np.sqrt((((lig + c) - lig0) ** 2).sum(axis=1).mean()) > 2.0
+        assert poses._near_cutoff_pairs(xyz) == []
+
+
+def test_uneven_pool_size_distribution():
+    """Ligand sizes log-normal around a median of 32 atoms (clipped to 8..90), pockets uniform in 150..1000."""
+    pool = poses.make_uneven_pool(80, 1)
+    n_lig = np.array([p[2] for p in pool])
+    n_poc = np.array([len(p[0]) - p[2] for p in pool])
+    assert n_lig.min() >= 8 and n_lig.max() <= 90
+    assert 27 <= np.median(n_lig) <= 39
+    assert 0.3 <= np.std(np.log(n_lig)) <= 0.6
+    assert n_poc.min() >= 150 and n_poc.max() <= 1000
+    assert 450 <= n_poc.mean() <= 700
