@@ -1,9 +1,11 @@
 """The seeded generators: deterministic, within the stated ranges, and free of
 atom pairs within 1e-5 A^2 of a squared edge cutoff; the uneven pools' pose
 groups are one ligand moved rigidly (plus jitter) in one pocket, with ligand
-and pocket sizes distributed as stated."""
+and pocket sizes distributed as stated; the random-init weights follow the
+stated bounds (restated from each tensor's shape) with uniform moments."""
 
 import numpy as np
+import pytest
 
 from synth import configs, poses, weights
 
@@ -92,3 +94,38 @@ def test_uneven_pool_size_distribution():
     assert 0.3 <= np.std(np.log(n_lig)) <= 0.6
     assert n_poc.min() >= 150 and n_poc.max() <= 1000
     assert 450 <= n_poc.mean() <= 700
+
+
+def _expected_bound(name, W, desc):
+    """The init rule of the weights module, restated from each tensor's shape: Kaiming-uniform sqrt(6 / fan_in)
+    for ReLU layers (convs, CNN dense), U(+-1/sqrt(fan_in)) for biases, message transforms, gates, the gather
+    and the last head layer, U(+-1/sqrt(H)) for the GRU, LeCun-uniform sqrt(3 / fan_in) for SELU head layers."""
+    H = desc["sg_hidden"]
+    if ".gru." in name:
+        return 1.0 / np.sqrt(H)
+    layer, kind = name.rsplit(".", 1)
+    w = W[layer + ".w"] if kind == "b" else W[name]
+    fan = int(np.prod(w.shape[1:]))
+    if kind == "b":
+        return 1.0 / np.sqrt(fan)
+    if name.startswith("conv") or name == "cnn_dense.w":
+        return np.sqrt(6.0 / fan)
+    if name.startswith("head"):
+        last = int(layer[4:]) == len(desc["head"]) - 1
+        return 1.0 / np.sqrt(fan) if last else np.sqrt(3.0 / fan)
+    return 1.0 / np.sqrt(fan)
+
+
+def test_weight_init_bounds_and_moments():
+    desc = configs.model("fusion-48grid-c64")
+    W = weights.init_weights(desc, 0)
+    names = [n for n, _s, _k, _f in weights.layout(desc)]
+    assert sorted(names) == sorted(W)
+    for name in names:
+        w = W[name].astype(np.float64)
+        b = _expected_bound(name, W, desc)
+        assert np.abs(w).max() <= b * (1 + 1e-6), name
+        if w.size >= 4096:   # enough draws to see the whole range and the uniform moments
+            assert np.abs(w).max() >= 0.99 * b, name
+            assert abs(w.mean()) < 0.05 * b, name
+            assert w.var() == pytest.approx(b * b / 3.0, rel=0.05), name
