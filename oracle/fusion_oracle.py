@@ -364,13 +364,3 @@ def score_pose(desc, W, xyz, feat, n_lig, stages=None, origin=None):
         stages["affinity"] = a
     return a
 
-
-def score_batch(desc, W, batch, poses=None):
-    """Affinities of the poses (all, or the listed indices) of a packed batch."""
-    off = batch["atom_off"]
-    idx = range(len(batch["n_lig"])) if poses is None else poses
-    out = []
-    for p in idx:
-        a, b = int(off[p]), int(off[p + 1])
-        out.append(score_pose(desc, W, batch["xyz"][a:b], batch["feat"][a:b], int(batch["n_lig"][p])))
-    return np.array(out)
