@@ -292,7 +292,8 @@ int fusion_server_submit(fusion_server *s, const float *xyz, const float *feat, 
 
 /* Non-blocking: FUSION_OK with the affinity and the latency from submission
  * to completion (seconds) once the pose is scored (each result is returned
- * once), FUSION_EAGAIN while it is pending. */
+ * once), FUSION_EAGAIN while it is pending; FUSION_EINVAL for a ticket this
+ * server never issued or whose result was already collected. */
 int fusion_server_poll(fusion_server *s, uint64_t ticket, float *affinity, double *latency_s);
 
 /* Wait until every submitted pose is scored (FUSION_ETIMEOUT after timeout_s). */
@@ -318,14 +319,19 @@ void fusion_server_destroy(fusion_server *s);
  * that loads it until the process exits.
  *
  * x: device float32 [B][K]; w: device float32 [N][K]; bias: device float32 [N];
- * y: device float32 [B][N]; all caller-owned.  K must be a positive multiple
+ * y: device float32 [B][N]; all caller-owned.  x and w must be 16-byte
+ * aligned (they are read 16 bytes at a time), bias and y 4-byte aligned;
+ * other pointers return FUSION_EINVAL before anything is launched.  K must be a positive multiple
  * of 8, and splits(K) x B x N must fit FUSION_NOALLOC_MAX_PARTIALS floats,
  * where splits(K) = clamp(K / 2048, 1, 128); larger sizes return FUSION_EINVAL
  * with a message naming the limit.  The kernels are enqueued on `cuda_stream`
  * (a cudaStream_t; NULL is the legacy default stream) and the call returns
  * without waiting for them.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  Every call shares the one array:
+ * that first call before any stream capture.  The address is kept until the
+ * process exits and does not survive cudaDeviceReset: do not call this entry
+ * point again after resetting the device.  A CUDA error already pending when
+ * the call starts is returned as FUSION_ECUDA and nothing is launched.  Every call shares the one array:
  * calls whose kernels overlap on the GPU race and must be serialised by the
  * caller (for example by issuing them on one stream).  Nothing in the array
  * needs clearing between calls. */

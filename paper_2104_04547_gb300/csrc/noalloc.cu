@@ -14,13 +14,17 @@
 // lifetime of the process (8 MiB).  Host code cannot use the array's name as a
 // device address, so the address is looked up once per device with
 // cudaGetSymbolAddress on the first call made with that device current; that
-// first call should therefore come before any stream capture.  All calls share
+// first call should therefore come before any stream capture.  The looked-up
+// address is kept for the life of the process: it does not survive a
+// cudaDeviceReset of that device, after which this entry point must not be
+// called again in the same process.  All calls share
 // the one array: calls whose kernels overlap on the GPU (different streams, or
 // different host threads on one device) race on it and must be serialised by
 // the caller.  Nothing in the array needs to start at zero: every partial the
 // reduction reads is written earlier in the same call.
 #include "fusion_internal.cuh"
 
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -41,6 +45,12 @@ int noalloc_fail(int code, const std::string &m) { return fusion::set_last_error
 extern "C" int fusion_cnn_dense_noalloc(const float *x, const float *w, const float *bias, int32_t B, int32_t N,
                                         int32_t K, int32_t relu, float *y, void *cuda_stream) {
     if (!x || !w || !bias || !y) return noalloc_fail(FUSION_EINVAL, "NULL pointer argument");
+    // x and w are read 16 bytes at a time (rows of K floats, K a multiple of 8, stay aligned), bias and y
+    // one float at a time: an offset view would make the kernel fault and lose the caller's context
+    if (((uintptr_t)x | (uintptr_t)w) & 15u)
+        return noalloc_fail(FUSION_EINVAL, "x and w must be 16-byte aligned");
+    if (((uintptr_t)bias | (uintptr_t)y) & 3u)
+        return noalloc_fail(FUSION_EINVAL, "bias and y must be 4-byte aligned");
     if (B < 1 || N < 1 || K < 8 || K % 8 != 0)
         return noalloc_fail(FUSION_EINVAL, "need B >= 1, N >= 1 and K a positive multiple of 8");
     const int splits = fusion::dense_splits(K);
@@ -65,6 +75,11 @@ extern "C" int fusion_cnn_dense_noalloc(const float *x, const float *w, const fl
         }
         scratch = g_scratch_addr[dev];
     }
+    // an error left pending by earlier work would otherwise be reported below as this call's launch failure
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess)
+        return noalloc_fail(FUSION_ECUDA, std::string("a CUDA error was pending before this call (nothing launched): ") +
+                                              cudaGetErrorString(e));
     fusion::DenseArgs a{x, w, bias, static_cast<float *>(scratch), y, B, N, K, splits, 0, relu ? 1 : 0};
     fusion::launch_dense(a, static_cast<cudaStream_t>(cuda_stream));
     e = cudaGetLastError();

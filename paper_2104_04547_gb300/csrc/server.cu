@@ -31,6 +31,7 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 namespace {
@@ -68,6 +69,7 @@ struct fusion_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request> queue;
     std::unordered_map<uint64_t, Result> done;
+    std::unordered_set<uint64_t> outstanding;   // submitted, result not yet collected
     uint64_t next_ticket = 1;
     int64_t inflight = 0;
     bool stop = false;
@@ -220,6 +222,7 @@ int fusion_server_submit(fusion_server *s, const float *xyz, const float *feat, 
         r.ticket = s->next_ticket++;
         r.t_arrive = Clock::now();
         *ticket = r.ticket;
+        s->outstanding.insert(r.ticket);
         s->queue.push_back(std::move(r));
         s->submitted += 1;
     }
@@ -233,10 +236,12 @@ int fusion_server_poll(fusion_server *s, uint64_t ticket, float *affinity, doubl
     auto it = s->done.find(ticket);
     if (it == s->done.end()) {
         if (ticket == 0 || ticket >= s->next_ticket) return srv_fail(FUSION_EINVAL, "unknown ticket");
+        if (!s->outstanding.count(ticket)) return srv_fail(FUSION_EINVAL, "ticket already collected");
         return FUSION_EAGAIN;
     }
     const Result r = it->second;
     s->done.erase(it);
+    s->outstanding.erase(ticket);
     if (affinity) *affinity = r.affinity;
     if (latency_s) *latency_s = r.latency_s;
     if (r.status != FUSION_OK) return srv_fail(r.status, "scoring the batch of this pose failed");

@@ -1,7 +1,7 @@
 """Continuous-batching server through the C ABI: every pose's result is the
 same as scoring that pose alone, whatever mix of uneven poses it was batched
-with; bad poses are rejected at submission; a full queue answers EAGAIN; the
-HBM budget limits the slots."""
+with; bad poses are rejected at submission; a full queue answers EAGAIN; a result
+is collected once; the HBM budget limits the slots."""
 
 import time
 
@@ -68,6 +68,10 @@ def test_rejections_and_queue_capacity(F):
     srv.drain(timeout_s=30.0)
     vals = [srv.poll(v)[0] for v in t]
     assert vals[0] == vals[1] == vals[2]
+    # a result is handed out once: polling a collected ticket again is an error, not a pending result
+    with pytest.raises(F.FusionError) as e:
+        srv.poll(t[0])
+    assert e.value.code == F.FUSION_EINVAL and "already collected" in str(e.value)
     assert srv.stats()["rejected"] == 1
     srv.close()
 
