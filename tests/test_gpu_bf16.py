@@ -78,6 +78,9 @@ def test_full_size_bf16(F):
     assert g["input_digest"] == poses.digest(batch)
     m = F.Model(desc, weights.to_blob(desc, W), max_poses=64, max_atoms=1200, keep_stages=True)
     got = m.score(batch).copy()
+    idx = [int(k) for k in g["poses"]]
+    d_or = np.abs(got[idx] - np.array([g["poses"][str(i)]["affinity"] for i in idx]))
+    print(f"vs the FP64 oracle over {len(idx)} stored poses: mean |d| {d_or.mean():.2e}, max |d| {d_or.max():.2e}")
     for k, v in g["poses"].items():
         assert abs(float(got[int(k)]) - v["affinity"]) <= BF16_AFFINITY_TOL, (k, got[int(k)], v["affinity"])
     # the residual 7^3 layer and the stride-2 layer of one pose, in isolation

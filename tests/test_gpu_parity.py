@@ -5,8 +5,8 @@
 * voxel grid, conv maps, latents: FP32 rounding tolerances;
 * affinity: <= 1e-4 absolute (the FP32 target);
 at the small single-pose model, a ragged 20^3 model over a mixed batch (tiles
-and a ragged tail), and the full-size model on the 64-pose batch (sampled
-poses against stored oracle values, edges and grids of every / sampled pose).
+and a ragged tail), and the full-size model on the 64-pose batch (every pose
+against stored oracle values, edges of every pose, grids of sampled poses).
 """
 
 import numpy as np
@@ -94,6 +94,9 @@ def test_full_size_batch64_sampled(F):
     m = F.Model(desc, weights.to_blob(desc, W), max_poses=64, max_atoms=1200)
     got = m.score(batch)
     assert np.all(np.isfinite(got))
+    idx = [int(k) for k in g["poses"]]
+    d_or = np.abs(got[idx] - np.array([g["poses"][str(i)]["affinity"] for i in idx]))
+    print(f"f32 vs the FP64 oracle over {len(idx)} stored poses: mean |d| {d_or.mean():.2e}, max |d| {d_or.max():.2e}")
     for k, v in g["poses"].items():
         p = int(k)
         np.testing.assert_allclose(m.fetch(F.STAGE_CNN_LATENT, p), v["cnn_latent"], rtol=1e-4, atol=1e-5)
