@@ -33,13 +33,16 @@ the earlier FAST work, which is not available; the readings used here are:
   (u_d = lower voxel edge) over the cube of voxels within +-k of its
   containing voxel; voxels outside the grid are dropped, never renormalised;
 * conv: same padding k // 2, bias, ReLU; residual block y = x + ReLU(conv(x));
-  pool 2^3 stride 2; flatten in (C, D, H, W) order; dense + ReLU;
+  pool 2^3 stride 2; flatten in (C, D, H, W) order; dense + ReLU (and, when the
+  model has one, a second dense + ReLU whose output is the CNN latent);
 * edges (exact float32, no fused multiply-add): s = fl(fl(fl(dx dx) + fl(dy dy)) + fl(dz dz))
   with dx = fl(x_i - x_j); covalent iff s < fl(c_cov c_cov); non-covalent iff
   not covalent and s < fl(c_nc c_nc); i != j;
-* h0 = features zero-padded to the hidden width H; message
+* h0 = features zero-padded to the first stage's width (the hidden width H
+  unless a stage width is given); message
   m_i = sum over edge types e and neighbours j of (W_e h_j + b_e);
-  h <- GRU(m, h); gate between stages h <- sigmoid(W_i [h, h0] + b_i) * (W_j h + b_j);
+  h <- GRU(m, h); gate between stages h <- sigmoid(W_i [h, h0] + b_i) * (W_j h + b_j),
+  which maps to the next stage's width;
 * gather over ligand atoms i < n_lig: gated sum
   sum_i sigmoid(W_g [h_i, x_i] + b_g) * (W_o h_i + b_o), x_i = the input of the
   last stage, or the linear sum sum_i (W h_i + b);
@@ -181,6 +184,12 @@ def cnn_branch(desc, W, G, stages=None):
             stages["pool"] = x
     v = x.transpose(3, 0, 1, 2).reshape(-1)
     out = relu(W["cnn_dense.w"].astype(np.float64) @ v + W["cnn_dense.b"])
+    if desc.get("cnn_dense2"):
+        # a second dense layer (Section 3.3.1: the second dense layer is the first reduced by a factor of 2);
+        # the latent the fusion layers read is the last hidden layer, Layer^{M-1} (Section 2.2)
+        if stages is not None:
+            stages["cnn_dense1"] = out
+        out = relu(W["cnn_dense2.w"].astype(np.float64) @ out + W["cnn_dense2.b"])
     if stages is not None:
         stages["cnn_latent"] = out
     return out
@@ -246,18 +255,29 @@ def _edge_names(mask):
     return out
 
 
-def sg_branch(desc, W, feat, n_lig, graph, stages=None):
-    """SG-CNN latent (Section 3.3.1, Table II): gated graph conv stages + ligand gather."""
-    W = {k: v.astype(np.float64) for k, v in W.items() if k.startswith(("sg", "gather"))}
+def stage_widths(desc):
+    """Node-state width of each SG-CNN stage: sg_width[s] when given (nonzero), else sg_hidden."""
     H = desc["sg_hidden"]
+    w = list(desc.get("sg_width") or [])
+    return [w[s] if s < len(w) and w[s] else H for s in range(len(desc["sg_stages"]))]
+
+
+def sg_branch(desc, W, feat, n_lig, graph, stages=None):
+    """SG-CNN latent (Section 3.3.1, Table II): gated graph conv stages + ligand gather.
+
+    Stage s keeps node states of its own width w_s (the first stage at least the feature count); the gate
+    between stages maps [h, h0] to the next stage's width (the covalent gather width of Table II)."""
+    W = {k: v.astype(np.float64) for k, v in W.items() if k.startswith(("sg", "gather"))}
+    widths = stage_widths(desc)
     N = len(feat)
-    h0 = np.zeros((N, H))
+    h0 = np.zeros((N, widths[0]))
     h0[:, :feat.shape[1]] = np.asarray(feat, dtype=np.float64)
     h = h0
     x_in = h0
     nst = len(desc["sg_stages"])
     for s, st in enumerate(desc["sg_stages"]):
         x_in = h
+        H = widths[s]
         for step in range(st["steps"]):
             m = np.zeros((N, H))
             for e in _edge_names(st["edges"]):

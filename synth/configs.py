@@ -106,9 +106,14 @@ FUSION_RAGGED = dict(
 )
 
 # The architecture of the final models in Tables II, III and V: 3D-CNN with
-# 32 then 64 filters, 5^3 then 3^3 kernels, residual option 2, dense 128;
-# SG-CNN covalent K=6 at 2.24 A, non-covalent K=3 at 5.22 A, gather width 128;
-# four SELU fusion layers.  Grid 48^3 at 1 A.
+# 32 then 64 filters, 5^3 then 3^3 kernels, residual option 2, dense 128 then
+# 128 / 2 = 64 (Section 3.3.1), whose output is the CNN latent (Layer^{M-1},
+# Section 2.2); SG-CNN (PotentialNet): a covalent stage of K=6 steps at 2.24 A
+# on the 19 atom features, gated to the covalent gather width 24, then a
+# non-covalent stage of K=3 steps at 5.22 A at width 24 over both edge types,
+# gated and summed over the ligand to the non-covalent gather width 128 (the SG
+# latent, Layer^{N-3}); four SELU fusion layers.  Grid 48^3 at 1 A.  The graph
+# kernels carry both stages at width 32.
 FUSION_PAPER = dict(
     name="fusion-paper-final",
     n_feat=N_FEAT,
@@ -117,7 +122,9 @@ FUSION_PAPER = dict(
           _conv(32, 64, 3, stride=2), _conv(64, 64, 3, residual=1)],
     pool=2,
     cnn_dense=128,
-    sg_hidden=64,
+    cnn_dense2=64,
+    sg_hidden=32,
+    sg_width=[19, 24],
     sg_stages=[dict(steps=6, edges=EDGE_COV), dict(steps=3, edges=EDGE_COV | EDGE_NC)],
     sg_gate=1,
     sg_gather="gated",
@@ -147,8 +154,19 @@ FUSION_FULL_MID = _variant(FUSION_FULL, "fusion-48grid-c64-mid", fusion="mid", c
 FUSION_FULL_LATE = _variant(FUSION_FULL, "fusion-48grid-c64-late", fusion="late", cnn_out=[64, 1],
                             sg_out=[64, 1], head=[])
 
+# The paper-final branches in the earlier fusion forms.  Late Fusion: each model's own output layers on its
+# latent, the 3D-CNN's output layer (64 -> 1) and the SG-CNN's dense layers reduced from the gather width by a
+# factor of 1.5 and then 2 (128 -> 85 -> 42, Section 3.3.1) before its output layer.  Mid-level Fusion (Table
+# IV): model-specific dense layers, their outputs concatenated after the latents, five residual fusion layers
+# (the widths are not given in the paper; chosen here).
+FUSION_PAPER_LATE = _variant(FUSION_PAPER, "fusion-paper-final-late", fusion="late", cnn_out=[1],
+                             sg_out=[85, 42, 1], head=[])
+FUSION_PAPER_MID = _variant(FUSION_PAPER, "fusion-paper-final-mid", fusion="mid", cnn_out=[32], sg_out=[64],
+                            head=[288, 288, 128, 128, 1], head_residual=1)
+
 MODELS = {m["name"]: m for m in (FUSION_TINY, FUSION_FULL, FUSION_RAGGED, FUSION_PAPER, FUSION_TINY_MID,
-                                 FUSION_TINY_LATE, FUSION_FULL_MID, FUSION_FULL_LATE)}
+                                 FUSION_TINY_LATE, FUSION_FULL_MID, FUSION_FULL_LATE, FUSION_PAPER_LATE,
+                                 FUSION_PAPER_MID)}
 
 
 def model(name: str, dtype: str | None = None) -> dict:

@@ -7,7 +7,8 @@ No trained checkpoint exists, so weights are drawn from
   bound sqrt(6 / fan_in), fan_in = C_in k^3 (or the input width);
 * biases, message transforms, gates and the last head layer:
   U(+-1/sqrt(fan_in));
-* GRU matrices and biases: U(+-1/sqrt(H)) (the usual GRU init);
+* GRU matrices and biases: U(+-1/sqrt(w)) with w the stage's node-state width
+  (the usual GRU init);
 * SELU head layers: LeCun-uniform, bound sqrt(3 / fan_in).
 
 The blob is every tensor of ``layout(desc)`` in order, each row-major
@@ -15,7 +16,10 @@ float32 little-endian, with no header or padding.  Tensor shapes follow the
 PyTorch conventions: conv ``[C_out][C_in][kd][kh][kw]``, linear ``[out][in]``,
 GRU ``w_ih``/``w_hh`` ``[3H][H]`` with gate rows in (reset, update, new)
 order.  The CNN dense layer's input index is the (C, D, H, W) flattening of
-the pooled map.
+the pooled map.  A model with a second CNN dense layer (``cnn_dense2``) has
+it right after the first; SG-CNN stages of their own widths (``sg_width``)
+have matrices of those widths, the gate between stages mapping
+[h (w_0), h0 (w_0)] to w_1.
 """
 
 from __future__ import annotations
@@ -36,6 +40,13 @@ def cnn_out_shape(desc):
     if desc["pool"] and desc["pool"] > 1:
         n = n // desc["pool"]
     return c, n
+
+
+def stage_widths(desc):
+    """Node-state width of each SG-CNN stage: sg_width[s] when given (nonzero), else sg_hidden."""
+    H = desc["sg_hidden"]
+    w = list(desc.get("sg_width") or [])
+    return [w[s] if s < len(w) and w[s] else H for s in range(len(desc["sg_stages"]))]
 
 
 def edge_types(mask):
@@ -60,8 +71,14 @@ def layout(desc):
     flat = c * n ** 3
     L.append(("cnn_dense.w", (desc["cnn_dense"], flat), "kaiming", flat))
     L.append(("cnn_dense.b", (desc["cnn_dense"],), "bias", flat))
-    H = desc["sg_hidden"]
+    d2 = desc.get("cnn_dense2", 0)
+    if d2:
+        L.append(("cnn_dense2.w", (d2, desc["cnn_dense"]), "kaiming", desc["cnn_dense"]))
+        L.append(("cnn_dense2.b", (d2,), "bias", desc["cnn_dense"]))
+    cnn_latent = d2 or desc["cnn_dense"]
+    wid = stage_widths(desc)
     for s, st in enumerate(desc["sg_stages"]):
+        H = wid[s]
         for e in edge_types(st["edges"]):
             L.append((f"sg{s}.{e}.w", (H, H), "bias", H))
             L.append((f"sg{s}.{e}.b", (H,), "bias", H))
@@ -70,11 +87,13 @@ def layout(desc):
         L.append((f"sg{s}.gru.b_ih", (3 * H,), "gru", H))
         L.append((f"sg{s}.gru.b_hh", (3 * H,), "gru", H))
         if desc["sg_gate"] and s + 1 < len(desc["sg_stages"]):
-            L.append((f"sg{s}.gate.wi", (H, 2 * H), "bias", 2 * H))
-            L.append((f"sg{s}.gate.bi", (H,), "bias", 2 * H))
-            L.append((f"sg{s}.gate.wj", (H, H), "bias", H))
-            L.append((f"sg{s}.gate.bj", (H,), "bias", H))
+            Hn = wid[s + 1]
+            L.append((f"sg{s}.gate.wi", (Hn, H + wid[0]), "bias", H + wid[0]))
+            L.append((f"sg{s}.gate.bi", (Hn,), "bias", H + wid[0]))
+            L.append((f"sg{s}.gate.wj", (Hn, H), "bias", H))
+            L.append((f"sg{s}.gate.bj", (Hn,), "bias", H))
     G = desc["sg_gather_width"]
+    H = wid[-1]
     if desc["sg_gather"] == "gated":
         L.append(("gather.wg", (G, 2 * H), "bias", 2 * H))
         L.append(("gather.bg", (G,), "bias", 2 * H))
@@ -85,7 +104,7 @@ def layout(desc):
         L.append(("gather.b", (G,), "bias", H))
     mode = desc.get("fusion", "coherent")
     # branch output layers: Late Fusion's own affinity stacks (ReLU between), Mid-level's dense layers (SELU)
-    for br, fin in (("cnn_out", desc["cnn_dense"]), ("sg_out", G)):
+    for br, fin in (("cnn_out", cnn_latent), ("sg_out", G)):
         widths = desc.get(br, [])
         for l, w in enumerate(widths):
             last = l + 1 == len(widths)
@@ -93,7 +112,7 @@ def layout(desc):
             L.append((f"{br}{l}.w", (w, fin), kind, fin))
             L.append((f"{br}{l}.b", (w,), "bias", fin))
             fin = w
-    fin = desc["cnn_dense"] + G
+    fin = cnn_latent + G
     if mode == "mid":
         fin += desc["cnn_out"][-1] + desc["sg_out"][-1]
     for l, w in enumerate(desc["head"]):
@@ -113,9 +132,7 @@ def init_weights(desc, seed: int):
             bound = np.sqrt(6.0 / fan)
         elif kind == "lecun":
             bound = np.sqrt(3.0 / fan)
-        elif kind == "gru":
-            bound = 1.0 / np.sqrt(desc["sg_hidden"])
-        else:
+        else:                                          # bias-style, and GRU (fan = the stage's width)
             bound = 1.0 / np.sqrt(fan)
         W[name] = ((rng.random(shape, dtype=np.float32) * 2.0 - 1.0) * np.float32(bound)).astype(np.float32)
     return W

@@ -60,9 +60,12 @@ def test_maxpool_matches_torch():
     np.testing.assert_array_equal(O.maxpool3d(x, 2), ref)
 
 
-def test_cnn_branch_matches_torch_restatement():
+@pytest.mark.parametrize("dense2", [0, 16])
+def test_cnn_branch_matches_torch_restatement(dense2):
+    """The CNN branch, and with a second dense layer (Section 3.3.1) whose output is the latent."""
     from synth import configs, weights
     desc = configs.model("fusion-20grid-ragged")
+    desc["cnn_dense2"] = dense2
     W = weights.init_weights(desc, 4)
     rng = np.random.default_rng(4)
     G = np.abs(rng.normal(size=(20, 20, 20, 19))) * 0.1
@@ -74,5 +77,8 @@ def test_cnn_branch_matches_torch_restatement():
         x = x + y if cv["residual"] else y
     x = F.max_pool3d(x, 2)
     exp = F.relu(F.linear(x.reshape(-1), torch.from_numpy(W["cnn_dense.w"]).double(),
-                          torch.from_numpy(W["cnn_dense.b"]).double())).numpy()
-    np.testing.assert_allclose(got, exp, rtol=1e-10, atol=1e-12)
+                          torch.from_numpy(W["cnn_dense.b"]).double()))
+    if dense2:
+        exp = F.relu(F.linear(exp, torch.from_numpy(W["cnn_dense2.w"]).double(),
+                              torch.from_numpy(W["cnn_dense2.b"]).double()))
+    np.testing.assert_allclose(got, exp.numpy(), rtol=1e-10, atol=1e-12)

@@ -48,11 +48,11 @@ MUTATIONS = [
       cnn_pins.test_conv3d_unit_kernel_is_matmul]),
     ("average pooling instead of max",
      [(".max(axis=(1, 3, 5))", ".mean(axis=(1, 3, 5))")],
-     [cnn_pins.test_maxpool_matches_torch, cnn_pins.test_cnn_branch_matches_torch_restatement]),
+     [cnn_pins.test_maxpool_matches_torch, lambda: cnn_pins.test_cnn_branch_matches_torch_restatement(0)]),
     ("ReLU after the residual add",
      [("        y = relu(conv3d(x, W[f\"conv{i}.w\"], W[f\"conv{i}.b\"], cv[\"stride\"]))\n        if cv[\"residual\"]:\n            y = x + y",
        "        y = conv3d(x, W[f\"conv{i}.w\"], W[f\"conv{i}.b\"], cv[\"stride\"])\n        if cv[\"residual\"]:\n            y = x + y\n        y = relu(y)")],
-     [cnn_pins.test_cnn_branch_matches_torch_restatement]),
+     [lambda: cnn_pins.test_cnn_branch_matches_torch_restatement(0)]),
     ("non-strict cutoff",
      [("cov = (s < c2) & off", "cov = (s <= c2) & off"), ("nc = (~cov) & (s < n2) & off", "nc = (~cov) & (s <= n2) & off")],
      [graph_pins.test_boundary_pairs_use_strict_inequality]),
@@ -96,10 +96,10 @@ MUTATIONS = [
     ("convolution without its bias",
      [("y = np.zeros((Do, Ho, Wo, Co)) + np.asarray(b, dtype=np.float64)", "y = np.zeros((Do, Ho, Wo, Co))")],
      [lambda: cnn_pins.test_conv3d_matches_torch_float64(6, 2, 3, 3, 1),
-      cnn_pins.test_cnn_branch_matches_torch_restatement]),
+      lambda: cnn_pins.test_cnn_branch_matches_torch_restatement(0)]),
     ("flatten in (D, H, W, C) order instead of (C, D, H, W)",
      [("v = x.transpose(3, 0, 1, 2).reshape(-1)", "v = x.reshape(-1)")],
-     [cnn_pins.test_cnn_branch_matches_torch_restatement]),
+     [lambda: cnn_pins.test_cnn_branch_matches_torch_restatement(0)]),
     ("stage gate reading h twice instead of [h, h0]",
      [("hh = np.concatenate([h, h0], axis=1)", "hh = np.concatenate([h, h], axis=1)")],
      [lambda: sg_pins.test_sg_branch_matches_dense_adjacency_torch("fusion-20grid-ragged")]),
@@ -107,12 +107,22 @@ MUTATIONS = [
      [("T = h @ W[f\"sg{s}.{e}.w\"].T + W[f\"sg{s}.{e}.b\"]", "T = h @ W[f\"sg{s}.{e}.w\"].T")],
      [lambda: sg_pins.test_sg_branch_matches_dense_adjacency_torch("fusion-24grid-c32"),
       sg_pins.test_tiny_network_end_to_end_matches_torch_restatement]),
+    ("second CNN dense layer without its ReLU",
+     [("out = relu(W[\"cnn_dense2.w\"].astype(np.float64) @ out + W[\"cnn_dense2.b\"])",
+       "out = W[\"cnn_dense2.w\"].astype(np.float64) @ out + W[\"cnn_dense2.b\"]")],
+     [lambda: cnn_pins.test_cnn_branch_matches_torch_restatement(16)]),
+    ("CNN latent taken before the second dense layer",
+     [("out = relu(W[\"cnn_dense2.w\"].astype(np.float64) @ out + W[\"cnn_dense2.b\"])", "pass")],
+     [lambda: cnn_pins.test_cnn_branch_matches_torch_restatement(16)]),
+    ("stage gate reading the padded features in place of the stage's own states",
+     [("hh = np.concatenate([h, h0], axis=1)", "hh = np.concatenate([h0, h0], axis=1)")],
+     [lambda: sg_pins.test_sg_branch_matches_dense_adjacency_torch("fusion-paper-final")]),
     ("gather over every atom, not only the ligand's",
      [("hl = h[:n_lig]", "hl = h"), ("xl = x_in[:n_lig]", "xl = x_in")],
      [sg_pins.test_zero_steps_linear_gather_closed_form,
       lambda: sg_pins.test_sg_branch_matches_dense_adjacency_torch("fusion-20grid-ragged")]),
     ("gated gather reading the first stage's input instead of the last",
-     [("        x_in = h\n        for step in range(st[\"steps\"]):", "        for step in range(st[\"steps\"]):")],
+     [("        x_in = h\n        H = widths[s]\n", "        H = widths[s]\n")],
      [lambda: sg_pins.test_sg_branch_matches_dense_adjacency_torch("fusion-20grid-ragged")]),
     ("GRU blend with z and 1 - z swapped",
      [("return (1.0 - z) * nn + z * h", "return z * nn + (1.0 - z) * h")],
@@ -128,7 +138,7 @@ MUTATIONS = [
      [vox_pins.test_containing_voxel_on_boundary_and_centroid_rule]),
     ("max-pool window of the first voxel only",
      [(".max(axis=(1, 3, 5))", "[:, 0, :, 0, :, 0]")],
-     [cnn_pins.test_maxpool_matches_torch, cnn_pins.test_cnn_branch_matches_torch_restatement]),
+     [cnn_pins.test_maxpool_matches_torch, lambda: cnn_pins.test_cnn_branch_matches_torch_restatement(0)]),
 ]
 
 

@@ -35,10 +35,16 @@ def test_activations_match_torch():
     np.testing.assert_allclose(O.sigmoid(x), torch.sigmoid(torch.from_numpy(x)).numpy(), rtol=1e-14)
 
 
+def _widths(desc):
+    w = list(desc.get("sg_width") or [])
+    return [w[s] if s < len(w) and w[s] else desc["sg_hidden"] for s in range(len(desc["sg_stages"]))]
+
+
 def _torch_sg(desc, W, feat, n_lig, graph):
-    """Dense-adjacency restatement with torch modules."""
+    """Dense-adjacency restatement with torch modules (a GRUCell and Linear layers of each stage's width)."""
     T = lambda a: torch.from_numpy(np.asarray(a, dtype=np.float64))
-    H = desc["sg_hidden"]
+    widths = _widths(desc)
+    H = widths[0]
     N = len(feat)
     A = {}
     for e, (rp, col) in graph.items():
@@ -52,6 +58,7 @@ def _torch_sg(desc, W, feat, n_lig, graph):
     x_in = h0
     for s, st in enumerate(desc["sg_stages"]):
         x_in = h
+        H = widths[s]
         cell = torch.nn.GRUCell(H, H).double()
         with torch.no_grad():
             cell.weight_ih.copy_(T(W[f"sg{s}.gru.w_ih"]))
@@ -74,8 +81,9 @@ def _torch_sg(desc, W, feat, n_lig, graph):
     return v.sum(0).numpy()
 
 
-@pytest.mark.parametrize("name", ["fusion-24grid-c32", "fusion-20grid-ragged"])
+@pytest.mark.parametrize("name", ["fusion-24grid-c32", "fusion-20grid-ragged", "fusion-paper-final"])
 def test_sg_branch_matches_dense_adjacency_torch(name):
+    """Includes the paper-final SG-CNN: stage widths 19 then 24 (Table II's covalent gather width)."""
     desc = configs.model(name)
     W = weights.init_weights(desc, 2)
     xyz, feat, n_lig = poses.make_pose(5, (20, 30), (60, 90))
