@@ -100,6 +100,16 @@ typedef struct {
     int32_t sg_out[FUSION_MAX_HEAD];
     int32_t head_residual;     /* 1: a hidden fusion layer whose input and output widths match returns
                                   x + SELU(W x + b) */
+    int32_t cnn_dense2;        /* 0, or the width of a second CNN dense layer (ReLU) after the first
+                                  (Section 3.3.1: the first reduced by a factor of 2); the CNN latent the
+                                  fusion layers and branches read is then its output, the 3D-CNN's last
+                                  hidden layer Layer^{M-1} (Section 2.2).  cnn_dense must then be a multiple
+                                  of 8 */
+    int32_t sg_width[FUSION_MAX_STAGES];  /* node-state width of each stage (0 = sg_hidden; at most
+                                  sg_hidden; stage 0 at least n_feat).  The gate maps stage 0's states to
+                                  stage 1's width (Table II: the covalent gather width), so unequal widths
+                                  need sg_gate; the GPU carries every stage at sg_hidden with the extra
+                                  channels held at exactly zero */
 } fusion_model_desc;
 
 /* A batch of poses in packed structure-of-arrays form.  Ligand atoms come
@@ -119,14 +129,18 @@ typedef struct fusion_model fusion_model;
  * little-endian, no header, in this order (PyTorch shape conventions):
  *   per conv i: W [c_out][c_in][k][k][k], b [c_out]
  *   CNN dense: W [cnn_dense][C*S*S*S] (input in (C, D, H, W) flatten order of the pooled map), b
- *   per stage s: per edge type present (covalent first): W_e [H][H], b_e [H];
+ *   if cnn_dense2: W [cnn_dense2][cnn_dense], b [cnn_dense2]
+ *   per stage s (H = the stage's width w_s): per edge type present (covalent first): W_e [H][H], b_e [H];
  *                GRU W_ih [3H][H], W_hh [3H][H], b_ih [3H], b_hh [3H] (gate rows reset, update, new);
- *                if sg_gate and s is not the last stage: W_i [H][2H], b_i [H], W_j [H][H], b_j [H]
- *   gather: gated: W_g [G][2H], b_g [G], W_o [G][H], b_o [G]; linear: W [G][H], b [G]
- *   per CNN branch layer l: W [out][in], b [out]  (in = cnn_dense for l = 0)
+ *                if sg_gate and s is not the last stage: W_i [w_{s+1}][H + w_0], b_i [w_{s+1}],
+ *                W_j [w_{s+1}][H], b_j [w_{s+1}]
+ *   gather (H = the last stage's width): gated: W_g [G][2H], b_g [G], W_o [G][H], b_o [G];
+ *                                        linear: W [G][H], b [G]
+ *   per CNN branch layer l: W [out][in], b [out]  (in = the CNN latent width for l = 0)
  *   per SG branch layer l: W [out][in], b [out]   (in = G for l = 0)
- *   per head layer l: W [out][in], b [out]  (in = cnn_dense + G for l = 0, plus the last CNN and SG
- *                                            branch widths for FUSION_MID)
+ *   per head layer l: W [out][in], b [out]  (in = CNN latent width + G for l = 0, plus the last CNN and
+ *                                            SG branch widths for FUSION_MID)
+ * The CNN latent width is cnn_dense2 when nonzero, else cnn_dense.
  * Branch layers: FUSION_MID applies SELU after each; FUSION_LATE applies ReLU between them, the last
  * linear, and averages the two branch outputs.  Fusion layers: SELU between, the last linear.
  * Returns 0 if the descriptor is invalid. */
@@ -212,6 +226,11 @@ int fusion_last_timings(fusion_model *m, float *out, int32_t n);
                                                them all; -1 = the default, 4.  Every node's sums keep their
                                                order, so scores are the same for every value.  Drops
                                                captured graphs.  Any dtype */
+#define FUSION_OPT_SERIAL_BRANCHES 5   /* measurement mode: value 1 runs the graph branch after the grid
+                                          branch on one stream, so fusion_last_timings gives each stage's
+                                          kernel time alone (normally the branches overlap on two streams);
+                                          0 restores the default.  Scores are the same.  Drops captured
+                                          graphs.  Any dtype */
 
 /* Set a runtime option of a model (FUSION_OPT_*). */
 int fusion_set_option(fusion_model *m, int32_t option, int64_t value);
@@ -266,7 +285,10 @@ typedef struct {
     int32_t max_batch;         /* poses per batch, 1 .. desc->max_poses */
     double  batch_window_us;   /* longest wait for a batch to fill once a request is queued */
     size_t  hbm_budget_bytes;  /* device memory the slots may use; 0 = no limit */
-    int32_t queue_capacity;    /* poses that may wait in the queue; beyond it submit returns FUSION_EAGAIN */
+    int32_t queue_capacity;    /* poses that may wait in the queues; beyond it submit returns FUSION_EAGAIN */
+    int32_t dtypes;            /* mask of (1 << FUSION_F32 / FUSION_BF16 / FUSION_FP8): the dtypes the server
+                                  runs slots of, besides desc->dtype (0 = desc->dtype only); slots cycle
+                                  through them, at least one slot per dtype */
 } fusion_server_config;
 
 typedef struct {
@@ -274,6 +296,7 @@ typedef struct {
     size_t  slot_bytes;        /* measured device footprint of one slot */
     int64_t submitted, completed, rejected, failed, batches, queued, inflight;
     double  gpu_busy_s;        /* summed wall time of the slots' scoring calls */
+    int32_t slots_by_dtype[3]; /* slots admitted per dtype (FUSION_F32, FUSION_BF16, FUSION_FP8) */
 } fusion_server_stats;
 
 typedef struct fusion_server fusion_server;
@@ -285,10 +308,18 @@ int fusion_server_create(const fusion_model_desc *desc, const void *weights, siz
                          const fusion_server_config *cfg, fusion_server **out);
 
 /* Queue one pose (host arrays xyz[n_atoms][3], feat[n_atoms][19], ligand atoms
- * first; copied before return).  *ticket identifies its result.  Invalid poses
- * return FUSION_EINVAL; a full queue returns FUSION_EAGAIN. */
+ * first; copied before return) for scoring in desc->dtype.  *ticket identifies
+ * its result.  Invalid poses return FUSION_EINVAL; a full queue returns
+ * FUSION_EAGAIN. */
 int fusion_server_submit(fusion_server *s, const float *xyz, const float *feat, int32_t n_atoms, int32_t n_lig,
                          uint64_t *ticket);
+
+/* As fusion_server_submit, scored by a slot of `dtype` (FUSION_F32 / FUSION_BF16
+ * / FUSION_FP8), which must be one the server runs (FUSION_EINVAL otherwise).
+ * A pose's result depends only on the pose and its dtype, not on the poses it
+ * is batched with. */
+int fusion_server_submit_dtype(fusion_server *s, const float *xyz, const float *feat, int32_t n_atoms,
+                               int32_t n_lig, int32_t dtype, uint64_t *ticket);
 
 /* Non-blocking: FUSION_OK with the affinity and the latency from submission
  * to completion (seconds) once the pose is scored (each result is returned

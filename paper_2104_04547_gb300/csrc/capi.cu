@@ -58,6 +58,11 @@ Shape cnn_final(const fusion_model_desc &d) {
     return s;
 }
 
+// Width of the CNN latent the fusion layers read: the second dense layer's when there is one.
+int cnn_latent(const fusion_model_desc &d) { return d.cnn_dense2 ? d.cnn_dense2 : d.cnn_dense; }
+// Node-state width of SG-CNN stage s (carried at sg_hidden on the GPU, the rest held at zero).
+int stage_width(const fusion_model_desc &d, int s) { return d.sg_width[s] ? d.sg_width[s] : d.sg_hidden; }
+
 bool check_desc(const fusion_model_desc *d, std::string *why) {
 #define REQ(cond, msg)             \
     do {                           \
@@ -97,7 +102,14 @@ bool check_desc(const fusion_model_desc *d, std::string *why) {
     REQ(d->sg_gate == 0 || d->sg_gate == 1, "sg_gate must be 0 or 1");
     REQ(d->sg_gather == FUSION_GATHER_LINEAR || d->sg_gather == FUSION_GATHER_GATED, "bad sg_gather");
     REQ(d->sg_gather_width >= 1 && d->sg_gather_width <= 256, "sg_gather_width must be in [1, 256]");
-    REQ(d->cnn_dense + d->sg_gather_width <= 512, "cnn_dense + sg_gather_width must be <= 512");
+    REQ(d->cnn_dense2 >= 0 && d->cnn_dense2 <= 512, "cnn_dense2 must be in [0, 512]");
+    if (d->cnn_dense2) REQ(d->cnn_dense % 8 == 0, "cnn_dense must be a multiple of 8 when cnn_dense2 is set");
+    for (int s = 0; s < d->sg_n_stages; ++s)
+        REQ(d->sg_width[s] >= 0 && d->sg_width[s] <= d->sg_hidden, "sg_width must be 0 or in [1, sg_hidden]");
+    REQ(stage_width(*d, 0) >= d->n_feat, "the first stage's width must hold the 19 features");
+    if (d->sg_n_stages == 2 && stage_width(*d, 0) != stage_width(*d, 1))
+        REQ(d->sg_gate, "stages of unequal widths need sg_gate");
+    REQ(cnn_latent(*d) + d->sg_gather_width <= 512, "CNN latent width + sg_gather_width must be <= 512");
     REQ(d->fusion == FUSION_COHERENT || d->fusion == FUSION_MID || d->fusion == FUSION_LATE, "bad fusion form");
     REQ(d->n_cnn_out >= 0 && d->n_cnn_out <= FUSION_MAX_HEAD && d->n_sg_out >= 0 && d->n_sg_out <= FUSION_MAX_HEAD,
         "branch layer counts must be in [0, 6]");
@@ -107,7 +119,7 @@ bool check_desc(const fusion_model_desc *d, std::string *why) {
     if (d->fusion == FUSION_COHERENT) REQ(d->n_cnn_out == 0 && d->n_sg_out == 0, "coherent fusion has no branch layers");
     if (d->fusion != FUSION_COHERENT) REQ(d->n_cnn_out >= 1 && d->n_sg_out >= 1, "mid and late fusion need branch layers");
     if (d->fusion == FUSION_MID)
-        REQ(d->cnn_dense + d->sg_gather_width + d->cnn_out[d->n_cnn_out - 1] + d->sg_out[d->n_sg_out - 1] <= 1024,
+        REQ(cnn_latent(*d) + d->sg_gather_width + d->cnn_out[d->n_cnn_out - 1] + d->sg_out[d->n_sg_out - 1] <= 1024,
             "mid-level fusion input (latents + branch outputs) must be <= 1024 wide");
     if (d->fusion == FUSION_LATE) {
         REQ(d->cnn_out[d->n_cnn_out - 1] == 1 && d->sg_out[d->n_sg_out - 1] == 1,
@@ -133,7 +145,7 @@ bool check_desc(const fusion_model_desc *d, std::string *why) {
 
 // Width of the first fusion layer's input: the two latents, plus the branch outputs for mid-level fusion.
 static int head_input_width(const fusion_model_desc &d) {
-    int w = d.cnn_dense + d.sg_gather_width;
+    int w = cnn_latent(d) + d.sg_gather_width;
     if (d.fusion == FUSION_MID) w += d.cnn_out[d.n_cnn_out - 1] + d.sg_out[d.n_sg_out - 1];
     return w;
 }
@@ -155,9 +167,14 @@ std::vector<TensorSpec> blob_layout(const fusion_model_desc &d) {
     const size_t flat = (size_t)f.c * f.n * f.n * f.n;
     L.push_back({"cnn_dense.w", (size_t)d.cnn_dense * flat});
     L.push_back({"cnn_dense.b", (size_t)d.cnn_dense});
-    const size_t H = d.sg_hidden;
+    if (d.cnn_dense2) {
+        L.push_back({"cnn_dense2.w", (size_t)d.cnn_dense2 * d.cnn_dense});
+        L.push_back({"cnn_dense2.b", (size_t)d.cnn_dense2});
+    }
+    const size_t w0 = stage_width(d, 0);
     for (int s = 0; s < d.sg_n_stages; ++s) {
         const std::string p = "sg" + std::to_string(s);
+        const size_t H = stage_width(d, s);
         if (d.sg_edges[s] & FUSION_EDGE_COV) {
             L.push_back({p + ".cov.w", H * H});
             L.push_back({p + ".cov.b", H});
@@ -171,12 +188,14 @@ std::vector<TensorSpec> blob_layout(const fusion_model_desc &d) {
         L.push_back({p + ".gru.b_ih", 3 * H});
         L.push_back({p + ".gru.b_hh", 3 * H});
         if (d.sg_gate && s + 1 < d.sg_n_stages) {
-            L.push_back({p + ".gate.wi", H * 2 * H});
-            L.push_back({p + ".gate.bi", H});
-            L.push_back({p + ".gate.wj", H * H});
-            L.push_back({p + ".gate.bj", H});
+            const size_t Hn = stage_width(d, s + 1);
+            L.push_back({p + ".gate.wi", Hn * (H + w0)});
+            L.push_back({p + ".gate.bi", Hn});
+            L.push_back({p + ".gate.wj", Hn * H});
+            L.push_back({p + ".gate.bj", Hn});
         }
     }
+    const size_t H = stage_width(d, d.sg_n_stages - 1);
     const size_t G = d.sg_gather_width;
     if (d.sg_gather == FUSION_GATHER_GATED) {
         L.push_back({"gather.wg", G * 2 * H});
@@ -190,7 +209,7 @@ std::vector<TensorSpec> blob_layout(const fusion_model_desc &d) {
     for (int br = 0; br < 2; ++br) {
         const int nl = br == 0 ? d.n_cnn_out : d.n_sg_out;
         const int32_t *wd = br == 0 ? d.cnn_out : d.sg_out;
-        size_t bin = br == 0 ? (size_t)d.cnn_dense : G;
+        size_t bin = br == 0 ? (size_t)cnn_latent(d) : G;
         for (int l = 0; l < nl; ++l) {
             const std::string p = (br == 0 ? "cnn_out" : "sg_out") + std::to_string(l);
             L.push_back({p + ".w", (size_t)wd[l] * bin});
@@ -227,6 +246,7 @@ struct fusion_model {
     } conv[FUSION_MAX_CONV];
     void *dense_w = nullptr;      // f32 or bf16 [cnn_dense][flat], flat in (D, H, W, C) order
     float *dense_b = nullptr;
+    float *dense2_w = nullptr, *dense2_b = nullptr;   // second CNN dense layer, f32 [cnn_dense2][cnn_dense]
     bool bf16 = false;            // bf16 activations, pool and dense (tensor-core conv)
     bool fp8 = false;             // conv operands in FP8 E4M3 (per-channel weight, per-pose activation scales)
     size_t esz = 4;               // bytes per grid / activation element
@@ -245,9 +265,8 @@ struct fusion_model {
     int32_t *in_off = nullptr, *in_nlig = nullptr;
     float *in_xyz = nullptr, *in_feat = nullptr;
     float *origin = nullptr;
-    int4 *atom_vox = nullptr;
-    uint32_t *tile_mask = nullptr;    // [B][kTileMaskWords]: voxelize tiles some atom's support meets
-    float *atom_w = nullptr;
+    int32_t *cell_row = nullptr;      // [B][cell_row_stride]: voxel-cell list row index per pose
+    float *atom_rec = nullptr;        // [A][atom_rec_floats]: per-atom voxelize records in cell order
     void *grid = nullptr;
     int grid_cx = kGridCxF32;
     int grid_fold = -1;                           // bf16 grid: features 16..18 folded along x at this pad, or -1
@@ -258,12 +277,14 @@ struct fusion_model {
     float *amax = nullptr, *qscale = nullptr;   // FP8: per-pose max |activation| and scale [max_poses]
     float *conv_sw[FUSION_MAX_CONV] = {};       // FP8: per-output-channel weight scales
     float *dense_part = nullptr, *cnn_lat = nullptr;
+    float *cnn_lat2 = nullptr;    // second CNN dense layer's output (the CNN latent when present)
     int32_t *e_beg[2] = {}, *e_deg[2] = {}, *e_col[2] = {};
     float *hbuf[2] = {}, *Tbuf[2][2] = {}, *xin = nullptr, *sg_lat = nullptr, *aff = nullptr;
     unsigned *err = nullptr;
 
     // pinned host staging
     int32_t *h_off = nullptr;
+    int32_t *h_nlig = nullptr;
     unsigned *h_err = nullptr;
     float *h_aff = nullptr;
 
@@ -274,6 +295,7 @@ struct fusion_model {
     bool use_graph = false;                       // replay captured CUDA graphs, one per batch size
     int group_mode = -1;                          // conv output slices per MMA: -1 default per layer, or 1, 2, 4
     int sg_npw = 4;                               // graph convolution: nodes per warp (1, 2, 4, 8)
+    bool serial_branches = false;                 // both branches on the grid stream, one after the other
     std::map<int, cudaGraphExec_t> graph_exec;
     std::map<int, cudaGraph_t> graph;
 
@@ -386,6 +408,21 @@ std::vector<float> pack_gru(const float *wih, const float *whh, int H) {
     return t;
 }
 
+// A [rows][cols] matrix into a zero [R][C] one, row r -> rmap(r), column c -> cmap(c).
+template <class RM, class CM>
+std::vector<float> pad_mat(const float *w, int rows, int cols, int R, int C, RM rmap, CM cmap) {
+    std::vector<float> t((size_t)R * C, 0.f);
+    for (int r = 0; r < rows; ++r)
+        for (int c = 0; c < cols; ++c) t[(size_t)rmap(r) * C + cmap(c)] = w[(size_t)r * cols + c];
+    return t;
+}
+std::vector<float> pad_vec(const float *b, int n, int N, int groups = 1) {   // groups of n -> groups of N
+    std::vector<float> t((size_t)N * groups, 0.f);
+    for (int g = 0; g < groups; ++g)
+        for (int i = 0; i < n; ++i) t[(size_t)g * N + i] = b[(size_t)g * n + i];
+    return t;
+}
+
 #define RC(x)                 \
     do {                      \
         int rc_ = (x);        \
@@ -453,53 +490,72 @@ int load_weights(fusion_model *m, const float *blob) {
         }
         RC(upload(m, &m->dense_b, std::vector<float>(b, b + d.cnn_dense)));
     }
+    if (d.cnn_dense2) {
+        const float *w = take();
+        const float *b = take();
+        RC(upload(m, &m->dense2_w, std::vector<float>(w, w + (size_t)d.cnn_dense2 * d.cnn_dense)));
+        RC(upload(m, &m->dense2_b, std::vector<float>(b, b + d.cnn_dense2)));
+    }
+    // Graph weights at the kernels' width H: a stage of width w < H gets its matrices zero-padded, so its
+    // extra channels stay exactly zero (zero transform rows and biases give zero messages; a GRU channel with
+    // zero rows and biases keeps h' = (1 - 1/2) tanh(0) + h / 2 = 0 from h = 0; the gate and gather columns
+    // of those channels are zero), and every real channel's sums are those of the unpadded model.
     const int H = d.sg_hidden;
+    const int w0 = stage_width(d, 0);
+    auto id = [](int i) { return i; };
     for (int s = 0; s < d.sg_n_stages; ++s) {
+        const int w = stage_width(d, s);
         for (int e = 0; e < 2; ++e) {
             if (!(d.sg_edges[s] & (1 << e))) continue;
-            const float *w = take();
+            const float *we = take();
             const float *b = take();
-            RC(upload(m, &m->we_p[s][e], pack_edge(w, H)));
-            RC(upload(m, &m->be[s][e], std::vector<float>(b, b + H)));
+            RC(upload(m, &m->we_p[s][e], pack_edge(pad_mat(we, w, w, H, H, id, id).data(), H)));
+            RC(upload(m, &m->be[s][e], pad_vec(b, w, H)));
         }
         const float *wih = take();
         const float *whh = take();
         const float *bih = take();
         const float *bhh = take();
-        RC(upload(m, &m->gru_p[s], pack_gru(wih, whh, H)));
-        RC(upload(m, &m->bih[s], std::vector<float>(bih, bih + 3 * H)));
-        RC(upload(m, &m->bhh[s], std::vector<float>(bhh, bhh + 3 * H)));
+        auto grow = [w, H](int r) { return (r / w) * H + r % w; };     // gate rows (reset, update, new)
+        RC(upload(m, &m->gru_p[s], pack_gru(pad_mat(wih, 3 * w, w, 3 * H, H, grow, id).data(),
+                                            pad_mat(whh, 3 * w, w, 3 * H, H, grow, id).data(), H)));
+        RC(upload(m, &m->bih[s], pad_vec(bih, w, H, 3)));
+        RC(upload(m, &m->bhh[s], pad_vec(bhh, w, H, 3)));
         if (d.sg_gate && s + 1 < d.sg_n_stages) {
+            const int wn = stage_width(d, s + 1);
             const float *wi = take();
             const float *bi = take();
             const float *wj = take();
             const float *bj = take();
-            RC(upload(m, &m->gi_t, transpose(wi, H, 2 * H)));
-            RC(upload(m, &m->gbi, std::vector<float>(bi, bi + H)));
-            RC(upload(m, &m->gj_t, transpose(wj, H, H)));
-            RC(upload(m, &m->gbj, std::vector<float>(bj, bj + H)));
+            auto hcol = [w, H](int c) { return c < w ? c : H + (c - w); };   // [h (w), h0 (w0)] -> [h, h0] at H
+            RC(upload(m, &m->gi_t, transpose(pad_mat(wi, wn, w + w0, H, 2 * H, id, hcol).data(), H, 2 * H)));
+            RC(upload(m, &m->gbi, pad_vec(bi, wn, H)));
+            RC(upload(m, &m->gj_t, transpose(pad_mat(wj, wn, w, H, H, id, id).data(), H, H)));
+            RC(upload(m, &m->gbj, pad_vec(bj, wn, H)));
         }
     }
     const int G = d.sg_gather_width;
+    const int wl = stage_width(d, d.sg_n_stages - 1);
     if (d.sg_gather == FUSION_GATHER_GATED) {
         const float *wg = take();
         const float *bg = take();
         const float *wo = take();
         const float *bo = take();
-        RC(upload(m, &m->gat_wg_t, transpose(wg, G, 2 * H)));
+        auto xcol = [wl, H](int c) { return c < wl ? c : H + (c - wl); };    // [h, x] -> [h, x] at H
+        RC(upload(m, &m->gat_wg_t, transpose(pad_mat(wg, G, 2 * wl, G, 2 * H, id, xcol).data(), G, 2 * H)));
         RC(upload(m, &m->gat_bg, std::vector<float>(bg, bg + G)));
-        RC(upload(m, &m->gat_wo_t, transpose(wo, G, H)));
+        RC(upload(m, &m->gat_wo_t, transpose(pad_mat(wo, G, wl, G, H, id, id).data(), G, H)));
         RC(upload(m, &m->gat_bo, std::vector<float>(bo, bo + G)));
     } else {
         const float *w = take();
         const float *b = take();
-        RC(upload(m, &m->gat_wo_t, transpose(w, G, H)));
+        RC(upload(m, &m->gat_wo_t, transpose(pad_mat(w, G, wl, G, H, id, id).data(), G, H)));
         RC(upload(m, &m->gat_bo, std::vector<float>(b, b + G)));
     }
     for (int br = 0; br < 2; ++br) {
         const int nl = br == 0 ? d.n_cnn_out : d.n_sg_out;
         const int32_t *wd = br == 0 ? d.cnn_out : d.sg_out;
-        int bin = br == 0 ? d.cnn_dense : G;
+        int bin = br == 0 ? cnn_latent(d) : G;
         for (int l = 0; l < nl; ++l) {
             const float *w = take();
             const float *b = take();
@@ -524,15 +580,13 @@ int alloc_workspace(fusion_model *m) {
     const fusion_model_desc &d = m->d;
     const size_t B = d.max_poses;
     const size_t A = B * d.max_atoms;
-    const int KW = 2 * d.support + 1;
     RC(dalloc(m, &m->in_off, B + 1));
     RC(dalloc(m, &m->in_nlig, B));
     RC(dalloc(m, &m->in_xyz, A * 3));
     RC(dalloc(m, &m->in_feat, A * kFeat));
     RC(dalloc(m, &m->origin, B * 3));
-    RC(dalloc(m, &m->atom_vox, A));
-    RC(dalloc(m, &m->tile_mask, B * kTileMaskWords));
-    RC(dalloc(m, &m->atom_w, A * 3 * KW));
+    RC(dalloc(m, &m->cell_row, B * cell_row_stride(d.grid_n, d.support)));
+    RC(dalloc(m, &m->atom_rec, A * atom_rec_floats(d.support)));
     const size_t n3 = (size_t)d.grid_n * d.grid_n * d.grid_n;
     RC(dalloc_bytes(m, &m->grid, B * n3 * m->grid_cx * m->esz));
     size_t biggest = 0;
@@ -562,8 +616,10 @@ int alloc_workspace(fusion_model *m) {
         RC(dalloc(m, &m->qscale, B));
     }
     if (m->bf16) m->dense_tc_splits = dense_tc_splits(m->flat, d.cnn_dense);
-    RC(dalloc(m, &m->dense_part, (size_t)std::max(m->splits, m->dense_tc_splits) * B * d.cnn_dense));
+    RC(dalloc(m, &m->dense_part, std::max((size_t)std::max(m->splits, m->dense_tc_splits) * B * d.cnn_dense,
+                                          (size_t)dense_splits(d.cnn_dense) * B * d.cnn_dense2)));
     RC(dalloc(m, &m->cnn_lat, B * d.cnn_dense));
+    if (d.cnn_dense2) RC(dalloc(m, &m->cnn_lat2, B * d.cnn_dense2));
     for (int e = 0; e < 2; ++e) {
         RC(dalloc(m, &m->e_beg[e], A));
         RC(dalloc(m, &m->e_deg[e], A));
@@ -579,6 +635,7 @@ int alloc_workspace(fusion_model *m) {
     RC(dalloc(m, &m->aff, B));
     RC(dalloc(m, &m->err, 4));
     RC(halloc(m, &m->h_off, B + 1));
+    RC(halloc(m, &m->h_nlig, B));
     RC(halloc(m, &m->h_err, 4));
     RC(halloc(m, &m->h_aff, B));
     for (auto &e : m->ev) CU(cudaEventCreate(&e));
@@ -813,8 +870,8 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     mark(ms);
 
     // pose prep + voxelize
-    PrepArgs pa{off_d, nlig_d, xyz_d, B, d.max_atoms, d.grid_n, d.grid_h, d.sigma, d.support,
-                m->origin, m->atom_vox, m->atom_w, m->err, m->tile_mask};
+    PrepArgs pa{off_d, nlig_d, xyz_d, feat_d, B, d.max_atoms, d.grid_n, d.grid_h, d.sigma, d.support,
+                m->origin, m->err, m->cell_row, m->atom_rec};
     launch_prep(pa, ms);
     RC(check_launch("prep"));
     map[0] = ei; mark(ms);
@@ -827,85 +884,92 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     // tails, the small kernels) instead of holding SMs a conv CTA waits for:
     // measured on the 64-pose batch, serializing the two branches cost 2-3%,
     // and sharing the SMs without priorities slowed each conv layer.
-    cudaStream_t sgs = m->sg_stream;
+    // With FUSION_OPT_SERIAL_BRANCHES both branches run on the grid stream, the grid branch first, so that
+    // every stage's events time that stage's kernels alone (a measurement mode).
+    cudaStream_t sgs = m->serial_branches ? st : m->sg_stream;
     CU(cudaEventRecord(m->fork_ev, ms));
-    CU(cudaStreamWaitEvent(sgs, m->fork_ev, 0));
+    if (!m->serial_branches) CU(cudaStreamWaitEvent(sgs, m->fork_ev, 0));
     CU(cudaStreamWaitEvent(st, m->fork_ev, 0));
     auto sg_mark = [&](int k) {
         if (timed) cudaEventRecord(m->ev_sg[k], sgs);
     };
-    sg_mark(0);
-    // radius graph
-    GraphArgs ga{off_d, xyz_d, B, d.max_atoms, d.max_degree, d.cut_cov, d.cut_nc,
-                 {m->e_beg[0], m->e_beg[1]}, {m->e_deg[0], m->e_deg[1]}, {m->e_col[0], m->e_col[1]}, m->err};
-    launch_radius_graph(ga, sgs);
-    RC(check_launch("radius_graph"));
-    sg_mark(1);
+    auto graph_branch = [&]() -> int {
+        sg_mark(0);
+        // radius graph
+        GraphArgs ga{off_d, xyz_d, B, d.max_atoms, d.max_degree, d.cut_cov, d.cut_nc,
+                     {m->e_beg[0], m->e_beg[1]}, {m->e_deg[0], m->e_deg[1]}, {m->e_col[0], m->e_col[1]}, m->err};
+        launch_radius_graph(ga, sgs);
+        RC(check_launch("radius_graph"));
+        sg_mark(1);
 
-    // SG-CNN stages: each stage's input goes to xin (the gather reads the last
-    // one); GRU steps ping-pong between hbuf[0] and hbuf[1].
-    const int H = d.sg_hidden;
-    int tcur = 0;   // Tbuf ping-pong index holding the current transforms
-    const float *h = nullptr;
-    for (int s = 0; s < d.sg_n_stages; ++s) {
-        SgTransformArgs ta{};
-        ta.feat = feat_d;
-        ta.A = A;
-        ta.H = H;
-        ta.init = (s == 0);
-        ta.A_dev = A_dev;
-        ta.nodes_per_warp = m->sg_npw;
-        ta.h_in = h;            // read row by row before the same row of xin is written
-        ta.h_out = m->xin;
-        if (s > 0 && d.sg_gate) {
-            ta.gi_t = m->gi_t; ta.gbi = m->gbi; ta.gj_t = m->gj_t; ta.gbj = m->gbj;
-        }
-        for (int e = 0; e < 2; ++e) {
-            const bool use = (d.sg_edges[s] & (1 << e)) && d.sg_steps[s] > 0;
-            ta.we_p[e] = use ? m->we_p[s][e] : nullptr;
-            ta.be[e] = use ? m->be[s][e] : nullptr;
-            ta.T[e] = m->Tbuf[e][tcur];
-        }
-        launch_sg_transform(ta, sgs);
-        RC(check_launch("sg_transform"));
-        h = m->xin;
-        for (int k = 0; k < d.sg_steps[s]; ++k) {
-            SgStepArgs sa{};
-            sa.h_in = h;
-            float *hout = (h == m->hbuf[0]) ? m->hbuf[1] : m->hbuf[0];
-            sa.h_out = hout;
-            const bool more = (k + 1 < d.sg_steps[s]);
-            for (int e = 0; e < 2; ++e) {
-                const bool use = (d.sg_edges[s] & (1 << e)) != 0;
-                sa.T_in[e] = use ? m->Tbuf[e][tcur] : nullptr;
-                sa.T_out[e] = (use && more) ? m->Tbuf[e][tcur ^ 1] : nullptr;
-                sa.beg[e] = m->e_beg[e];
-                sa.deg[e] = m->e_deg[e];
-                sa.col[e] = m->e_col[e];
-                sa.we_p[e] = use ? m->we_p[s][e] : nullptr;
-                sa.be[e] = use ? m->be[s][e] : nullptr;
+        // SG-CNN stages: each stage's input goes to xin (the gather reads the last
+        // one); GRU steps ping-pong between hbuf[0] and hbuf[1].
+        const int H = d.sg_hidden;
+        int tcur = 0;   // Tbuf ping-pong index holding the current transforms
+        const float *h = nullptr;
+        for (int s = 0; s < d.sg_n_stages; ++s) {
+            SgTransformArgs ta{};
+            ta.feat = feat_d;
+            ta.A = A;
+            ta.H = H;
+            ta.init = (s == 0);
+            ta.A_dev = A_dev;
+            ta.nodes_per_warp = m->sg_npw;
+            ta.h_in = h;            // read row by row before the same row of xin is written
+            ta.h_out = m->xin;
+            if (s > 0 && d.sg_gate) {
+                ta.gi_t = m->gi_t; ta.gbi = m->gbi; ta.gj_t = m->gj_t; ta.gbj = m->gbj;
             }
-            sa.gru_p = m->gru_p[s]; sa.bih = m->bih[s]; sa.bhh = m->bhh[s];
-            sa.A = A;
-            sa.H = H;
-            sa.A_dev = A_dev;
-            sa.nodes_per_warp = m->sg_npw;
-            launch_sg_step(sa, sgs);
-            RC(check_launch("sg_step"));
-            h = hout;
-            tcur ^= 1;
+            for (int e = 0; e < 2; ++e) {
+                const bool use = (d.sg_edges[s] & (1 << e)) && d.sg_steps[s] > 0;
+                ta.we_p[e] = use ? m->we_p[s][e] : nullptr;
+                ta.be[e] = use ? m->be[s][e] : nullptr;
+                ta.T[e] = m->Tbuf[e][tcur];
+            }
+            launch_sg_transform(ta, sgs);
+            RC(check_launch("sg_transform"));
+            h = m->xin;
+            for (int k = 0; k < d.sg_steps[s]; ++k) {
+                SgStepArgs sa{};
+                sa.h_in = h;
+                float *hout = (h == m->hbuf[0]) ? m->hbuf[1] : m->hbuf[0];
+                sa.h_out = hout;
+                const bool more = (k + 1 < d.sg_steps[s]);
+                for (int e = 0; e < 2; ++e) {
+                    const bool use = (d.sg_edges[s] & (1 << e)) != 0;
+                    sa.T_in[e] = use ? m->Tbuf[e][tcur] : nullptr;
+                    sa.T_out[e] = (use && more) ? m->Tbuf[e][tcur ^ 1] : nullptr;
+                    sa.beg[e] = m->e_beg[e];
+                    sa.deg[e] = m->e_deg[e];
+                    sa.col[e] = m->e_col[e];
+                    sa.we_p[e] = use ? m->we_p[s][e] : nullptr;
+                    sa.be[e] = use ? m->be[s][e] : nullptr;
+                }
+                sa.gru_p = m->gru_p[s]; sa.bih = m->bih[s]; sa.bhh = m->bhh[s];
+                sa.A = A;
+                sa.H = H;
+                sa.A_dev = A_dev;
+                sa.nodes_per_warp = m->sg_npw;
+                launch_sg_step(sa, sgs);
+                RC(check_launch("sg_step"));
+                h = hout;
+                tcur ^= 1;
+            }
         }
-    }
-    m->last_h = h;
-    const float *stage_in = m->xin;
-    sg_mark(2);
-    SgGatherArgs gg{off_d, nlig_d, m->last_h, stage_in, m->gat_wg_t, m->gat_bg, m->gat_wo_t, m->gat_bo,
-                    m->sg_lat, B, H, d.sg_gather_width, d.sg_gather == FUSION_GATHER_GATED};
-    launch_sg_gather(gg, sgs);
-    RC(check_launch("sg_gather"));
-    sg_mark(3);
-    VoxArgs va{off_d, feat_d, m->atom_vox, m->atom_w, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx,
-               m->bf16 ? 1 : 0, m->grid_fold, bf16_blocked_in(m, 0) ? 1 : 0, m->tile_mask,
+        m->last_h = h;
+        const float *stage_in = m->xin;
+        sg_mark(2);
+        SgGatherArgs gg{off_d, nlig_d, m->last_h, stage_in, m->gat_wg_t, m->gat_bg, m->gat_wo_t, m->gat_bo,
+                        m->sg_lat, B, H, d.sg_gather_width, d.sg_gather == FUSION_GATHER_GATED};
+        launch_sg_gather(gg, sgs);
+        RC(check_launch("sg_gather"));
+        sg_mark(3);
+        return FUSION_OK;
+    };
+    if (!m->serial_branches) RC(graph_branch());
+
+    VoxArgs va{off_d, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx,
+               m->bf16 ? 1 : 0, m->grid_fold, bf16_blocked_in(m, 0) ? 1 : 0, m->cell_row, m->atom_rec,
                m->fp8 ? m->amax : nullptr};
     // FP8: voxelize also reduces each pose's max |grid value| (the first layer's input scale)
     if (m->fp8) CU(cudaMemsetAsync(m->amax, 0, sizeof(float) * B, st));
@@ -955,18 +1019,27 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     } else {
         launch_dense(da, st);
     }
+    if (d.cnn_dense2) {
+        // the second CNN dense layer (FP32 on every dtype: a cnn_dense x cnn_dense2 matrix per pose)
+        DenseArgs d2{m->cnn_lat, m->dense2_w, m->dense2_b, m->dense_part, m->cnn_lat2, B, d.cnn_dense2, d.cnn_dense,
+                     dense_splits(d.cnn_dense), 0, 1};
+        launch_dense(d2, st);
+    }
     RC(check_launch("dense"));
     map[11] = ei; mark(st);
+    if (m->serial_branches) RC(graph_branch());
 
     // join both branches
     CU(cudaEventRecord(m->cnn_join_ev, st));
     CU(cudaStreamWaitEvent(ms, m->cnn_join_ev, 0));
-    CU(cudaEventRecord(m->join_ev, sgs));
-    CU(cudaStreamWaitEvent(ms, m->join_ev, 0));
+    if (!m->serial_branches) {
+        CU(cudaEventRecord(m->join_ev, sgs));
+        CU(cudaStreamWaitEvent(ms, m->join_ev, 0));
+    }
     mark(ms);
 
     HeadArgs ha{};
-    ha.cnn = m->cnn_lat;
+    ha.cnn = d.cnn_dense2 ? m->cnn_lat2 : m->cnn_lat;
     ha.sg = m->sg_lat;
     for (int l = 0; l < d.n_head; ++l) {
         ha.wt[l] = m->head_wt[l];
@@ -987,7 +1060,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     ha.mode = d.fusion;
     ha.residual = d.head_residual;
     ha.B = B;
-    ha.Dc = d.cnn_dense;
+    ha.Dc = cnn_latent(d);
     ha.G = d.sg_gather_width;
     ha.out = m->aff;
     launch_head(ha, ms);
@@ -1027,8 +1100,12 @@ int fusion_score(fusion_model *m, const fusion_poses *poses, int32_t n_poses, fl
         for (size_t i = 0; i < A * 3; ++i)
             if (!std::isfinite(poses->xyz[i]))
                 return fail(FUSION_EINVAL, "non-finite coordinate at atom " + std::to_string(i / 3));
-        CU(cudaMemcpyAsync(m->in_off, off.data(), sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, st));
-        CU(cudaMemcpyAsync(m->in_nlig, nlig.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, st));
+        // offsets through the model's pinned staging (a pageable source would make the copy synchronous),
+        // which stays untouched until the end-of-call synchronisation
+        std::memcpy(m->h_off, off.data(), sizeof(int32_t) * (B + 1));
+        std::memcpy(m->h_nlig, nlig.data(), sizeof(int32_t) * B);
+        CU(cudaMemcpyAsync(m->in_off, m->h_off, sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(m->in_nlig, m->h_nlig, sizeof(int32_t) * B, cudaMemcpyHostToDevice, st));
         CU(cudaMemcpyAsync(m->in_xyz, poses->xyz, sizeof(float) * A * 3, cudaMemcpyHostToDevice, st));
         CU(cudaMemcpyAsync(m->in_feat, poses->feat, sizeof(float) * A * kFeat, cudaMemcpyHostToDevice, st));
         off_d = m->in_off;
@@ -1173,7 +1250,7 @@ int64_t fusion_stage_bytes(fusion_model *m, int32_t stage, int32_t index) {
         return (int64_t)s.n * s.n * s.n * s.c * 4;
     }
     case FUSION_STAGE_POOL: return (int64_t)m->flat * 4;
-    case FUSION_STAGE_CNN_LATENT: return (int64_t)d.cnn_dense * 4;
+    case FUSION_STAGE_CNN_LATENT: return (int64_t)cnn_latent(d) * 4;
     case FUSION_STAGE_EDGES_COV:
     case FUSION_STAGE_EDGES_NC: {
         const int e = stage == FUSION_STAGE_EDGES_COV ? 0 : 1;
@@ -1232,7 +1309,8 @@ int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst,
         return FUSION_OK;
     }
     case FUSION_STAGE_CNN_LATENT:
-        CU(cudaMemcpy(dst, m->cnn_lat + (size_t)p * d.cnn_dense, need, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(dst, (d.cnn_dense2 ? m->cnn_lat2 : m->cnn_lat) + (size_t)p * cnn_latent(d), need,
+                      cudaMemcpyDeviceToHost));
         return FUSION_OK;
     case FUSION_STAGE_EDGES_COV:
     case FUSION_STAGE_EDGES_NC: {
@@ -1283,6 +1361,11 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
         if (value != -1 && value != 1 && value != 2 && value != 4 && value != 8)
             return fail(FUSION_EINVAL, "graph nodes per warp must be -1 (default), 1, 2, 4 or 8");
         m->sg_npw = value == -1 ? 4 : (int)value;
+        drop_graphs(m);
+        return FUSION_OK;
+    case FUSION_OPT_SERIAL_BRANCHES:
+        if (value != 0 && value != 1) return fail(FUSION_EINVAL, "serial branches takes 0 or 1");
+        m->serial_branches = value != 0;
         drop_graphs(m);
         return FUSION_OK;
     case FUSION_OPT_CONV_SLICES_PER_MMA: {

@@ -28,26 +28,32 @@ struct PrepArgs {
     const int32_t *atom_off;
     const int32_t *n_lig;
     const float *xyz;
+    const float *feat;    // [A][19]
     int n_poses;
     int max_atoms;
     int grid_n;
     float h, sigma;
     int k;
     float *origin;        // [B][3]
-    int4 *atom_vox;       // [A]: (cz, cy, cx, pose)
-    float *atom_w;        // [A][3][2k+1]: z, y, x axis weights
     unsigned *err;
-    uint32_t *tile_mask;  // [B][kTileMaskWords]: bit t set iff some atom's support cube meets 8^3 tile t
+    // 1 A voxel-cell list of each pose: the atoms whose support cube meets the grid, sorted by containing
+    // voxel (z, y, x) over the extended range [-k, n-1+k]^3 and then by atom index.  Record j of pose p
+    // (atom_rec + (atom_off[p] + j) * atom_rec_floats(k)) is the j-th atom in that order: its containing
+    // voxel and pose as int (cz, cy, cx, p), its 3 x (2k+1) axis weights (z, y, x; zero-padded to a multiple
+    // of 4) and its 19 features + one zero.  cell_row[p][(cz + k) R + (cy + k)] (R = n + 2k) is where the
+    // (cz, cy) row of cells starts, cell_row[p][R^2] the number of listed atoms.
+    int32_t *cell_row;    // [B][cell_row_stride(n, k)]
+    float *atom_rec;      // [A][atom_rec_floats(k)]
 };
-// Grid tiles of 8^3 voxels per pose are at most 12^3 (grid_n <= 96): one bit each.
-constexpr int kTileMaskWords = (12 * 12 * 12 + 31) / 32;
+// Entries of one pose's cell-row index: (n + 2k)^2 + 1.
+inline int cell_row_stride(int n, int k) { return (n + 2 * k) * (n + 2 * k) + 1; }
+// Floats of an atom record: 4 (voxel, pose) + 3 (2k+1) weights rounded up to a multiple of 4 + 20 features.
+__host__ __device__ inline int atom_rec_wpad(int k) { return (3 * (2 * k + 1) + 3) & ~3; }
+__host__ __device__ inline int atom_rec_floats(int k) { return 4 + atom_rec_wpad(k) + 20; }
 void launch_prep(const PrepArgs &a, cudaStream_t s);
 
 struct VoxArgs {
     const int32_t *atom_off;
-    const float *feat;
-    const int4 *atom_vox;
-    const float *atom_w;
     int n_poses;
     int grid_n;
     int k;
@@ -59,7 +65,8 @@ struct VoxArgs {
                           // channel 16 + 3 s + f of voxel x holds feature 16 + f of voxel x - p + s
                           // (s = 0..4, zero outside the grid), channel 31 zero
     int blocked;          // bf16 only: store channel-blocked, [B][n][n][cx / 8][n][8]
-    const uint32_t *tile_mask;   // PrepArgs::tile_mask: a tile whose bit is clear stores zeros at once
+    const int32_t *cell_row;     // PrepArgs::cell_row
+    const float *atom_rec;       // PrepArgs::atom_rec (records in cell order)
     float *amax;          // bf16 only, may be null: per-pose max |stored value| (atomic max; zeroed by the caller)
 };
 void launch_voxelize(const VoxArgs &a, cudaStream_t s);

@@ -43,10 +43,11 @@ FUSION_OPT_CUDA_GRAPH = 1
 FUSION_OPT_CONV_SLICES_PER_MMA = 2
 FUSION_OPT_TEST_WAIT_TIMEOUT = 3
 FUSION_OPT_GRAPH_NODES_PER_WARP = 4
+FUSION_OPT_SERIAL_BRANCHES = 5
 
 EXPORTED = ["fusion_weights_bytes", "fusion_create", "fusion_score", "fusion_destroy", "fusion_last_error",
             "fusion_stage_bytes", "fusion_fetch_stage", "fusion_last_timings", "fusion_cnn_dense_noalloc",
-            "fusion_server_create", "fusion_server_submit", "fusion_server_poll", "fusion_server_drain",
+            "fusion_server_create", "fusion_server_submit", "fusion_server_submit_dtype", "fusion_server_poll", "fusion_server_drain",
             "fusion_server_get_stats", "fusion_server_destroy", "fusion_set_option", "fusion_autotune",
             "fusion_describe_conv", "fusion_best_per_compound", "fusion_graph_schedule"]
 
@@ -75,7 +76,7 @@ class fusion_model_desc(C.Structure):
                 ("max_poses", C.c_int32), ("max_atoms", C.c_int32), ("max_degree", C.c_int32),
                 ("keep_stages", C.c_int32), ("fusion", C.c_int32), ("n_cnn_out", C.c_int32),
                 ("cnn_out", C.c_int32 * MAX_HEAD), ("n_sg_out", C.c_int32), ("sg_out", C.c_int32 * MAX_HEAD),
-                ("head_residual", C.c_int32)]
+                ("head_residual", C.c_int32), ("cnn_dense2", C.c_int32), ("sg_width", C.c_int32 * MAX_STAGES)]
 
 
 class fusion_poses(C.Structure):
@@ -85,13 +86,13 @@ class fusion_poses(C.Structure):
 
 class fusion_server_config(C.Structure):
     _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("batch_window_us", C.c_double),
-                ("hbm_budget_bytes", C.c_size_t), ("queue_capacity", C.c_int32)]
+                ("hbm_budget_bytes", C.c_size_t), ("queue_capacity", C.c_int32), ("dtypes", C.c_int32)]
 
 
 class fusion_server_stats(C.Structure):
     _fields_ = [("slots", C.c_int32), ("slot_bytes", C.c_size_t), ("submitted", C.c_int64), ("completed", C.c_int64),
                 ("rejected", C.c_int64), ("failed", C.c_int64), ("batches", C.c_int64), ("queued", C.c_int64),
-                ("inflight", C.c_int64), ("gpu_busy_s", C.c_double)]
+                ("inflight", C.c_int64), ("gpu_busy_s", C.c_double), ("slots_by_dtype", C.c_int32 * 3)]
 
 
 def _load():
@@ -123,6 +124,9 @@ def _load():
     lib.fusion_server_create.restype = C.c_int
     lib.fusion_server_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, P(C.c_uint64)]
     lib.fusion_server_submit.restype = C.c_int
+    lib.fusion_server_submit_dtype.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                               P(C.c_uint64)]
+    lib.fusion_server_submit_dtype.restype = C.c_int
     lib.fusion_server_poll.argtypes = [C.c_void_p, C.c_uint64, P(C.c_float), P(C.c_double)]
     lib.fusion_server_poll.restype = C.c_int
     lib.fusion_server_drain.argtypes = [C.c_void_p, C.c_double]
@@ -192,6 +196,9 @@ def make_desc(model: dict, max_poses: int = 64, max_atoms: int = 1200, max_degre
     for l, w in enumerate(model.get("sg_out", [])):
         d.sg_out[l] = w
     d.head_residual = int(model.get("head_residual", 0))
+    d.cnn_dense2 = int(model.get("cnn_dense2", 0))
+    for s, w in enumerate(model.get("sg_width", []) or []):
+        d.sg_width[s] = int(w)
     d.dtype = DTYPES[dtype or model["dtype"]]
     d.max_poses = max_poses
     d.max_atoms = max_atoms
@@ -367,6 +374,10 @@ class Model:
     def use_cuda_graphs(self, on=True):
         fusion_set_option(self.handle, FUSION_OPT_CUDA_GRAPH, int(on))
 
+    def serial_branches(self, on=True):
+        """Measurement mode: both branches on one stream, so timings() gives each stage's own kernel time."""
+        fusion_set_option(self.handle, FUSION_OPT_SERIAL_BRANCHES, int(on))
+
     def conv_slices_per_mma(self, mode):
         """-1: default per layer; 1, 2 or 4: output slices per MMA on every layer."""
         fusion_set_option(self.handle, FUSION_OPT_CONV_SLICES_PER_MMA, int(mode))
@@ -417,6 +428,19 @@ def fusion_server_submit(server, xyz, feat, n_lig: int) -> int | None:
     return t.value
 
 
+def fusion_server_submit_dtype(server, xyz, feat, n_lig: int, dtype: int) -> int | None:
+    """Ticket of the pose queued for a slot of `dtype`, or None when the queue is full (FUSION_EAGAIN)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    feat = np.ascontiguousarray(feat, dtype=np.float32)
+    t = C.c_uint64()
+    rc = lib.fusion_server_submit_dtype(server, xyz.ctypes.data, feat.ctypes.data, len(xyz), int(n_lig), int(dtype),
+                                        C.byref(t))
+    if rc == FUSION_EAGAIN:
+        return None
+    _check(rc)
+    return t.value
+
+
 def fusion_server_poll(server, ticket: int):
     """(affinity, latency_s) once scored, else None."""
     a = C.c_float()
@@ -435,7 +459,9 @@ def fusion_server_drain(server, timeout_s: float = 600.0) -> None:
 def fusion_server_get_stats(server) -> dict:
     st = fusion_server_stats()
     _check(lib.fusion_server_get_stats(server, C.byref(st)))
-    return {k: getattr(st, k) for k, _ in fusion_server_stats._fields_}
+    out = {k: getattr(st, k) for k, _ in fusion_server_stats._fields_}
+    out["slots_by_dtype"] = {name: int(st.slots_by_dtype[v]) for name, v in DTYPES.items()}
+    return out
 
 
 def fusion_server_destroy(server) -> None:
@@ -446,13 +472,20 @@ class Server:
     """Continuous-batching server: ``Server(model_dict, weights_blob, max_batch=64, ...)``."""
 
     def __init__(self, model: dict, weights, max_batch=64, slots=0, batch_window_us=2000.0,
-                 hbm_budget_bytes=0, queue_capacity=1 << 20, max_atoms=1200, max_degree=64, dtype=None):
+                 hbm_budget_bytes=0, queue_capacity=1 << 20, max_atoms=1200, max_degree=64, dtype=None,
+                 dtypes=()):
+        """dtypes: further dtypes ("bf16", "fp8", "f32") to run slots of, besides the model's own."""
         self.desc = make_desc(model, max_batch, max_atoms, max_degree, False, dtype)
-        cfg = fusion_server_config(slots, max_batch, batch_window_us, hbm_budget_bytes, queue_capacity)
+        mask = 0
+        for name in dtypes:
+            mask |= 1 << DTYPES[name]
+        cfg = fusion_server_config(slots, max_batch, batch_window_us, hbm_budget_bytes, queue_capacity, mask)
         self.handle = fusion_server_create(self.desc, weights, cfg)
 
-    def submit(self, xyz, feat, n_lig):
-        return fusion_server_submit(self.handle, xyz, feat, n_lig)
+    def submit(self, xyz, feat, n_lig, dtype=None):
+        if dtype is None:
+            return fusion_server_submit(self.handle, xyz, feat, n_lig)
+        return fusion_server_submit_dtype(self.handle, xyz, feat, n_lig, DTYPES[dtype])
 
     def poll(self, ticket):
         return fusion_server_poll(self.handle, ticket)

@@ -125,7 +125,19 @@ BAD_DESCRIPTORS = [
     ("stage gate flag", _set(sg_gate=2), "sg_gate must be 0 or 1"),
     ("gather kind", _set(sg_gather=5), "bad sg_gather"),
     ("gather width", _set(sg_gather_width=0), "sg_gather_width must be in [1, 256]"),
-    ("latent width", _set(cnn_dense=400, sg_gather_width=200), "cnn_dense + sg_gather_width must be <= 512"),
+    ("latent width", _set(cnn_dense=400, sg_gather_width=200), "CNN latent width + sg_gather_width must be <= 512"),
+    ("second CNN dense width", _set(cnn_dense2=513), "cnn_dense2 must be in [0, 512]"),
+    ("first CNN dense width with a second", _set(cnn_dense=60, cnn_dense2=32), "cnn_dense must be a multiple of 8"),
+    ("latent width with a second CNN dense", _set(cnn_dense2=500, sg_gather_width=64),
+     "CNN latent width + sg_gather_width must be <= 512"),
+    ("stage width above the hidden width", lambda d: d.sg_width.__setitem__(0, 40),
+     "sg_width must be 0 or in [1, sg_hidden]"),
+    ("first stage narrower than the features", lambda d: d.sg_width.__setitem__(0, 18),
+     "the first stage's width must hold the 19 features"),
+    ("unequal stage widths without a gate",
+     lambda d: (_set(sg_n_stages=2, sg_gate=0)(d), d.sg_steps.__setitem__(1, 1), d.sg_edges.__setitem__(1, 3),
+                d.sg_width.__setitem__(0, 19), d.sg_width.__setitem__(1, 24)),
+     "stages of unequal widths need sg_gate"),
     ("fusion form", _set(fusion=7), "bad fusion form"),
     ("branch layers on coherent fusion", lambda d: (_set(n_cnn_out=1)(d), d.cnn_out.__setitem__(0, 32)),
      "coherent fusion has no branch layers"),

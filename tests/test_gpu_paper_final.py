@@ -2,13 +2,18 @@
 
 The `fusion-paper-final` preset: 3D-CNN 19->32 5^3, residual 32 5^3, 32->64 3^3 stride 2, residual 64 3^3
 (the 24^3 layer after the stride-2 one reads its input channel-blocked, as the stride-2 layer's epilogue
-writes it), dense 128; SG-CNN with 6 covalent then 3 mixed gated steps, covalent cutoff 2.24 A and
-non-covalent 5.22 A; head 128 -> 64 -> 24 -> 1.  Four poses of the 64-pose workload, weights seed 1
-(affinity spread 0.53):
+writes it), dense 128 then 64 (the CNN latent); SG-CNN with 6 covalent steps at the 19 feature channels,
+the gate to the covalent gather width 24, then 3 mixed steps at width 24 (covalent cutoff 2.24 A,
+non-covalent 5.22 A), gated gather to 128; head 128 -> 64 -> 24 -> 1.  The graph kernels carry both stages
+at width 32 with the extra channels held at zero.  Four poses of the 64-pose workload, weights seed 1:
 
-* FP32: every edge list bit-exact, affinities of two poses within 1e-4 of the FP64 oracle;
+* FP32: every edge list bit-exact; the CNN latent (second dense layer), the SG latent and the affinities
+  of two poses against the FP64 oracle (1e-4); the last node states equal the oracle's 24 channels and
+  hold exact zeros in the padding channels;
 * BF16 and FP8: each conv layer of a pose in isolation (the GPU's own input map convolved in float64),
-  affinity within 0.05 of the oracle, and a pose alone scores as in the batch.
+  affinity within 0.05 of the oracle, and a pose alone scores as in the batch;
+* the Late and Mid-level Fusion forms on the same branches (the SG-CNN's own 128 -> 85 -> 42 -> 1 stack
+  in Late Fusion): FP32 affinities against the oracle head on the oracle's latents (1e-4), BF16 within 0.05.
 """
 
 import numpy as np
@@ -33,12 +38,16 @@ def F():
 def case():
     batch = poses.subset(poses.make_batch(configs.WORKLOADS["batch64-lig20to50-pocket300to600"]), [0, 1, 2, 3])
     W = weights.init_weights(configs.model(NAME), 1)
-    exp = [O.score_pose(configs.model(NAME), W, *poses.pose_slice(batch, p)) for p in (0, 1)]
-    return batch, W, exp
+    stages = []
+    for p in (0, 1):
+        st = {}
+        O.score_pose(configs.model(NAME), W, *poses.pose_slice(batch, p), stages=st)
+        stages.append(st)
+    return batch, W, stages
 
 
 def test_paper_final_f32(F, case):
-    batch, W, exp = case
+    batch, W, stages = case
     desc = configs.model(NAME, dtype="f32")
     m = F.Model(desc, weights.to_blob(desc, W), max_poses=4, max_atoms=1200, keep_stages=True)
     got = m.score(batch).copy()
@@ -49,14 +58,22 @@ def test_paper_final_f32(F, case):
             rp, col = split_csr(m.fetch(stage, p), len(xyz))
             np.testing.assert_array_equal(rp, g[name][0], err_msg=f"pose {p} {name} row_ptr")
             np.testing.assert_array_equal(col, g[name][1], err_msg=f"pose {p} {name} col")
-    m.close()
     for p in (0, 1):
-        assert abs(float(got[p]) - exp[p]) <= F32_AFFINITY_TOL, (p, got[p], exp[p])
+        st = stages[p]
+        cnn = m.fetch(F.STAGE_CNN_LATENT, p)
+        assert cnn.shape == (64,)
+        np.testing.assert_allclose(cnn, st["cnn_latent"], rtol=1e-4, atol=1e-5)
+        np.testing.assert_allclose(m.fetch(F.STAGE_SG_LATENT, p), st["sg_latent"], rtol=1e-4, atol=1e-4)
+        h = m.fetch(F.STAGE_SG_STATE, p).reshape(-1, 32)
+        np.testing.assert_allclose(h[:, :24], st["sg1.step2"], rtol=1e-4, atol=1e-5)
+        assert np.all(h[:, 24:] == 0.0)
+        assert abs(float(got[p]) - st["affinity"]) <= F32_AFFINITY_TOL, (p, got[p], st["affinity"])
+    m.close()
 
 
 @pytest.mark.parametrize("dtype,check", [("bf16", check_layer_bf16), ("fp8", check_layer_fp8)])
 def test_paper_final_tensor_cores(F, case, dtype, check):
-    batch, W, exp = case
+    batch, W, stages = case
     desc = configs.model(NAME, dtype=dtype)
     m = F.Model(desc, weights.to_blob(desc, W), max_poses=4, max_atoms=1200, keep_stages=True)
     got = m.score(batch).copy()
@@ -64,5 +81,25 @@ def test_paper_final_tensor_cores(F, case, dtype, check):
     alone = m.score(poses.subset(batch, [2]))[0]
     m.close()
     for p in (0, 1):
-        assert np.isfinite(got[p]) and abs(float(got[p]) - exp[p]) <= 0.05, (p, got[p], exp[p])
+        exp = stages[p]["affinity"]
+        assert np.isfinite(got[p]) and abs(float(got[p]) - exp) <= 0.05, (p, got[p], exp)
     assert alone == got[2]
+
+
+@pytest.mark.parametrize("form", ["late", "mid"])
+@pytest.mark.parametrize("dtype,tol", [("f32", F32_AFFINITY_TOL), ("bf16", 0.05)])
+def test_paper_final_fusion_forms(F, case, form, dtype, tol):
+    """The forms share the branches' weights (the same seed draws the same branch tensors first), so the
+    oracle's latents of the coherent model serve; the form's own head is the oracle's."""
+    batch, _, stages = case
+    name = f"{NAME}-{form}"
+    W = weights.init_weights(configs.model(name), 1)
+    desc = configs.model(name, dtype=dtype)
+    m = F.Model(desc, weights.to_blob(desc, W), max_poses=4, max_atoms=1200)
+    got = m.score(batch).copy()
+    alone = m.score(poses.subset(batch, [1]))[0]
+    m.close()
+    for p in (0, 1):
+        exp = O.head(configs.model(name), W, stages[p]["cnn_latent"], stages[p]["sg_latent"])
+        assert np.isfinite(got[p]) and abs(float(got[p]) - exp) <= tol, (form, dtype, p, got[p], exp)
+    assert alone == got[1]

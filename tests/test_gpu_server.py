@@ -1,7 +1,8 @@
 """Continuous-batching server through the C ABI: every pose's result is the
-same as scoring that pose alone, whatever mix of uneven poses it was batched
-with; bad poses are rejected at submission; a full queue answers EAGAIN; a result
-is collected once; the HBM budget limits the slots."""
+same as scoring that pose alone, whatever mix of uneven poses (and, in a
+server with BF16 and FP8 slots, of dtypes) it was batched with; bad poses are
+rejected at submission; a full queue answers EAGAIN; a result is collected
+once; the HBM budget limits the slots."""
 
 import time
 
@@ -44,6 +45,41 @@ def test_results_same_alone_and_in_the_mix(F, dtype):
     m = F.Model(desc, blob, max_poses=1, max_atoms=1200)
     alone = np.array([m.score(poses.pack([p]))[0] for p in pool])
     np.testing.assert_array_equal(np.array(got, dtype=np.float32), alone)
+
+
+def test_mixed_dtype_server_results_same_alone(F):
+    """One server with BF16 and FP8 slots (the serving workload mixes the two): each request names its dtype,
+    and every result equals that pose scored alone by a model of that dtype, bit for bit."""
+    desc = configs.model("fusion-20grid-ragged", dtype="bf16")
+    W = weights.init_weights(desc, 5)
+    blob = weights.to_blob(desc, W)
+    pool = poses.make_uneven_pool(3, 8, seed0=778)
+    srv = F.Server(desc, blob, max_batch=8, slots=4, batch_window_us=500.0, max_atoms=1200, dtypes=("fp8",))
+    st = srv.stats()
+    assert st["slots"] == 4 and st["slots_by_dtype"] == {"f32": 0, "bf16": 2, "fp8": 2}
+    with pytest.raises(F.FusionError) as e:
+        srv.submit(*pool[0], dtype="f32")            # no FP32 slots in this server
+    assert e.value.code == F.FUSION_EINVAL
+    rng = np.random.default_rng(1)
+    order = [(i, "bf16" if rng.random() < 0.5 else "fp8") for i in range(len(pool))]
+    order += [(i, "fp8" if dt == "bf16" else "bf16") for i, dt in order[::3]]   # some poses in both dtypes
+    tickets = []
+    for i, dt in order:
+        tickets.append(srv.submit(*pool[i], dtype=dt))
+        if rng.random() < 0.3:
+            time.sleep(rng.random() * 0.003)
+    srv.drain()
+    got = [srv.poll(t)[0] for t in tickets]
+    assert srv.stats()["completed"] == len(order)
+    srv.close()
+    alone = {}
+    for dt in ("bf16", "fp8"):
+        d = configs.model("fusion-20grid-ragged", dtype=dt)
+        m = F.Model(d, weights.to_blob(d, W), max_poses=1, max_atoms=1200)
+        alone[dt] = [float(m.score(poses.pack([p]))[0]) for p in pool]
+        m.close()
+    for (i, dt), g in zip(order, got):
+        assert np.float32(g) == np.float32(alone[dt][i]), (i, dt, g, alone[dt][i])
 
 
 def test_rejections_and_queue_capacity(F):
