@@ -49,13 +49,21 @@ CONV_TRAFFIC = {
 }
 
 
-def conv_source_hash():
-    """sha256 prefix of the conv kernel's source files with comments and blank lines removed (a code
+# DRAM bytes of one voxelize launch at 64 poses (ncu dram__bytes_read.sum + dram__bytes_write.sum), valid for the
+# voxelize source they were taken on (sha256 prefix as for the conv); otherwise null.
+VOX_TRAFFIC = {
+    "src": None,
+    "poses": 64,
+}
+
+
+def conv_source_hash(files=("k_conv_tc.cu", "tc_ptx.cuh")):
+    """sha256 prefix of the kernel's source files with comments and blank lines removed (a code
     change invalidates the measured traffic; an edit of a comment does not)."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in ("k_conv_tc.cu", "tc_ptx.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2104_04547_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
@@ -71,6 +79,14 @@ def conv_traffic(dtype, n_poses, model=MODEL):
         return None
     v = CONV_TRAFFIC[dtype]
     return sum(v) / len(v)
+
+
+def vox_traffic(dtype, n_poses, model=MODEL):
+    """Measured DRAM bytes of one voxelize launch, or None."""
+    if (model != MODEL or n_poses != VOX_TRAFFIC["poses"] or dtype not in VOX_TRAFFIC or
+            conv_source_hash(("k_voxelize.cu",)) != VOX_TRAFFIC["src"]):
+        return None
+    return VOX_TRAFFIC[dtype]
 
 
 def conv_algorithmic_bytes(desc, dtype, n_poses):
@@ -114,14 +130,96 @@ def conv_flops_per_pose(desc):
 
 
 def launches_per_step(desc):
-    # prep + voxelize, the convs, the pool, dense + its reduction, the radius graph (count, scan, fill),
+    # prep + voxelize, the convs, the pool, dense + its reduction (and a second dense layer's two), the radius
+    # graph (count, scan, fill),
     # a transform per stage, the steps, the gather, the head
-    return (2 + len(desc["conv"]) + (1 if desc["pool"] > 1 else 0) + 2 + 3 +
+    return (2 + len(desc["conv"]) + (1 if desc["pool"] > 1 else 0) + 2 + (2 if desc.get("cnn_dense2") else 0) + 3 +
             len(desc["sg_stages"]) + sum(s["steps"] for s in desc["sg_stages"]) + 1 + 1)
 
 
+def golden_affinities():
+    """Stored FP64 oracle affinities of this workload's poses ({pose: affinity}; written by the committed golden
+    script, which calls only the oracle), or {} when the file is missing."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "full64_w0.json")) as f:
+            g = json.load(f)
+    except OSError:
+        return {}
+    if g.get("model") != MODEL or g.get("workload") != WORKLOAD or g.get("weights_seed") != WEIGHTS_SEED:
+        return {}
+    return {int(k): float(v["affinity"]) for k, v in g["poses"].items()}
+
+
+def delta_vs_oracle(got, model_name, batch_digest, gold_digest, gold):
+    """|affinity - stored FP64 oracle| over the stored poses (None if they do not apply to this run)."""
+    import numpy as np
+    if model_name != MODEL or not gold or batch_digest != gold_digest:
+        return None
+    idx = sorted(p for p in gold if p < len(got))
+    d = np.abs(np.asarray([got[p] for p in idx], dtype=np.float64) - np.asarray([gold[p] for p in idx]))
+    return {"vs": f"FP64 oracle, stored values of {len(idx)} poses", "mean": float(d.mean()), "max": float(d.max()),
+            "tolerance": 0.05}
+
+
+def voxelize_algorithmic_bytes(desc, dtype, n_atoms):
+    """Grid write n^3 x 19 channels x element size per pose + atom reads (12 B coordinates + 76 B features)."""
+    esz = 4 if dtype == "f32" else 2
+    return desc["grid_n"] ** 3 * 19 * esz, 88 * n_atoms
+
+
+def graph_branch_flops(desc, n_atoms, n_lig, e_cov, e_nc):
+    """Algorithmic flops of the gated graph convolution and gather of one pose: 2 per multiply-add of the edge
+    transforms, stage gate, GRU (input and hidden matrices) and gather matrices, plus H additions per directed
+    edge in the message sums.  The radius graph is integer and compare work, not counted."""
+    H, G = desc["sg_hidden"], desc["sg_gather_width"]
+    N = n_atoms
+    f = 0
+    for s, st in enumerate(desc["sg_stages"]):
+        types = [e for e, bit in ((e_cov, 1), (e_nc, 2)) if st["edges"] & bit]
+        nt = len(types)
+        if s > 0 and desc["sg_gate"]:
+            f += N * (2 * 2 * H * H + 2 * H * H)             # sigmoid(W_i [h, h0] + b) * (W_j h + b)
+        if st["steps"] > 0:
+            f += N * nt * 2 * H * H                          # first transforms W_e h + b_e
+        for k in range(st["steps"]):
+            f += N * 2 * 2 * 3 * H * H                       # GRU: W_ih m and W_hh h, three gates each
+            f += sum(types) * H                              # message sums over the directed edges
+            if k + 1 < st["steps"]:
+                f += N * nt * 2 * H * H                      # transforms of the new states
+    f += n_lig * (2 * 2 * H * G + 2 * H * G if desc["sg_gather"] == "gated" else 2 * H * G)
+    return f
+
+
+def measure_fp8_peak(torch):
+    """Dense FP8 E4M3 GEMM throughput on this GPU (torch._scaled_mm, 8192^3, best of 10 with and without fast
+    accumulation), TFLOP/s; None when the call is unavailable."""
+    n = 8192
+    try:
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        one = torch.ones((), device="cuda", dtype=torch.float32)
+        best = None
+        for fast in (False, True):
+            for _ in range(3):
+                torch._scaled_mm(a, b.t(), scale_a=one, scale_b=one, out_dtype=torch.bfloat16, use_fast_accum=fast)
+            for _ in range(10):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch._scaled_mm(a, b.t(), scale_a=one, scale_b=one, out_dtype=torch.bfloat16, use_fast_accum=fast)
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / 1e3
+                v = 2 * n ** 3 / t / 1e12
+                best = v if best is None else max(best, v)
+        del a, b
+        torch.cuda.empty_cache()
+        return best
+    except Exception:
+        return None
+
+
 def grid_folded(desc):
-    """The bf16 path stores the grid's channels 16..18 folded along x (one extra pass after voxelize)."""
+    """The bf16 path stores the grid's channels 16..18 folded along x (written so by voxelize)."""
     c0 = desc["conv"][0]
     return c0["stride"] == 1 and c0["k"] in (3, 5, 7) and not c0["residual"] and c0["c_in"] == 19
 
@@ -223,6 +321,210 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_steps(model, devb, B, out, stream, flush, steps, warmup, barrier):
+    """W untimed calls, then K calls each bracketed by CUDA events on the model's stream, with the L2 flushed
+    between them outside the events.  Returns (per-step ms, per-step stage timings)."""
+    import torch
+    for _ in range(warmup):
+        model.score(devb, n_poses=B, out=out, on_device=True)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stage_ms = []
+    for k in range(steps):
+        flush.zero_()                     # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        model.score(devb, n_poses=B, out=out, on_device=True)
+        ev[k][1].record(stream)
+        stage_ms.append(model.timings())
+    barrier()
+    return [s.elapsed_time(e) for s, e in ev], stage_ms
+
+
+def conv_roofline(desc, dtype, B, stage_ms, pk, pk_src, model_name, fp8_peak=None):
+    import statistics as st
+    conv_names = [f"conv{i}" for i in range(len(desc["conv"]))]
+    conv_ms = st.mean(sum(s[n] for n in conv_names) for s in stage_ms)
+    achieved = conv_flops_per_pose(desc) * B / (conv_ms / 1000.0) / 1e12
+    if dtype == "f32":
+        return {"bound": "alu", "achieved": achieved, "peak": F32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / F32_ALU_PEAK_TFLOPS, "traffic": None,
+                "kernel": f"conv3d_f32_kernel ({len(conv_names)} launches per step)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    # The burst peak: the step keeps the SM clock at its maximum (see `clocks`), while the sustained figure was
+    # taken with the clock held down by the power cap, so it would flatter the kernel.
+    if dtype == "fp8" and fp8_peak:
+        p, src = fp8_peak, "FP8 E4M3 GEMM measured in this run (torch._scaled_mm 8192^3, best of 10)"
+        ps = None
+    else:
+        ratio = 2.0 if dtype == "fp8" else 1.0
+        p = pk["bf16_tflops"] * ratio
+        ps = pk["bf16_tflops_sustained"] * ratio
+        src = f"bf16_tflops burst ({pk_src})" + (" x 2 (nominal fp8/bf16 ratio)" if ratio != 1 else "")
+    roof = {"bound": "tensor", "achieved": achieved, "peak": p, "unit": "TFLOP/s", "frac": achieved / p,
+            "traffic": conv_traffic(dtype, B, model_name),
+            "kernel": f"conv3d_tc_kernel {dtype} ({len(conv_names)} launches per step)", "peak_source": src}
+    if ps:
+        roof["frac_of_sustained"] = achieved / ps
+    roof["traffic_unit"] = f"DRAM bytes per conv launch (mean of the step's {len(conv_names)}), ncu"
+    roof["algorithmic_bytes"] = conv_algorithmic_bytes(desc, dtype, B)
+    return roof
+
+
+def edge_counts(F, model, batch, B):
+    """Directed covalent and non-covalent edges of each pose of the last call (from the CSR sizes)."""
+    off = batch["atom_off"]
+    ec, en = [], []
+    for p in range(B):
+        N = int(off[p + 1] - off[p])
+        ec.append(F.fusion_stage_bytes(model.handle, F.STAGE_EDGES_COV, p) // 4 - N - 1)
+        en.append(F.fusion_stage_bytes(model.handle, F.STAGE_EDGES_NC, p) // 4 - N - 1)
+    return ec, en
+
+
+def side_rooflines(F, model, desc, dtype, batch, B, devb, out, stage_ms, pk, pk_src):
+    """Voxelize (HBM), the graph branch (FP32 ALU) and the CNN dense (HBM, its weight stream): each kernel
+    group's algorithmic work over its own CUDA-event time.  Voxelize is timed in the timed steps (it runs on
+    the grid branch's stream); the graph branch overlaps the convolutions there, so it is timed in three more
+    calls with both branches on one stream (FUSION_OPT_SERIAL_BRANCHES), median per stage."""
+    import statistics as st
+    import torch
+    off = batch["atom_off"]
+    n_atoms = [int(off[p + 1] - off[p]) for p in range(B)]
+    grid_b, atom_b = voxelize_algorithmic_bytes(desc, dtype, 1)
+    vox_bytes = B * grid_b + atom_b * sum(n_atoms)
+    vox_ms = st.mean(s["voxelize"] for s in stage_ms)
+    hbm = pk["hbm_gbs"]
+    vox_gbs = vox_bytes / (vox_ms / 1e3) / 1e9
+    out_ = {"voxelize": {"bound": "hbm", "achieved": vox_gbs, "peak": hbm, "unit": "GB/s", "frac": vox_gbs / hbm,
+                         "traffic": vox_traffic(dtype, B, desc["name"]), "algorithmic_bytes": vox_bytes,
+                         "kernel_ms": vox_ms, "kernel": f"voxelize_kernel ({dtype} grid, one launch per step)",
+                         "peak_source": f"hbm_gbs ({pk_src})"}}
+    model.serial_branches(True)
+    ser = []
+    for _ in range(3):
+        model.score(devb, n_poses=B, out=out, on_device=True)
+        ser.append(model.timings())
+    model.serial_branches(False)
+    torch.cuda.synchronize()
+    ec, en = edge_counts(F, model, batch, B)
+    fl = sum(graph_branch_flops(desc, n_atoms[p], int(batch["n_lig"][p]), ec[p], en[p]) for p in range(B))
+    g_ms = st.median(s["sg_steps"] + s["sg_gather"] for s in ser)
+    r_ms = st.median(s["radius_graph"] for s in ser)
+    g_tf = fl / (g_ms / 1e3) / 1e12
+    out_["graph_branch"] = {
+        "bound": "alu", "achieved": g_tf, "peak": F32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": g_tf / F32_ALU_PEAK_TFLOPS, "traffic": None, "algorithmic_flops": fl, "kernel_ms": g_ms,
+        "radius_graph_ms": r_ms, "edges_per_pose": (sum(ec) + sum(en)) / B,
+        "kernel": "sg_transform_kernel + sg_step_kernel + sg_gather_kernel (FP32 CUDA cores), timed with the "
+                  "branches serialised",
+        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    if dtype != "f32":
+        K = model_flat(desc)
+        wbytes = desc["cnn_dense"] * K * 2
+        d_ms = st.median(s["cnn_dense"] for s in ser)
+        d_gbs = (wbytes + B * K * 2) / (d_ms / 1e3) / 1e9
+        out_["cnn_dense"] = {"bound": "hbm", "achieved": d_gbs, "peak": hbm, "unit": "GB/s", "frac": d_gbs / hbm,
+                             "traffic": None, "algorithmic_bytes": wbytes + B * K * 2, "kernel_ms": d_ms,
+                             "kernel": "dense_tc_kernel + dense_reduce_kernel (bf16 weight stream)",
+                             "peak_source": f"hbm_gbs ({pk_src})"}
+    return out_
+
+
+def model_flat(desc):
+    n, c = desc["grid_n"], 19
+    for cv in desc["conv"]:
+        n = (n + 2 * (cv["k"] // 2) - cv["k"]) // cv["stride"] + 1
+        c = cv["c_out"]
+    if desc["pool"] and desc["pool"] > 1:
+        n //= desc["pool"]
+    return c * n ** 3
+
+
+def serving_run(F, desc_name, W, blob_of, requests, seconds_cap=60.0):
+    """A bounded serving measurement: one server with BF16 and FP8 slots (requests alternate between the two,
+    as in the serving workload's mix), uneven poses (ligands log-normal around 32 atoms, pockets 150-1000),
+    first saturating (all queued at once) for the peak, then (after 500 unmeasured requests) Poisson arrivals
+    at 25% (three runs), 50% and 90% of it.  Per-pose latency is the server's submission-to-completion time;
+    `generator_lag_ms` is how late the load generator submitted (a stall there shows up as a burst)."""
+    import gc
+
+    import numpy as np
+
+    from synth import configs, poses
+    desc = configs.model(desc_name, dtype="bf16")
+    pool = poses.make_uneven_pool(16, 8)
+    srv = F.Server(desc, blob_of("bf16"), max_batch=64, slots=4, batch_window_us=2000.0,
+                   hbm_budget_bytes=120 << 30, queue_capacity=1 << 22, max_atoms=1200, dtypes=("fp8",))
+    dts = ["bf16", "fp8"]
+
+    def submit(i):
+        x, f, nl = pool[i % len(pool)]
+        return srv.submit(x, f, nl, dtype=dts[i % 2])
+
+    def collect(tickets):
+        lat = np.empty(len(tickets))
+        for i, t in enumerate(tickets):
+            r = srv.poll(t)
+            while r is None:
+                time.sleep(0.0002)
+                r = srv.poll(t)
+            lat[i] = r[1]
+        return lat
+
+    def pct(lat):
+        return {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
+                "p99.9": 1e3 * float(np.percentile(lat, 99.9)), "max": 1e3 * float(lat.max())}
+
+    def poisson(rate, n, rng):
+        """n requests at Poisson arrivals of `rate`; returns (latencies, achieved poses/s, generator lag)."""
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        tickets, lag = [], np.empty(n)
+        t0 = time.perf_counter()
+        for i in range(n):
+            target = t0 + arrivals[i]
+            while True:
+                now = time.perf_counter()
+                if now >= target:
+                    break
+                if target - now > 0.002:
+                    time.sleep(target - now - 0.001)
+            lag[i] = time.perf_counter() - target
+            tickets.append(submit(i))
+        srv.drain()
+        elapsed = time.perf_counter() - t0
+        return collect(tickets), n / elapsed, lag
+
+    collect([submit(i) for i in range(256)])            # warm-up
+    gc.collect()
+    gc.disable()                                       # no collector pauses in the load generator
+    try:
+        t0 = time.perf_counter()
+        tickets = [submit(i) for i in range(requests)]
+        srv.drain()
+        peak = requests / (time.perf_counter() - t0)
+        res = {"saturating": {"poses_per_s": peak, "requests": requests, "latency_ms": pct(collect(tickets))}}
+        rng = np.random.default_rng(7)
+        poisson(0.25 * peak, 500, rng)                 # unmeasured: the generator and the slots settle first
+        for load, reps in ((0.25, 3), (0.5, 1), (0.9, 1)):
+            n = int(min(requests, load * peak * seconds_cap / 10))
+            for r in range(reps):
+                lat, achieved, lag = poisson(load * peak, n, rng)
+                res[f"load_{int(load * 100)}" + (f"_run{r + 1}" if reps > 1 else "")] = {
+                    "offered_poses_per_s": load * peak, "poses_per_s": achieved, "requests": n,
+                    "latency_ms": pct(lat),
+                    "generator_lag_ms": {"p99.9": 1e3 * float(np.percentile(lag, 99.9)),
+                                         "max": 1e3 * float(lag.max())}}
+    finally:
+        gc.enable()
+    st = srv.stats()
+    srv.close()
+    res.update({"slots": st["slots_by_dtype"], "slot_gb": round(st["slot_bytes"] / 2 ** 30, 2), "max_batch": 64,
+                "batch_window_us": 2000.0, "hbm_budget_gb": 120, "dtype_mix": "requests alternate bf16 / fp8",
+                "pool": f"{len(pool)} uneven poses (16 ligands x 8 rigid poses)",
+                "latency": "per pose, submission to completion (server clock)"})
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -246,9 +548,12 @@ def run_ours(args):
     W = weights.init_weights(desc, WEIGHTS_SEED)
     blob = weights.to_blob(desc, W)
     batch = poses.make_batch(configs.WORKLOADS[WORKLOAD])
+    full_digest = poses.digest(batch)
     if args.poses < len(batch["n_lig"]):
         batch = poses.subset(batch, range(args.poses))     # profiling captures only
     B = len(batch["n_lig"])
+    gold = golden_affinities() if B == 64 else {}
+    gold_digest = full_digest if B == 64 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -260,9 +565,6 @@ def run_ours(args):
     out = torch.empty(B, dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    for _ in range(args.warmup):
-        model.score(devb, n_poses=B, out=out, on_device=True)
-
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
@@ -270,24 +572,15 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     clocks = Clocks(dev)
-    barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stage_ms = []
-    for k in range(args.steps):
-        flush.zero_()                     # L2 flush between timed steps (outside the events)
-        ev[k][0].record(stream)
-        model.score(devb, n_poses=B, out=out, on_device=True)
-        ev[k][1].record(stream)
-        stage_ms.append(model.timings())
-    barrier()
+    step_ms, stage_ms = time_steps(model, devb, B, out, stream, flush, args.steps, args.warmup, barrier)
     clk = clocks.stop()
-    step_ms = [s.elapsed_time(e) for s, e in ev]
     tot_ms = sum(step_ms)
     t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     tot_ms = float(t.item())
     value = world * B * args.steps / (tot_ms / 1000.0)
+    got = out.float().cpu().numpy().copy()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -310,11 +603,15 @@ def run_ours(args):
         e2e = {"value": world * B * args.steps / wall, "unit": "poses/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 4 * B}
 
-    # |affinity difference| against the FP32 path on the same batch (outside the timed region)
-    delta = None
+    pk, pk_src = peaks()
+    extra = {}
+    if rank == 0 and not args.no_extras:
+        extra["rooflines"] = side_rooflines(F, model, desc, args.dtype, batch, B, devb, out, stage_ms, pk, pk_src)
+
+    # |affinity difference| against the stored FP64 oracle values, and against the FP32 path on the same batch
+    delta = delta_vs_oracle(got, args.model, full_digest if B == 64 else None, gold_digest, gold)
     fp32_path = None
     if args.dtype != "f32" and not args.no_f32_compare:
-        got = out.float().cpu().numpy().copy()
         d32 = configs.model(args.model, dtype="f32")
         m32 = F.Model(d32, weights.to_blob(d32, W), max_poses=B, max_atoms=1200, max_degree=64,
                       stream=stream.cuda_stream)
@@ -328,43 +625,45 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         t32 = e0.elapsed_time(e1)
-        fp32_path = {"value": B / (t32 / 1000.0), "unit": "poses/s", "ms_per_step": t32,
-                     "note": "FP32 CUDA-core path, same batch and GPU, one step after one untimed step"}
-        m32.close()
         dd = np.abs(got - ref)
-        delta = {"vs": "f32 path, same poses and weights", "mean": float(dd.mean()), "max": float(dd.max()),
-                 "tolerance": 0.05}
+        fp32_path = {"value": B / (t32 / 1000.0), "unit": "poses/s", "ms_per_step": t32,
+                     "note": "FP32 CUDA-core path, same batch and GPU, one step after one untimed step",
+                     "delta_vs_this_dtype": {"mean": float(dd.mean()), "max": float(dd.max())},
+                     "delta_vs_oracle": delta_vs_oracle(ref, args.model, full_digest if B == 64 else None,
+                                                        gold_digest, gold)}
+        m32.close()
+
+    # the other tensor-core dtype (FP8 beside a BF16 run, BF16 beside FP8): same batch, same timing rules
+    if rank == 0 and args.dtype in ("bf16", "fp8") and not args.no_extras:
+        other = "fp8" if args.dtype == "bf16" else "bf16"
+        fp8_peak = measure_fp8_peak(torch)
+        d2 = configs.model(args.model, dtype=other)
+        m2 = F.Model(d2, weights.to_blob(d2, W), max_poses=B, max_atoms=1200, max_degree=64, stream=stream.cuda_stream)
+        out2 = torch.empty(B, dtype=torch.float32, device="cuda")
+        sm2, st2 = time_steps(m2, devb, B, out2, stream, flush, args.steps, args.warmup, barrier)
+        got2 = out2.float().cpu().numpy().copy()
+        m2.close()
+        extra[other] = {"value": B * args.steps / (sum(sm2) / 1000.0), "unit": "poses/s",
+                        "ms_per_step": sum(sm2) / args.steps,
+                        "latency_ms": {"p50": float(np.percentile(sm2, 50)), "p99": float(np.percentile(sm2, 99))},
+                        "stage_ms": {k: round(statistics.mean(s[k] for s in st2), 4) for k in st2[0]
+                                     if statistics.mean(s[k] for s in st2) > 0},
+                        "roofline": conv_roofline(d2, other, B, st2, pk, pk_src, args.model, fp8_peak),
+                        "delta_affinity": delta_vs_oracle(got2, args.model, full_digest if B == 64 else None,
+                                                          gold_digest, gold)}
+        extra["fp8_peak_tflops"] = {"value": fp8_peak, "how": "torch._scaled_mm E4M3 8192^3, best of 10 "
+                                                              "(with and without fast accumulation), this run"}
+
+    if rank == 0 and world == 1 and not args.no_serving and args.model == MODEL:
+        extra["serving"] = serving_run(F, args.model, W, lambda dt: weights.to_blob(configs.model(args.model, dt), W),
+                                       args.serving_requests)
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
 
-    conv_names = [f"conv{i}" for i in range(len(desc["conv"]))]
-    conv_ms = statistics.mean(sum(s[n] for n in conv_names) for s in stage_ms)
-    conv_flops = conv_flops_per_pose(desc) * B
-    achieved = conv_flops / (conv_ms / 1000.0) / 1e12
-    pk, pk_src = peaks()
-    traffic = conv_traffic(args.dtype, B, args.model)
-    if args.dtype == "f32":
-        roof = {"bound": "alu", "achieved": achieved, "peak": F32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / F32_ALU_PEAK_TFLOPS, "traffic": None,
-                "kernel": f"conv3d_f32_kernel ({len(conv_names)} launches per step)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-    else:
-        # The burst peak: the step keeps the SM clock at its maximum (see `clocks`), while the sustained
-        # figure was taken with the clock held down by the power cap, so it would flatter the kernel.
-        # No FP8 peak is measured: FP8 uses the BF16 figure x the nominal FP8/BF16 ratio (4.5 / 2.25).
-        ratio = 2.0 if args.dtype == "fp8" else 1.0
-        p = pk["bf16_tflops"] * ratio
-        ps = pk["bf16_tflops_sustained"] * ratio
-        roof = {"bound": "tensor", "achieved": achieved, "peak": p, "unit": "TFLOP/s", "frac": achieved / p,
-                "traffic": traffic, "kernel": f"conv3d_tc_kernel {args.dtype} ({len(conv_names)} launches per step)",
-                "peak_source": f"bf16_tflops burst ({pk_src})" + (" x 2 (nominal fp8/bf16 ratio)" if ratio != 1 else ""),
-                "frac_of_sustained": achieved / ps}
-    if args.dtype != "f32":
-        roof["traffic_unit"] = f"DRAM bytes per conv launch (mean of the step's {len(conv_names)}), ncu"
-        roof["algorithmic_bytes"] = conv_algorithmic_bytes(desc, args.dtype, B)
+    roof = conv_roofline(desc, args.dtype, B, stage_ms, pk, pk_src, args.model)
     stage_mean = {n: statistics.mean(s[n] for s in stage_ms) for n in stage_ms[0]}
     line = {
         "metric": METRIC, "value": value, "unit": "poses/s", "n_gpus": world, "steps": args.steps,
@@ -375,14 +674,14 @@ def run_ours(args):
                    "l2": "256 MiB written between timed steps; step working set (activations) > L2",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                       "note": "per-pose latency = its batch's latency (all 64 poses finish together)"},
+                       "note": "per-pose latency = its batch's latency (all 64 poses finish together); "
+                               "per-pose serving latency under load is in `serving`"},
         "stage_ms": {k: round(v, 4) for k, v in stage_mean.items() if v > 0},
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": (launches_per_step(desc) + (len(desc["conv"]) if args.dtype == "fp8" else 0) +
-                         (1 if args.dtype == "bf16" and grid_folded(desc) else 0)) * args.steps,
+        "gpu_launches": (launches_per_step(desc) + (len(desc["conv"]) if args.dtype == "fp8" else 0)) * args.steps,
         "clocks": clk,
-        "affinity_std": float(out.float().std().item()),
+        "affinity_std": float(np.std(got)),
     }
     if delta is not None:
         line["delta_affinity"] = delta
@@ -390,6 +689,7 @@ def run_ours(args):
         line["fp32_path"] = fp32_path
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -405,6 +705,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f32-compare", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the per-kernel-group rooflines and the other tensor-core dtype's run")
+    ap.add_argument("--no-serving", action="store_true", help="skip the bounded serving measurement")
+    ap.add_argument("--serving-requests", type=int, default=4000)
     ap.add_argument("--poses", type=int, default=64, help="first N poses of the batch (small profiling captures)")
     ap.add_argument("--model", default=MODEL,
                     help="model preset (synth.configs); the benchmark model by default, others for comparison")

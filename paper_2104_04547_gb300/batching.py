@@ -6,7 +6,8 @@ graph half scales with atoms, so poses are sorted by atom count and cut into
 batches of similar total size; each batch is one scoring call (optionally a
 CUDA-graph replay).
 
-    python -m paper_2104_04547_gb300.batching [--groups 100] [--dtype bf16]
+    python -m paper_2104_04547_gb300.batching [--groups 100] [--dtype bf16] [--passes 5] [--jobs 16]
+    python -m paper_2104_04547_gb300.batching --groups 10000 --passes 1 --graphs-only --jobs 16   # 100k poses
 
 measures poses/s over the packed batches with plain launches, with CUDA graphs,
 and with graphs after the conv tile autotuner, and prints one JSON line each.
@@ -65,7 +66,7 @@ def run(args):
     desc = configs.model("fusion-48grid-c64", dtype=args.dtype)
     W = weights.init_weights(desc, 0)
     blob = weights.to_blob(desc, W)
-    pool = poses.make_uneven_pool(args.groups, 10)
+    pool = poses.make_uneven_pool(args.groups, 10, jobs=args.jobs)
     sizes = [len(p[0]) for p in pool]
     batches = pack_by_atoms(sizes, args.max_batch, args.max_batch * 700)
     packed = [poses.pack([pool[i] for i in b]) for b in batches]
@@ -78,7 +79,7 @@ def run(args):
             "batches": len(batches), "max_batch": args.max_batch,
             "atoms_per_pose_mean": float(np.mean(sizes))}
 
-    def timed(label, passes=5):
+    def timed(label, passes=args.passes):
         # one untimed pass over every batch: each batch size's graph is captured here, not in the timed loop;
         # then `passes` timed passes over the pool, reported as the median (and the range)
         for pb, db in zip(packed, dev):
@@ -94,9 +95,13 @@ def run(args):
         print(json.dumps({**base, "mode": label, "poses_per_s": float(np.median(rates)),
                           "poses_per_s_range": [float(min(rates)), float(max(rates))], "passes": passes}), flush=True)
 
-    timed("plain launches")
+    if not args.graphs_only:
+        timed("plain launches")
     m.use_cuda_graphs(True)
     timed("cuda graphs")
+    if args.graphs_only:
+        m.close()
+        return
     m.autotune(packed[len(packed) // 2])
     print(json.dumps({**base, "autotuned_tiles": m.conv_tiles(), "graph_nodes_per_warp": m.graph_nodes_per_warp()}),
           flush=True)
@@ -125,7 +130,7 @@ def batch_sweep(args):
     torch.cuda.set_device(0)
     desc = configs.model("fusion-48grid-c64", dtype=args.dtype)
     blob = weights.to_blob(desc, weights.init_weights(desc, 0))
-    pool = poses.make_uneven_pool(args.groups, 10)
+    pool = poses.make_uneven_pool(args.groups, 10, jobs=args.jobs)
     sizes = [len(p[0]) for p in pool]
     for mb in [int(v) for v in args.batch_sweep.split(",")]:
         batches = pack_by_atoms(sizes, mb, mb * 700)
@@ -153,6 +158,9 @@ def main():
     ap.add_argument("--dtype", choices=["f32", "bf16", "fp8"], default="bf16")
     ap.add_argument("--max-batch", type=int, default=64)
     ap.add_argument("--batch-sweep", default="", help="comma-separated batch sizes: run the batch-size study")
+    ap.add_argument("--passes", type=int, default=5, help="timed passes over the pool per mode (median reported)")
+    ap.add_argument("--graphs-only", action="store_true", help="time only the CUDA-graph mode (large pools)")
+    ap.add_argument("--jobs", type=int, default=1, help="processes generating the pool")
     args = ap.parse_args()
     if args.batch_sweep:
         batch_sweep(args)

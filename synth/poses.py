@@ -370,9 +370,31 @@ def make_pose_group(seed: int, n_rot: int = 10):
     return out
 
 
-def make_uneven_pool(n_groups: int, n_rot: int = 10, seed0: int = 500000):
-    """Poses of n_groups ligands x n_rot rotations, in generation order."""
+def make_uneven_pool(n_groups: int, n_rot: int = 10, seed0: int = 500000, jobs: int = 1):
+    """Poses of n_groups ligands x n_rot rotations, in generation order.
+
+    With jobs > 1 the groups are generated in that many worker processes (each group comes from its own seed,
+    so the poses and their order are the same); the workers are spawned, so this may run after a CUDA
+    context exists in the calling process."""
+    if jobs <= 1 or n_groups < 2 * jobs:
+        poses = []
+        for g in range(n_groups):
+            poses.extend(make_pose_group(seed0 + g, n_rot))
+        return poses
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    step = (n_groups + 4 * jobs - 1) // (4 * jobs)
+    chunks = [(seed0 + g0, min(step, n_groups - g0), n_rot) for g0 in range(0, n_groups, step)]
     poses = []
-    for g in range(n_groups):
-        poses.extend(make_pose_group(seed0 + g, n_rot))
+    with ProcessPoolExecutor(max_workers=jobs, mp_context=mp.get_context("spawn")) as ex:
+        for part in ex.map(_pool_chunk, chunks):
+            poses.extend(part)
     return poses
+
+
+def _pool_chunk(args):
+    first, count, n_rot = args
+    out = []
+    for g in range(count):
+        out.extend(make_pose_group(first + g, n_rot))
+    return out
