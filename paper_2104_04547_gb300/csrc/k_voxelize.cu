@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(kVoxThreads, 6) voxelize_kernel(VoxArgs a) {
 
     int4 *s_v = reinterpret_cast<int4 *>(smem);                      // [kStage] (cz, cy, cx, pose)
     float *s_r = reinterpret_cast<float *>(s_v + kStage);            // [kStage][RW] weights, then features
-    int *s_list = reinterpret_cast<int *>(s_r + kStage * RW);        // [max_atoms] record positions
+    float *s_wzy = s_r + kStage * RW;                                // [kStage][8] wz(z) wy(y) of the tile's rows
+    int *s_list = reinterpret_cast<int *>(s_wzy + kStage * 8);       // [max_atoms] record positions
     __nv_bfloat16 *s_hi = reinterpret_cast<__nv_bfloat16 *>(s_list + a.max_atoms);   // [2][4][nxb * 4][3]
     __shared__ int s_rb[kMaxRuns], s_ro[kMaxRuns + 1];
 
@@ -313,12 +314,22 @@ __global__ void __launch_bounds__(kVoxThreads, 6) voxelize_kernel(VoxArgs a) {
     // stage candidates r0 .. r0 + nr: records copied 16 bytes at a time (whole rows are contiguous in memory)
     const int q4 = RECF / 4;
     const unsigned mq = ((1u << 20) + q4 - 1) / q4;    // e / q4 = (e mq) >> 20 for e < 2^16
+    // then, per staged atom and tile row (z0 + lz, y0 + ly), the product wz * wy (zero outside its support), so a
+    // visit needs only the x weight
     auto stage = [&](int r0, int nr) {
         for (int e = tid; e < nr * q4; e += kVoxThreads) {
             const int c = (int)(((unsigned)e * mq) >> 20), part = e - c * q4;
             const float4 v = reinterpret_cast<const float4 *>(a.atom_rec + (size_t)s_list[r0 + c] * RECF)[part];
             if (part == 0) s_v[c] = make_int4(__float_as_int(v.x), __float_as_int(v.y), __float_as_int(v.z), 0);
             else reinterpret_cast<float4 *>(s_r + c * RW)[part - 1] = v;
+        }
+        __syncthreads();
+        for (int e = tid; e < nr * 8; e += kVoxThreads) {
+            const int c = e >> 3, rz = (e >> 2) & 1, ry = e & 3;
+            const int4 v = s_v[c];
+            const unsigned dz = (unsigned)(z0 + rz - (v.x - K)), dy = (unsigned)(y0 + ry - (v.y - K));
+            const float *w = s_r + c * RW;
+            s_wzy[e] = dz < (unsigned)KW && dy < (unsigned)KW ? w[dz] * w[KW + dy] : 0.f;
         }
     };
     const bool single = M <= kStage;
@@ -363,22 +374,20 @@ __global__ void __launch_bounds__(kVoxThreads, 6) voxelize_kernel(VoxArgs a) {
                 while (todo) {
                     const int s = base + __ffs(todo) - 1;
                     todo &= todo - 1;
-                    const int4 v = s_v[s];
-                    const unsigned dz = (unsigned)(vz - (v.x - K));
-                    const unsigned dy = (unsigned)(vy - (v.y - K));
-                    const unsigned dx = (unsigned)(vx - (v.z - K));
-                    if (dz < (unsigned)KW && dy < (unsigned)KW && dx < (unsigned)KW) {
-                        const float *w = s_r + s * RW;
-                        const float wv = (w[dz] * w[KW + dy]) * w[2 * KW + dx];
-                        const float4 *f4 = reinterpret_cast<const float4 *>(w + WP);
+                    // the lane's weight: (wz wy) wx, zero outside the atom's support cube, and a zero weight adds
+                    // exactly nothing (fmaf(0, f, acc) == acc for the finite features), so no lane branches off
+                    const float *w = s_r + s * RW;
+                    const unsigned dx = (unsigned)(vx - (s_v[s].z - K));
+                    const float wx = dx < (unsigned)KW ? w[2 * KW + dx] : 0.f;
+                    const float wv = s_wzy[s * 8 + lz * 4 + ly] * wx;
+                    const float4 *f4 = reinterpret_cast<const float4 *>(w + WP);
 #pragma unroll
-                        for (int c4 = 0; c4 < 5; ++c4) {
-                            const float4 f = f4[c4];
-                            acc[4 * c4] = fmaf(wv, f.x, acc[4 * c4]);
-                            acc[4 * c4 + 1] = fmaf(wv, f.y, acc[4 * c4 + 1]);
-                            acc[4 * c4 + 2] = fmaf(wv, f.z, acc[4 * c4 + 2]);
-                            if (4 * c4 + 3 < kFeat) acc[4 * c4 + 3] = fmaf(wv, f.w, acc[4 * c4 + 3]);
-                        }
+                    for (int c4 = 0; c4 < 5; ++c4) {
+                        const float4 f = f4[c4];
+                        acc[4 * c4] = fmaf(wv, f.x, acc[4 * c4]);
+                        acc[4 * c4 + 1] = fmaf(wv, f.y, acc[4 * c4 + 1]);
+                        acc[4 * c4 + 2] = fmaf(wv, f.z, acc[4 * c4 + 2]);
+                        if (4 * c4 + 3 < kFeat) acc[4 * c4 + 3] = fmaf(wv, f.w, acc[4 * c4 + 3]);
                     }
                 }
             }
@@ -475,7 +484,7 @@ int vox_boxes_per_warp(int n) {
 
 size_t vox_smem(int n, int k, int max_atoms) {
     const int RW = atom_rec_wpad(k) + 20;
-    return (size_t)kStage * sizeof(int4) + (size_t)kStage * RW * 4 + (size_t)max_atoms * 4 +
+    return (size_t)kStage * sizeof(int4) + (size_t)kStage * RW * 4 + (size_t)kStage * 8 * 4 + (size_t)max_atoms * 4 +
            (size_t)kTileZ * kTileY * ((n + 3) / 4) * 4 * 3 * sizeof(__nv_bfloat16);
 }
 
