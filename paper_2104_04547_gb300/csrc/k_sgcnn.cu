@@ -159,37 +159,51 @@ __global__ void __launch_bounds__(kWarps * 32, step_min_blocks<H, NP>()) sg_step
     const int np = min(NP, A - i0);          // nodes of this warp (the rest of the NP slots are zero)
     float (*v)[2 * H] = sv[warp];
 
-    // message: segment sum of the neighbours' transforms, edge type by edge type, row order
+    // message: segment sum of the neighbours' transforms, edge type by edge type, each node's row in order.
+    // The warp's nodes walk their rows side by side (the q-th neighbour of every node per iteration), so NP
+    // neighbour rows are in flight at once; every node still adds its own neighbours in row order.
+    float m[NP][HJ];
 #pragma unroll
-    for (int n = 0; n < NP; ++n) {
-        float m[HJ];
+    for (int n = 0; n < NP; ++n)
 #pragma unroll
-        for (int j = 0; j < HJ; ++j) m[j] = 0.f;
-        if (n < np) {
-            const int i = i0 + n;
-            for (int e = 0; e < 2; ++e) {
-                if (!a.T_in[e]) continue;
-                const int beg = a.beg[e][i], d = a.deg[e][i];
-                const float *T = a.T_in[e];
-                for (int q0 = 0; q0 < d; q0 += 32) {
-                    const int jl = (q0 + lane < d) ? a.col[e][beg + q0 + lane] : 0;
-                    const int nq = min(32, d - q0);
-#pragma unroll 4
-                    for (int q = 0; q < nq; ++q) {
-                        const int jn = __shfl_sync(0xffffffffu, jl, q);
+        for (int j = 0; j < HJ; ++j) m[n][j] = 0.f;
+    for (int e = 0; e < 2; ++e) {
+        if (!a.T_in[e]) continue;
+        const float *T = a.T_in[e];
+        // lane n < NP holds node n's row start and degree
+        const int rb = lane < np ? a.beg[e][i0 + lane] : 0;
+        const int rd = lane < np ? a.deg[e][i0 + lane] : 0;
+        int dmax = rd;
+        for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        for (int q0 = 0; q0 < dmax; q0 += 32) {
+            int jl[NP];
 #pragma unroll
-                        for (int j = 0; j < HJ; ++j) m[j] += __ldg(T + (size_t)jn * H + lane + 32 * j);
+            for (int n = 0; n < NP; ++n) {
+                const int bn = __shfl_sync(0xffffffffu, rb, n), dn = __shfl_sync(0xffffffffu, rd, n);
+                jl[n] = (q0 + lane < dn) ? a.col[e][bn + q0 + lane] : -1;
+            }
+            const int nq = min(32, dmax - q0);
+#pragma unroll 2
+            for (int q = 0; q < nq; ++q) {
+#pragma unroll
+                for (int n = 0; n < NP; ++n) {
+                    const int jn = __shfl_sync(0xffffffffu, jl[n], q);
+                    if (jn >= 0) {                         // warp-uniform: q0 + q < the node's degree
+#pragma unroll
+                        for (int j = 0; j < HJ; ++j) m[n][j] += __ldg(T + (size_t)jn * H + lane + 32 * j);
                     }
                 }
             }
         }
+    }
+#pragma unroll
+    for (int n = 0; n < NP; ++n)
 #pragma unroll
         for (int j = 0; j < HJ; ++j) {
             const int o = lane + 32 * j;
-            v[n][o] = m[j];
+            v[n][o] = m[n][j];
             v[n][H + o] = n < np ? a.h_in[(size_t)(i0 + n) * H + o] : 0.f;
         }
-    }
     __syncwarp();
     // GRU.  Lane l owns outputs o = l + 32 j of each gate, one j at a time (24 accumulators at NP = 4, so
     // four blocks fit an SM and the latency-bound message sums keep their warps).  Its weights for input k
