@@ -135,9 +135,11 @@ def conv_flops_per_pose(desc):
 def launches_per_step(desc):
     # prep + voxelize, the convs, the pool, dense + its reduction (and a second dense layer's two), the radius
     # graph (count, scan, fill),
-    # a transform per stage, the steps, the gather, the head
+    # a transform per stage, the steps (tensor-core models: message sums, then the tensor-core GRU), the gather,
+    # the head
+    per_step = 2 if desc.get("dtype", "f32") != "f32" else 1
     return (2 + len(desc["conv"]) + (1 if desc["pool"] > 1 else 0) + 2 + (2 if desc.get("cnn_dense2") else 0) + 3 +
-            len(desc["sg_stages"]) + sum(s["steps"] for s in desc["sg_stages"]) + 1 + 1)
+            len(desc["sg_stages"]) + per_step * sum(s["steps"] for s in desc["sg_stages"]) + 1 + 1)
 
 
 def golden_affinities():

@@ -256,6 +256,7 @@ struct fusion_model {
     int pool_n = 0, pool_c = 0, flat = 0, splits = 1;
     float *we_p[FUSION_MAX_STAGES][2] = {}, *be[FUSION_MAX_STAGES][2] = {};
     float *gru_p[FUSION_MAX_STAGES] = {}, *bih[FUSION_MAX_STAGES] = {}, *bhh[FUSION_MAX_STAGES] = {};
+    uint16_t *gru_tc[FUSION_MAX_STAGES] = {};   // tensor-core step weights (sg_gru_tc_pack)
     float *gi_t = nullptr, *gbi = nullptr, *gj_t = nullptr, *gbj = nullptr;
     float *gat_wg_t = nullptr, *gat_bg = nullptr, *gat_wo_t = nullptr, *gat_bo = nullptr;
     float *head_wt[FUSION_MAX_HEAD] = {}, *head_b[FUSION_MAX_HEAD] = {};
@@ -280,6 +281,7 @@ struct fusion_model {
     float *cnn_lat2 = nullptr;    // second CNN dense layer's output (the CNN latent when present)
     int32_t *e_beg[2] = {}, *e_deg[2] = {}, *e_col[2] = {};
     float *hbuf[2] = {}, *Tbuf[2][2] = {}, *xin = nullptr, *sg_lat = nullptr, *aff = nullptr;
+    float *mbuf = nullptr;        // [A][H] messages of a tensor-core graph step
     unsigned *err = nullptr;
 
     // pinned host staging
@@ -296,6 +298,7 @@ struct fusion_model {
     int group_mode = -1;                          // conv output slices per MMA: -1 default per layer, or 1, 2, 4
     int sg_npw = 4;                               // graph convolution: nodes per warp (1, 2, 4, 8)
     bool serial_branches = false;                 // both branches on the grid stream, one after the other
+    bool sg_tc = false;                           // graph steps' GRU and transforms on the tensor cores
     std::map<int, cudaGraphExec_t> graph_exec;
     std::map<int, cudaGraph_t> graph;
 
@@ -505,11 +508,13 @@ int load_weights(fusion_model *m, const float *blob) {
     auto id = [](int i) { return i; };
     for (int s = 0; s < d.sg_n_stages; ++s) {
         const int w = stage_width(d, s);
+        std::vector<float> wep[2];
         for (int e = 0; e < 2; ++e) {
             if (!(d.sg_edges[s] & (1 << e))) continue;
             const float *we = take();
             const float *b = take();
-            RC(upload(m, &m->we_p[s][e], pack_edge(pad_mat(we, w, w, H, H, id, id).data(), H)));
+            wep[e] = pad_mat(we, w, w, H, H, id, id);
+            RC(upload(m, &m->we_p[s][e], pack_edge(wep[e].data(), H)));
             RC(upload(m, &m->be[s][e], pad_vec(b, w, H)));
         }
         const float *wih = take();
@@ -517,8 +522,15 @@ int load_weights(fusion_model *m, const float *blob) {
         const float *bih = take();
         const float *bhh = take();
         auto grow = [w, H](int r) { return (r / w) * H + r % w; };     // gate rows (reset, update, new)
-        RC(upload(m, &m->gru_p[s], pack_gru(pad_mat(wih, 3 * w, w, 3 * H, H, grow, id).data(),
-                                            pad_mat(whh, 3 * w, w, 3 * H, H, grow, id).data(), H)));
+        const std::vector<float> wihp = pad_mat(wih, 3 * w, w, 3 * H, H, grow, id);
+        const std::vector<float> whhp = pad_mat(whh, 3 * w, w, 3 * H, H, grow, id);
+        RC(upload(m, &m->gru_p[s], pack_gru(wihp.data(), whhp.data(), H)));
+        {
+            std::vector<uint16_t> img(sg_gru_tc_image_elems(H));
+            sg_gru_tc_pack(wihp.data(), whhp.data(), wep[0].empty() ? nullptr : wep[0].data(),
+                           wep[1].empty() ? nullptr : wep[1].data(), H, img.data());
+            RC(upload_raw(m, reinterpret_cast<void **>(&m->gru_tc[s]), img.data(), img.size() * 2));
+        }
         RC(upload(m, &m->bih[s], pad_vec(bih, w, H, 3)));
         RC(upload(m, &m->bhh[s], pad_vec(bhh, w, H, 3)));
         if (d.sg_gate && s + 1 < d.sg_n_stages) {
@@ -631,6 +643,7 @@ int alloc_workspace(fusion_model *m) {
     RC(dalloc(m, &m->xin, A * H));
     for (int e = 0; e < 2; ++e)
         for (int q = 0; q < 2; ++q) RC(dalloc(m, &m->Tbuf[e][q], A * H));
+    RC(dalloc(m, &m->mbuf, A * H));
     RC(dalloc(m, &m->sg_lat, B * d.sg_gather_width));
     RC(dalloc(m, &m->aff, B));
     RC(dalloc(m, &m->err, 4));
@@ -821,6 +834,7 @@ int fusion_create(const fusion_model_desc *desc, const void *weights, size_t wei
     m->splits = dense_splits(m->flat);
     m->bf16 = (m->d.dtype == FUSION_BF16 || m->d.dtype == FUSION_FP8);
     m->fp8 = (m->d.dtype == FUSION_FP8);
+    m->sg_tc = m->bf16;
     m->esz = m->bf16 ? 2 : 4;
     m->grid_cx = m->bf16 ? 32 : kGridCxF32;
     {
@@ -839,6 +853,7 @@ int fusion_create(const fusion_model_desc *desc, const void *weights, size_t wei
     if (!rc) rc = load_weights(m, static_cast<const float *>(weights));
     if (!rc && m->bf16) rc = plan_tensor_core_convs(m);
     if (!rc && m->bf16) rc = plan_tensor_core_dense(m);
+    if (!rc) sg_gru_tc_prepare(m->d.sg_hidden);
     if (rc) {
         std::string keep = g_err;
         fusion_destroy(m);
@@ -950,8 +965,30 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
                 sa.H = H;
                 sa.A_dev = A_dev;
                 sa.nodes_per_warp = m->sg_npw;
-                launch_sg_step(sa, sgs);
-                RC(check_launch("sg_step"));
+                if (m->sg_tc) {
+                    launch_sg_message(sa, m->mbuf, sgs);
+                    RC(check_launch("sg_message"));
+                    SgGruTcArgs ga{};
+                    ga.m = m->mbuf;
+                    ga.h_in = h;
+                    ga.h_out = hout;
+                    for (int e = 0; e < 2; ++e) {
+                        ga.T_out[e] = sa.T_out[e];
+                        ga.be[e] = sa.be[e];
+                    }
+                    ga.w = m->gru_tc[s];
+                    ga.bih = m->bih[s];
+                    ga.bhh = m->bhh[s];
+                    ga.A = A;
+                    ga.H = H;
+                    ga.A_dev = A_dev;
+                    ga.err = m->err;
+                    launch_sg_gru_tc(ga, sgs);
+                    RC(check_launch("sg_gru_tc"));
+                } else {
+                    launch_sg_step(sa, sgs);
+                    RC(check_launch("sg_step"));
+                }
                 h = hout;
                 tcur ^= 1;
             }
@@ -1366,6 +1403,12 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
     case FUSION_OPT_SERIAL_BRANCHES:
         if (value != 0 && value != 1) return fail(FUSION_EINVAL, "serial branches takes 0 or 1");
         m->serial_branches = value != 0;
+        drop_graphs(m);
+        return FUSION_OK;
+    case FUSION_OPT_GRAPH_TENSOR_CORES:
+        if (value != -1 && value != 0 && value != 1)
+            return fail(FUSION_EINVAL, "graph tensor cores takes -1 (default), 0 or 1");
+        m->sg_tc = value == -1 ? m->bf16 : value != 0;
         drop_graphs(m);
         return FUSION_OK;
     case FUSION_OPT_CONV_SLICES_PER_MMA: {

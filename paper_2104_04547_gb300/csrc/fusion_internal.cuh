@@ -238,6 +238,30 @@ struct SgStepArgs {
     int nodes_per_warp;    // 1, 2, 4 or 8 (anything else: 4); the results do not depend on it
 };
 void launch_sg_step(const SgStepArgs &a, cudaStream_t s);
+// The step's messages alone (the sums of sg_step_kernel, same order) into m [A][H].
+void launch_sg_message(const SgStepArgs &a, float *m, cudaStream_t s);
+
+// The step's GRU update and the next step's transforms on the tensor cores (k_sgcnn_tc.cu), from the
+// messages of launch_sg_message.
+struct SgGruTcArgs {
+    const float *m;        // [A][H] messages
+    const float *h_in;     // [A][H]
+    float *h_out;          // [A][H]
+    float *T_out[2];       // [A][H] transforms of h_out for the next step (nullptr: not needed)
+    const uint16_t *w;     // the stage's weight image (sg_gru_tc_pack), 16-byte aligned
+    const float *bih, *bhh;   // GRU biases [3H], [3H]
+    const float *be[2];       // transform biases [H] of the T_out slots
+    int A, H;              // H = 32 or 64
+    const int32_t *A_dev;  // non-null: the atom count is *A_dev (A is then the launch capacity)
+    unsigned *err;
+};
+void launch_sg_gru_tc(const SgGruTcArgs &a, cudaStream_t s);
+// Sets the kernel's shared-memory limit and sizes its persistent grid (call before any capture).
+void sg_gru_tc_prepare(int H);
+// The weight image of a stage: BF16 hi / lo parts of W_ih and W_hh ([3H][H]) and of the two transform
+// slots' W_e ([H][H]; nullptr: zeros), each part K-major [H/8][rows][8]; sg_gru_tc_image_elems(H) values.
+size_t sg_gru_tc_image_elems(int H);
+void sg_gru_tc_pack(const float *wih, const float *whh, const float *we0, const float *we1, int H, uint16_t *img);
 
 struct SgGatherArgs {
     const int32_t *atom_off;

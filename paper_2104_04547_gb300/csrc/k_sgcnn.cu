@@ -148,21 +148,13 @@ __global__ void __launch_bounds__(kWarps * 32) sg_transform_kernel(SgTransformAr
 template <int H, int NP>
 constexpr int step_min_blocks() { return (H == 64 && NP <= 4) ? 4 : 0; }
 
+// Messages of the warp's NP nodes i0 .. i0 + np: the segment sum of the neighbours' transforms, edge type by
+// edge type, each node's row in order.  The nodes walk their rows side by side (the q-th neighbour of every
+// node per iteration), so NP neighbour rows are in flight at once; every node still adds its own neighbours in
+// row order, so the sums do not depend on NP.  Lane l holds features l + 32 j of each node's message.
 template <int H, int NP>
-__global__ void __launch_bounds__(kWarps * 32, step_min_blocks<H, NP>()) sg_step_kernel(SgStepArgs a) {
+__device__ __forceinline__ void message_sums(const SgStepArgs &a, int lane, int i0, int np, float (&m)[NP][H / 32]) {
     constexpr int HJ = H / 32;
-    __shared__ __align__(16) float sv[kWarps][NP][2 * H];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int A = a.A_dev ? *a.A_dev : a.A;
-    const int i0 = (blockIdx.x * kWarps + warp) * NP;
-    if (i0 >= A) return;
-    const int np = min(NP, A - i0);          // nodes of this warp (the rest of the NP slots are zero)
-    float (*v)[2 * H] = sv[warp];
-
-    // message: segment sum of the neighbours' transforms, edge type by edge type, each node's row in order.
-    // The warp's nodes walk their rows side by side (the q-th neighbour of every node per iteration), so NP
-    // neighbour rows are in flight at once; every node still adds its own neighbours in row order.
-    float m[NP][HJ];
 #pragma unroll
     for (int n = 0; n < NP; ++n)
 #pragma unroll
@@ -196,6 +188,39 @@ __global__ void __launch_bounds__(kWarps * 32, step_min_blocks<H, NP>()) sg_step
             }
         }
     }
+}
+
+// The messages alone, written to m_out [A][H] (the tensor-core GRU reads them).
+template <int H, int NP>
+__global__ void __launch_bounds__(kWarps * 32) sg_message_kernel(SgStepArgs a, float *m_out) {
+    constexpr int HJ = H / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int A = a.A_dev ? *a.A_dev : a.A;
+    const int i0 = (blockIdx.x * kWarps + warp) * NP;
+    if (i0 >= A) return;
+    const int np = min(NP, A - i0);
+    float m[NP][HJ];
+    message_sums<H, NP>(a, lane, i0, np, m);
+#pragma unroll
+    for (int n = 0; n < NP; ++n)
+#pragma unroll
+        for (int j = 0; j < HJ; ++j)
+            if (n < np) m_out[(size_t)(i0 + n) * H + lane + 32 * j] = m[n][j];
+}
+
+template <int H, int NP>
+__global__ void __launch_bounds__(kWarps * 32, step_min_blocks<H, NP>()) sg_step_kernel(SgStepArgs a) {
+    constexpr int HJ = H / 32;
+    __shared__ __align__(16) float sv[kWarps][NP][2 * H];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int A = a.A_dev ? *a.A_dev : a.A;
+    const int i0 = (blockIdx.x * kWarps + warp) * NP;
+    if (i0 >= A) return;
+    const int np = min(NP, A - i0);          // nodes of this warp (the rest of the NP slots are zero)
+    float (*v)[2 * H] = sv[warp];
+
+    float m[NP][HJ];
+    message_sums<H, NP>(a, lane, i0, np, m);
 #pragma unroll
     for (int n = 0; n < NP; ++n)
 #pragma unroll
@@ -342,6 +367,22 @@ void launch_step_np(const SgStepArgs &a, cudaStream_t s) {
     sg_step_kernel<H, NP><<<blocks, kWarps * 32, 0, s>>>(a);
 }
 
+template <int H, int NP>
+void launch_message_np(const SgStepArgs &a, float *m, cudaStream_t s) {
+    const int blocks = (a.A + kWarps * NP - 1) / (kWarps * NP);
+    sg_message_kernel<H, NP><<<blocks, kWarps * 32, 0, s>>>(a, m);
+}
+
+template <int H>
+void launch_message_h(const SgStepArgs &a, float *m, cudaStream_t s) {
+    switch (a.nodes_per_warp) {
+    case 1: launch_message_np<H, 1>(a, m, s); break;
+    case 2: launch_message_np<H, 2>(a, m, s); break;
+    case 8: launch_message_np<H, 8>(a, m, s); break;
+    default: launch_message_np<H, 4>(a, m, s); break;
+    }
+}
+
 template <int H>
 void launch_transform_h(const SgTransformArgs &a, cudaStream_t s) {
     switch (a.nodes_per_warp) {
@@ -370,6 +411,11 @@ void launch_sg_transform(const SgTransformArgs &a, cudaStream_t s) {
 void launch_sg_step(const SgStepArgs &a, cudaStream_t s) {
     if (a.H == 64) launch_step_h<64>(a, s);
     else launch_step_h<32>(a, s);
+}
+
+void launch_sg_message(const SgStepArgs &a, float *m, cudaStream_t s) {
+    if (a.H == 64) launch_message_h<64>(a, m, s);
+    else launch_message_h<32>(a, m, s);
 }
 
 void launch_sg_gather(const SgGatherArgs &a, cudaStream_t s) {

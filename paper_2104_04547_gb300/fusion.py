@@ -44,6 +44,7 @@ FUSION_OPT_CONV_SLICES_PER_MMA = 2
 FUSION_OPT_TEST_WAIT_TIMEOUT = 3
 FUSION_OPT_GRAPH_NODES_PER_WARP = 4
 FUSION_OPT_SERIAL_BRANCHES = 5
+FUSION_OPT_GRAPH_TENSOR_CORES = 6
 
 EXPORTED = ["fusion_weights_bytes", "fusion_create", "fusion_score", "fusion_destroy", "fusion_last_error",
             "fusion_stage_bytes", "fusion_fetch_stage", "fusion_last_timings", "fusion_cnn_dense_noalloc",
@@ -377,6 +378,11 @@ class Model:
     def serial_branches(self, on=True):
         """Measurement mode: both branches on one stream, so timings() gives each stage's own kernel time."""
         fusion_set_option(self.handle, FUSION_OPT_SERIAL_BRANCHES, int(on))
+
+    def graph_tensor_cores(self, on=-1):
+        """1: graph steps' GRU and transforms on the tensor cores (three-term BF16 split); 0: FP32 CUDA
+        cores; -1: the dtype's default (tensor cores for BF16 / FP8)."""
+        fusion_set_option(self.handle, FUSION_OPT_GRAPH_TENSOR_CORES, int(on))
 
     def conv_slices_per_mma(self, mode):
         """-1: default per layer; 1, 2 or 4: output slices per MMA on every layer."""
