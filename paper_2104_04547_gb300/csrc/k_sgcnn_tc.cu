@@ -19,8 +19,9 @@
 // persistent CTA.  The node tile's m and h arrive by coalesced loads (8 rows x 64 bytes per warp access),
 // are split and stored in the same layout; h is also kept in FP32 for the z h term.  Tensor-memory columns:
 // [r | z] 0 .. 2H, n_i 2H .. 3H, n_h 3H .. 4H; the transforms reuse columns 0 .. 2H after the GRU epilogue
-// has read them.  Eight warps: warps w and w + 4 read lane quarter w % 4 (node rows) and split the output
-// columns between them.  Thread 0 issues the MMAs.  Every wait is bounded (FUSION_ERR_TIMEOUT).
+// has read them.  Sixteen warps: warps w, w + 4, w + 8 and w + 12 read lane quarter w % 4 (node rows) and
+// take a quarter of the output columns each.  Thread 0 issues the MMAs.  Every wait is bounded
+// (FUSION_ERR_TIMEOUT).
 #include "fusion_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -33,7 +34,7 @@ namespace fusion {
 namespace {
 
 constexpr int kTileM = 128;
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
 
 // 32 lanes x 16 columns of 32-bit from tensor memory (this warp's lane quarter).
@@ -45,8 +46,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
 }
 
-__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
-
 // Shared-memory plan for width H (bytes).
 template <int H>
 struct Plan {
@@ -54,14 +53,21 @@ struct Plan {
     static constexpr uint32_t kE = H * H * 2;               // one BF16 part of W_e, [H/8][H][8]
     static constexpr uint32_t kW = 4 * kIH + 4 * kE;        // the stage's weight image
     static constexpr uint32_t kA = kTileM * H * 2;          // one BF16 part of a node tile, [H/8][128][8]
-    static constexpr int kHoldStride = H + 4;               // FP32 h row stride (floats), bank-spread
-    static constexpr uint32_t kHold = kTileM * kHoldStride * 4;
+    static constexpr uint32_t kHold = kTileM * H * 4;       // h in FP32, [128][H], float4 slots XOR-swizzled
+    static constexpr uint32_t kBias = 6 * H * 4;            // b_ir+b_hr, b_iz+b_hz, b_in, b_hn, b_e0, b_e1
     static constexpr uint32_t oMhi = kW, oMlo = oMhi + kA, oHhi = oMlo + kA, oHlo = oHhi + kA;
     static constexpr uint32_t oHold = oHlo + kA;
-    static constexpr uint32_t oBar = oHold + kHold;         // w_bar, mma_bar, tmem slot
+    static constexpr uint32_t oBias = oHold + kHold;
+    static constexpr uint32_t oBar = oBias + kBias;         // w_bar, mma_bar, tmem slot
     static constexpr uint32_t kSmem = oBar + 32;
     static constexpr uint32_t kTmemCols = 4 * H;            // 256 or 128: a power of two >= 32
+    static constexpr int kCols = H / 4;                     // output columns per thread (four warps per quarter)
 };
+
+// Float4 slot of (row r, float4 column f4) in the FP32 h tile: rows are H floats, slots XOR-swizzled by r % 8,
+// so both the loaders' 8-row x 4-slot writes and the epilogue's 32-row reads of one slot spread over all banks.
+template <int H>
+__device__ __forceinline__ int hold_slot(int r, int f4) { return r * (H / 4) + (f4 ^ (r & 7)); }
 
 // x -> (bf16(x), bf16(x - bf16(x))) for four consecutive K values, as two 8-byte halves of core-matrix rows.
 __device__ __forceinline__ void split4(const float4 &x, uint2 &hi, uint2 &lo) {
@@ -73,6 +79,23 @@ __device__ __forceinline__ void split4(const float4 &x, uint2 &hi, uint2 &lo) {
     hi.y = *reinterpret_cast<const uint32_t *>(&h23);
     lo.x = *reinterpret_cast<const uint32_t *>(&l01);
     lo.y = *reinterpret_cast<const uint32_t *>(&l23);
+}
+
+// sigmoid and tanh from the exponential: 1 / (1 + e^-x) and 1 - 2 / (1 + e^2x) (both saturate correctly
+// when the exponential overflows to infinity).
+__device__ __forceinline__ float sigm_fast(float x) { return __fdividef(1.f, 1.f + __expf(-x)); }
+__device__ __forceinline__ float tanh_fast(float x) { return 1.f - __fdividef(2.f, 1.f + __expf(2.f * x)); }
+
+// 32 lanes x C columns (C = 8 or 16) of 32-bit from tensor memory (this warp's lane quarter).
+template <int C>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[C]) {
+    if constexpr (C == 16) {
+        tmem_ld16(taddr, r);
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(taddr));
+    }
 }
 
 // D (tensor memory, 128 x N) (+)= A B^T over K = H as three BF16 MMAs per K step (lo hi, hi lo, hi hi).
@@ -99,11 +122,13 @@ __device__ __forceinline__ void product3(uint32_t d, uint32_t a_hi, uint32_t a_l
 template <int H>
 __global__ void __launch_bounds__(kThreads, 1) sg_gru_tc_kernel(SgGruTcArgs a) {
     using P = Plan<H>;
+    constexpr int C = P::kCols;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *w_bar = reinterpret_cast<uint64_t *>(smem + P::oBar);
     uint64_t *mma_bar = w_bar + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_bar + 1);
-    float *hold = reinterpret_cast<float *>(smem + P::oHold);
+    float4 *hold = reinterpret_cast<float4 *>(smem + P::oHold);
+    float *sb = reinterpret_cast<float *>(smem + P::oBias);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int A = a.A_dev ? *a.A_dev : a.A;
@@ -118,6 +143,14 @@ __global__ void __launch_bounds__(kThreads, 1) sg_gru_tc_kernel(SgGruTcArgs a) {
         tc::fence_mbar_init();
     }
     if (warp == 0) tc::tmem_alloc(tmem_slot, P::kTmemCols);
+    for (int o = tid; o < H; o += kThreads) {
+        sb[o] = a.bih[o] + a.bhh[o];
+        sb[H + o] = a.bih[H + o] + a.bhh[H + o];
+        sb[2 * H + o] = a.bih[2 * H + o];
+        sb[3 * H + o] = a.bhh[2 * H + o];
+        sb[4 * H + o] = a.T_out[0] ? a.be[0][o] : 0.f;
+        sb[5 * H + o] = a.T_out[1] ? a.be[1][o] : 0.f;
+    }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -128,10 +161,12 @@ __global__ void __launch_bounds__(kThreads, 1) sg_gru_tc_kernel(SgGruTcArgs a) {
     if (tid == 0 && (int)blockIdx.x < n_tiles) {
         const unsigned char *g = reinterpret_cast<const unsigned char *>(a.w);
         uint32_t bytes = 4 * P::kIH;
+#pragma unroll
         for (int e = 0; e < 2; ++e)
             if (a.T_out[e]) bytes += 2 * P::kE;
         tc::mbar_expect_tx(w_bar, bytes);
         tc::bulk_load(smem, g, 4 * P::kIH, w_bar);
+#pragma unroll
         for (int e = 0; e < 2; ++e)
             if (a.T_out[e]) {
                 const uint32_t o = 4 * P::kIH + e * 2 * P::kE;
@@ -142,10 +177,10 @@ __global__ void __launch_bounds__(kThreads, 1) sg_gru_tc_kernel(SgGruTcArgs a) {
 
     const uint32_t s0 = tc::smem_u32(smem);
     const uint32_t sMhi = s0 + P::oMhi, sMlo = s0 + P::oMlo, sHhi = s0 + P::oHhi, sHlo = s0 + P::oHlo;
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3;
     const int row = quarter * 32 + lane;                  // this thread's node row in the tile
+    const int o0 = (warp >> 2) * C;                       // its output columns o0 .. o0 + C
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-    constexpr int kHalf = H / 2;
     uint32_t phase = 0;
     bool pending = false;                                 // a commit not yet seen complete
     bool ok = true;
@@ -156,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1) sg_gru_tc_kernel(SgGruTcArgs a) {
         {
             constexpr int F4 = H / 4;                     // float4 per row
             constexpr int CG = F4 / 4;                    // 4-float4 column groups per row
-#pragma unroll 4
+#pragma unroll
             for (int idx = tid; idx < kTileM * F4; idx += kThreads) {
                 const int g = idx >> 5, l = idx & 31;
                 const int r = (g / CG) * 8 + (l >> 2);
@@ -175,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 1) sg_gru_tc_kernel(SgGruTcArgs a) {
                 split4(xh, hi, lo);
                 *reinterpret_cast<uint2 *>(smem + P::oHhi + o) = hi;
                 *reinterpret_cast<uint2 *>(smem + P::oHlo + o) = lo;
-                *reinterpret_cast<float4 *>(hold + r * P::kHoldStride + f4 * 4) = xh;
+                hold[hold_slot<H>(r, f4)] = xh;
             }
         }
         tc::fence_proxy_async();
@@ -215,32 +250,35 @@ __global__ void __launch_bounds__(kThreads, 1) sg_gru_tc_kernel(SgGruTcArgs a) {
         // ---- GRU epilogue: h' to global, and its BF16 parts over the tile's m ----
         const int gi = i0 + row;
         const bool valid = gi < A;
-#pragma unroll 1
-        for (int c = 0; c < kHalf / 16; ++c) {
-            const int o0 = half * kHalf + c * 16;
-            uint32_t vr[16], vz[16], vn[16], vh[16];
-            tmem_ld16(tbase + lane_addr + o0, vr);
-            tmem_ld16(tbase + lane_addr + H + o0, vz);
-            tmem_ld16(tbase + lane_addr + 2 * H + o0, vn);
-            tmem_ld16(tbase + lane_addr + 3 * H + o0, vh);
+        {
+            uint32_t vr[C], vz[C], vn[C], vh[C];
+            tmem_ld_cols<C>(tbase + lane_addr + o0, vr);
+            tmem_ld_cols<C>(tbase + lane_addr + H + o0, vz);
+            tmem_ld_cols<C>(tbase + lane_addr + 2 * H + o0, vn);
+            tmem_ld_cols<C>(tbase + lane_addr + 3 * H + o0, vh);
             tc::tmem_ld_wait();
-            float hn[16];
+            float hn[C];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int o = o0 + q;
-                const float r = sigm(__uint_as_float(vr[q]) + __ldg(a.bih + o) + __ldg(a.bhh + o));
-                const float z = sigm(__uint_as_float(vz[q]) + __ldg(a.bih + H + o) + __ldg(a.bhh + H + o));
-                const float n = tanhf(__uint_as_float(vn[q]) + __ldg(a.bih + 2 * H + o) +
-                                      r * (__uint_as_float(vh[q]) + __ldg(a.bhh + 2 * H + o)));
-                hn[q] = (1.f - z) * n + z * hold[row * P::kHoldStride + o];
+            for (int q4 = 0; q4 < C / 4; ++q4) {
+                const float4 ho = hold[hold_slot<H>(row, o0 / 4 + q4)];
+                const float hv[4] = {ho.x, ho.y, ho.z, ho.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = 4 * q4 + u, o = o0 + q;
+                    const float r = sigm_fast(__uint_as_float(vr[q]) + sb[o]);
+                    const float z = sigm_fast(__uint_as_float(vz[q]) + sb[H + o]);
+                    const float n = tanh_fast(__uint_as_float(vn[q]) + sb[2 * H + o] +
+                                              r * (__uint_as_float(vh[q]) + sb[3 * H + o]));
+                    hn[q] = (1.f - z) * n + z * hv[u];
+                }
             }
             if (valid) {
                 float4 *dst = reinterpret_cast<float4 *>(a.h_out + (size_t)gi * H + o0);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) dst[q] = make_float4(hn[4 * q], hn[4 * q + 1], hn[4 * q + 2], hn[4 * q + 3]);
+                for (int q = 0; q < C / 4; ++q) dst[q] = make_float4(hn[4 * q], hn[4 * q + 1], hn[4 * q + 2], hn[4 * q + 3]);
             }
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
+            for (int s = 0; s < C / 8; ++s) {
                 uint2 h0, l0, h1, l1;
                 split4(make_float4(hn[8 * s], hn[8 * s + 1], hn[8 * s + 2], hn[8 * s + 3]), h0, l0);
                 split4(make_float4(hn[8 * s + 4], hn[8 * s + 5], hn[8 * s + 6], hn[8 * s + 7]), h1, l1);
@@ -277,21 +315,17 @@ __global__ void __launch_bounds__(kThreads, 1) sg_gru_tc_kernel(SgGruTcArgs a) {
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 if (!a.T_out[e]) continue;
-#pragma unroll 1
-                for (int c = 0; c < kHalf / 16; ++c) {
-                    const int o0 = half * kHalf + c * 16;
-                    uint32_t v[16];
-                    tmem_ld16(tbase + lane_addr + e * H + o0, v);
-                    tc::tmem_ld_wait();
-                    if (valid) {
-                        float4 *dst = reinterpret_cast<float4 *>(a.T_out[e] + (size_t)gi * H + o0);
+                uint32_t v[C];
+                tmem_ld_cols<C>(tbase + lane_addr + e * H + o0, v);
+                tc::tmem_ld_wait();
+                if (valid) {
+                    const float *be = sb + (4 + e) * H + o0;
+                    float4 *dst = reinterpret_cast<float4 *>(a.T_out[e] + (size_t)gi * H + o0);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            dst[q] = make_float4(__uint_as_float(v[4 * q]) + __ldg(a.be[e] + o0 + 4 * q),
-                                                 __uint_as_float(v[4 * q + 1]) + __ldg(a.be[e] + o0 + 4 * q + 1),
-                                                 __uint_as_float(v[4 * q + 2]) + __ldg(a.be[e] + o0 + 4 * q + 2),
-                                                 __uint_as_float(v[4 * q + 3]) + __ldg(a.be[e] + o0 + 4 * q + 3));
-                    }
+                    for (int q = 0; q < C / 4; ++q)
+                        dst[q] = make_float4(__uint_as_float(v[4 * q]) + be[4 * q], __uint_as_float(v[4 * q + 1]) + be[4 * q + 1],
+                                             __uint_as_float(v[4 * q + 2]) + be[4 * q + 2],
+                                             __uint_as_float(v[4 * q + 3]) + be[4 * q + 3]);
                 }
             }
         }
