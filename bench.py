@@ -425,8 +425,9 @@ def side_rooflines(F, model, desc, dtype, batch, B, devb, out, stage_ms, pk, pk_
         "frac": g_tf / F32_ALU_PEAK_TFLOPS, "traffic": None, "algorithmic_flops": fl, "kernel_ms": g_ms,
         "radius_graph_ms": r_ms, "edges_per_pose": (sum(ec) + sum(en)) / B,
         "kernel": ("sg_transform_kernel + sg_step_kernel + sg_gather_kernel (FP32 CUDA cores)" if dtype == "f32" else
-                   "sg_transform_kernel + per step sg_message_kernel and sg_gru_tc_kernel (GRU and transforms on "
-                   "the tcgen05 tensor cores, three BF16 terms per product) + sg_gather_kernel") +
+                   "sg_stage_tc_kernel (stage gate and first transforms) + per step sg_message_kernel and "
+                   "sg_gru_tc_kernel (GRU and next transforms), the contractions on the tcgen05 tensor cores with "
+                   "three BF16 terms per product, + sg_gather_kernel") +
                   ", timed with the branches serialised",
         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" +
                        ("" if dtype == "f32" else "; achieved counts the FP32 algorithmic flops once (the "

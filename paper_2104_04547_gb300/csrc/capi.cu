@@ -257,6 +257,7 @@ struct fusion_model {
     float *we_p[FUSION_MAX_STAGES][2] = {}, *be[FUSION_MAX_STAGES][2] = {};
     float *gru_p[FUSION_MAX_STAGES] = {}, *bih[FUSION_MAX_STAGES] = {}, *bhh[FUSION_MAX_STAGES] = {};
     uint16_t *gru_tc[FUSION_MAX_STAGES] = {};   // tensor-core step weights (sg_gru_tc_pack)
+    uint16_t *gate_tc = nullptr;                // tensor-core stage gate weights (sg_stage_tc_pack)
     float *gi_t = nullptr, *gbi = nullptr, *gj_t = nullptr, *gbj = nullptr;
     float *gat_wg_t = nullptr, *gat_bg = nullptr, *gat_wo_t = nullptr, *gat_bo = nullptr;
     float *head_wt[FUSION_MAX_HEAD] = {}, *head_b[FUSION_MAX_HEAD] = {};
@@ -540,10 +541,15 @@ int load_weights(fusion_model *m, const float *blob) {
             const float *wj = take();
             const float *bj = take();
             auto hcol = [w, H](int c) { return c < w ? c : H + (c - w); };   // [h (w), h0 (w0)] -> [h, h0] at H
-            RC(upload(m, &m->gi_t, transpose(pad_mat(wi, wn, w + w0, H, 2 * H, id, hcol).data(), H, 2 * H)));
+            const std::vector<float> wip = pad_mat(wi, wn, w + w0, H, 2 * H, id, hcol);
+            const std::vector<float> wjp = pad_mat(wj, wn, w, H, H, id, id);
+            RC(upload(m, &m->gi_t, transpose(wip.data(), H, 2 * H)));
             RC(upload(m, &m->gbi, pad_vec(bi, wn, H)));
-            RC(upload(m, &m->gj_t, transpose(pad_mat(wj, wn, w, H, H, id, id).data(), H, H)));
+            RC(upload(m, &m->gj_t, transpose(wjp.data(), H, H)));
             RC(upload(m, &m->gbj, pad_vec(bj, wn, H)));
+            std::vector<uint16_t> img(sg_stage_tc_image_elems(H));
+            sg_stage_tc_pack(wip.data(), wjp.data(), H, img.data());
+            RC(upload_raw(m, reinterpret_cast<void **>(&m->gate_tc), img.data(), img.size() * 2));
         }
     }
     const int G = d.sg_gather_width;
@@ -941,8 +947,31 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
                 ta.be[e] = use ? m->be[s][e] : nullptr;
                 ta.T[e] = m->Tbuf[e][tcur];
             }
-            launch_sg_transform(ta, sgs);
-            RC(check_launch("sg_transform"));
+            if (m->sg_tc) {
+                SgStageTcArgs ga{};
+                ga.feat = feat_d;
+                ga.h_in = s == 0 ? nullptr : h;
+                ga.x_out = m->xin;
+                for (int e = 0; e < 2; ++e) {
+                    ga.T_out[e] = ta.we_p[e] ? ta.T[e] : nullptr;
+                    ga.be[e] = ta.be[e];
+                }
+                if (s > 0 && d.sg_gate) {
+                    ga.wg = m->gate_tc;
+                    ga.gbi = m->gbi;
+                    ga.gbj = m->gbj;
+                }
+                ga.we = m->gru_tc[s] + 12 * (size_t)H * H;
+                ga.A = A;
+                ga.H = H;
+                ga.A_dev = A_dev;
+                ga.err = m->err;
+                launch_sg_stage_tc(ga, sgs);
+                RC(check_launch("sg_stage_tc"));
+            } else {
+                launch_sg_transform(ta, sgs);
+                RC(check_launch("sg_transform"));
+            }
             h = m->xin;
             for (int k = 0; k < d.sg_steps[s]; ++k) {
                 SgStepArgs sa{};

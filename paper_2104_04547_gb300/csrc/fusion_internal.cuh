@@ -256,8 +256,30 @@ struct SgGruTcArgs {
     unsigned *err;
 };
 void launch_sg_gru_tc(const SgGruTcArgs &a, cudaStream_t s);
-// Sets the kernel's shared-memory limit and sizes its persistent grid (call before any capture).
+// Sets the tensor-core graph kernels' shared-memory limits and sizes their persistent grids (call before
+// any capture).
 void sg_gru_tc_prepare(int H);
+
+// A stage's input and first transforms on the tensor cores (k_sgcnn_tc.cu): x = the gate of the previous
+// stage's states and h0 (wg set), or h0 (h_in null), or h_in; T_e = W_e x + b_e.
+struct SgStageTcArgs {
+    const float *feat;     // [A][19]
+    const float *h_in;     // [A][H] previous stage's final states (nullptr: the first stage, x = h0)
+    float *x_out;          // [A][H] the stage input (may be h_in: each row is read before it is written)
+    float *T_out[2];       // [A][H] transforms of x (nullptr: not needed)
+    const uint16_t *wg;    // gate image (sg_stage_tc_pack), nullptr: no gate
+    const uint16_t *we;    // the stage's two W_e slots, laid out as in the GRU image (its last 4 H^2 values)
+    const float *gbi, *gbj;   // gate biases [H]
+    const float *be[2];       // transform biases [H] of the T_out slots
+    int A, H;
+    const int32_t *A_dev;
+    unsigned *err;
+};
+void launch_sg_stage_tc(const SgStageTcArgs &a, cudaStream_t s);
+// The gate image: BF16 hi / lo parts of [W_i columns of h ; W_j] ([2H][H]) then of W_i's columns of h0
+// ([H][H]), K-major; wi is the padded [H][2H] gate matrix, wj [H][H]; sg_stage_tc_image_elems(H) values.
+size_t sg_stage_tc_image_elems(int H);
+void sg_stage_tc_pack(const float *wi, const float *wj, int H, uint16_t *img);
 // The weight image of a stage: BF16 hi / lo parts of W_ih and W_hh ([3H][H]) and of the two transform
 // slots' W_e ([H][H]; nullptr: zeros), each part K-major [H/8][rows][8]; sg_gru_tc_image_elems(H) values.
 size_t sg_gru_tc_image_elems(int H);

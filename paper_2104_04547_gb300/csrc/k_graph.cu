@@ -27,7 +27,7 @@ namespace {
 
 constexpr int kCells = kGridCellsMax * kGridCellsMax * kGridCellsMax;
 constexpr int kThreads = 256;
-constexpr int kGraphSplit = 4;      // CTAs per pose in the count and fill passes
+constexpr int kGraphSplit = 8;      // CTAs per pose in the count and fill passes
 
 // In-place exclusive scan of d[0..n) by the whole block; returns the total.
 __device__ int block_exscan(int *d, int n, int *s_tmp /* [33] */) {

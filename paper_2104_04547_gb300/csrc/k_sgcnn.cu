@@ -15,8 +15,8 @@
 // then by the previous step), so a step is a segment sum over the sorted CSR
 // row in a fixed order followed by the GRU matrix-vector products, all
 // deterministic.  The gather is one CTA per
-// pose: warps take ligand atoms round robin and the warp partials are added in
-// warp order.
+// pose and 32 outputs: warps take ligand atoms round robin and the warp
+// partials are added in warp order.
 #include "fusion_internal.cuh"
 
 namespace fusion {
@@ -302,53 +302,73 @@ __global__ void __launch_bounds__(kWarps * 32, step_min_blocks<H, NP>()) sg_step
         if (a.T_out[e]) edge_transform<H, NP>(v, a.we_p[e], a.be[e], lane, np, i0, a.T_out[e]);
 }
 
+// One CTA per (pose, 32 gather outputs): lane l computes output g = 32 blockIdx.y + l; the warps take the
+// pose's ligand atoms round robin and their partials are added in warp order, so every output's sum has the
+// same order whatever the gather width.  A warp evaluates its next four atoms together (four independent
+// multiply-add chains per lane) and adds them to its partial in atom order.
+constexpr int kGatherAtoms = 4;
+
 template <int H>
 __global__ void __launch_bounds__(kWarps * 32) sg_gather_kernel(SgGatherArgs a) {
-    __shared__ float sv[kWarps][2 * H];
-    __shared__ float part[kWarps][256];
+    __shared__ float sv[kWarps][kGatherAtoms][2 * H];
+    __shared__ float part[kWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x;
+    const int g = blockIdx.y * 32 + lane;
     const int a0 = a.atom_off[p];
     const int N = a.atom_off[p + 1] - a0;
     int nl = a.n_lig[p];
     if (nl > N || nl < 0) nl = 0;      // invalid pose: flagged by the prep kernel
     const int G = a.G;
-    float acc[8];
+    const bool on = g < G;
+    const int gc = on ? g : 0;         // a valid column for the loads of idle lanes
+    float acc = 0.f;
+    float (*v)[2 * H] = sv[warp];
+    for (int i0 = warp; i0 < nl; i0 += kWarps * kGatherAtoms) {
+        int na = 0;                    // atoms of this group: i0, i0 + 8, ... below nl
 #pragma unroll
-    for (int g = 0; g < 8; ++g) acc[g] = 0.f;
-    float *v = sv[warp];
-    for (int i = warp; i < nl; i += kWarps) {
-        const size_t ai = (size_t)a0 + i;
-        for (int o = lane; o < H; o += 32) {
-            v[o] = a.h[ai * H + o];
-            v[H + o] = a.x[ai * H + o];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int gj = 0; gj < 8; ++gj) {
-            const int g = lane + 32 * gj;
-            if (g >= G) break;
-            float w = a.bo[g];
-            for (int k = 0; k < H; ++k) w = fmaf(a.wo_t[k * G + g], v[k], w);
-            if (a.gated) {
-                float u = a.bg[g];
-                for (int k = 0; k < 2 * H; ++k) u = fmaf(a.wg_t[k * G + g], v[k], u);
-                acc[gj] += sigm(u) * w;
-            } else {
-                acc[gj] += w;
+        for (int t = 0; t < kGatherAtoms; ++t) {
+            const int i = i0 + t * kWarps;
+            if (i < nl) {
+                const size_t ai = (size_t)a0 + i;
+                for (int o = lane; o < H; o += 32) {
+                    v[t][o] = a.h[ai * H + o];
+                    v[t][H + o] = a.x[ai * H + o];
+                }
+                na = t + 1;
             }
         }
         __syncwarp();
-    }
+        float w[kGatherAtoms], u[kGatherAtoms];
 #pragma unroll
-    for (int gj = 0; gj < 8; ++gj) {
-        const int g = lane + 32 * gj;
-        if (g < G) part[warp][g] = acc[gj];
+        for (int t = 0; t < kGatherAtoms; ++t) {
+            w[t] = a.bo[gc];
+            u[t] = a.gated ? a.bg[gc] : 0.f;   // the linear gather has no gate (bg, wg_t are null)
+        }
+#pragma unroll 4
+        for (int k = 0; k < H; ++k) {
+            const float wk = __ldg(a.wo_t + k * G + gc);
+#pragma unroll
+            for (int t = 0; t < kGatherAtoms; ++t) w[t] = fmaf(wk, v[t][k], w[t]);
+        }
+        if (a.gated) {
+#pragma unroll 4
+            for (int k = 0; k < 2 * H; ++k) {
+                const float wk = __ldg(a.wg_t + k * G + gc);
+#pragma unroll
+                for (int t = 0; t < kGatherAtoms; ++t) u[t] = fmaf(wk, v[t][k], u[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kGatherAtoms; ++t)
+            if (t < na) acc += a.gated ? sigm(u[t]) * w[t] : w[t];
+        __syncwarp();
     }
+    part[warp][lane] = acc;
     __syncthreads();
-    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    if (threadIdx.x < 32 && on) {
         float s = 0.f;
-        for (int w = 0; w < kWarps; ++w) s += part[w][g];
+        for (int w = 0; w < kWarps; ++w) s += part[w][lane];
         a.out[(size_t)p * G + g] = s;
     }
 }
@@ -419,8 +439,9 @@ void launch_sg_message(const SgStepArgs &a, float *m, cudaStream_t s) {
 }
 
 void launch_sg_gather(const SgGatherArgs &a, cudaStream_t s) {
-    if (a.H == 64) sg_gather_kernel<64><<<a.B, kWarps * 32, 0, s>>>(a);
-    else sg_gather_kernel<32><<<a.B, kWarps * 32, 0, s>>>(a);
+    const dim3 grid(a.B, (a.G + 31) / 32);
+    if (a.H == 64) sg_gather_kernel<64><<<grid, kWarps * 32, 0, s>>>(a);
+    else sg_gather_kernel<32><<<grid, kWarps * 32, 0, s>>>(a);
 }
 
 }  // namespace fusion

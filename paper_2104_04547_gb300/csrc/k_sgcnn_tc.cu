@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 
 #include <cstring>
+#include <vector>
 
 namespace fusion {
 
@@ -348,6 +349,247 @@ __global__ void __launch_bounds__(kThreads, 1) sg_gru_tc_kernel(SgGruTcArgs a) {
     if (warp == 0) tc::tmem_dealloc(tbase, P::kTmemCols);
 }
 
+// ---- stage start: the stage input x and its first transforms ----
+//
+// x = sigmoid(W_i [h, h0] + b_i) * (W_j h + b_j) with the gate between stages, else x = h0 (the first stage:
+// atom features zero-padded to H) or x = h (no gate); then T_e = W_e x + b_e for the stage's edge types.
+// Tensor-memory columns: W_i [h, h0] at 0 .. H and W_j h at H .. 2H ([W_i,h ; W_j] is one N = 2H product of
+// h, W_i,h0 h0 accumulates onto the first half); the transforms reuse 0 .. 2H.
+template <int H>
+struct StagePlan {
+    static constexpr uint32_t kGa = 2 * H * H * 2;          // one BF16 part of [W_i,h ; W_j], [H/8][2H][8]
+    static constexpr uint32_t kGb = H * H * 2;              // one BF16 part of W_i,h0, [H/8][H][8]
+    static constexpr uint32_t kE = H * H * 2;               // one BF16 part of W_e
+    static constexpr uint32_t oGb = 2 * kGa, oE = oGb + 2 * kGb, kW = oE + 4 * kE;
+    static constexpr uint32_t kA = kTileM * H * 2;
+    static constexpr uint32_t oXhi = kW, oXlo = oXhi + kA, oYhi = oXlo + kA, oYlo = oYhi + kA;
+    static constexpr uint32_t oBias = oYlo + kA;            // b_i, b_j, b_e0, b_e1
+    static constexpr uint32_t oBar = oBias + 4 * H * 4;
+    static constexpr uint32_t kSmem = oBar + 32;
+    static constexpr uint32_t kTmemCols = 2 * H;            // 128 or 64
+    static constexpr int kCols = H / 4;
+};
+
+template <int H>
+__global__ void __launch_bounds__(kThreads, 1) sg_stage_tc_kernel(SgStageTcArgs a) {
+    using P = StagePlan<H>;
+    constexpr int C = P::kCols;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *w_bar = reinterpret_cast<uint64_t *>(smem + P::oBar);
+    uint64_t *mma_bar = w_bar + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_bar + 1);
+    float *sb = reinterpret_cast<float *>(smem + P::oBias);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int A = a.A_dev ? *a.A_dev : a.A;
+    if (A > a.A) A = a.A;
+    const int n_tiles = (A + kTileM - 1) / kTileM;
+    const bool gate = a.wg != nullptr && a.h_in != nullptr;
+    const bool any_T = a.T_out[0] || a.T_out[1];
+    const uint64_t deadline = tc::globaltimer() + kWaitNs;
+
+    if (tid == 0) {
+        tc::mbar_init(w_bar, 1);
+        tc::mbar_init(mma_bar, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, P::kTmemCols);
+    for (int o = tid; o < H; o += kThreads) {
+        sb[o] = gate ? a.gbi[o] : 0.f;
+        sb[H + o] = gate ? a.gbj[o] : 0.f;
+        sb[2 * H + o] = a.T_out[0] ? a.be[0][o] : 0.f;
+        sb[3 * H + o] = a.T_out[1] ? a.be[1][o] : 0.f;
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+
+    bool w_issued = false, w_ready = false;
+    if (tid == 0 && (int)blockIdx.x < n_tiles && (gate || any_T)) {
+        uint32_t bytes = gate ? 2 * P::kGa + 2 * P::kGb : 0;
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+            if (a.T_out[e]) bytes += 2 * P::kE;
+        tc::mbar_expect_tx(w_bar, bytes);
+        if (gate) tc::bulk_load(smem, a.wg, 2 * P::kGa + 2 * P::kGb, w_bar);
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+            if (a.T_out[e])
+                tc::bulk_load(smem + P::oE + e * 2 * P::kE, reinterpret_cast<const unsigned char *>(a.we) + e * 2 * P::kE,
+                              2 * P::kE, w_bar);
+        w_issued = true;
+    }
+
+    const uint32_t s0 = tc::smem_u32(smem);
+    const uint32_t sXhi = s0 + P::oXhi, sXlo = s0 + P::oXlo, sYhi = s0 + P::oYhi, sYlo = s0 + P::oYlo;
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const int o0 = (warp >> 2) * C;
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    uint32_t phase = 0;
+    bool pending = false, ok = true;
+
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int i0 = tile * kTileM;
+        // ---- operands: gate: X = h, Y = h0; otherwise X = x (= h0 or h), also written out here ----
+        {
+            constexpr int F4 = H / 4, CG = F4 / 4;
+#pragma unroll
+            for (int idx = tid; idx < kTileM * F4; idx += kThreads) {
+                const int g = idx >> 5, l = idx & 31;
+                const int r = (g / CG) * 8 + (l >> 2);
+                const int f4 = (g % CG) * 4 + (l & 3);
+                const int gi = i0 + r;
+                float4 h0 = make_float4(0.f, 0.f, 0.f, 0.f), h = h0;
+                if (gi < A) {
+                    float f[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int o = 4 * f4 + u;
+                        f[u] = o < kFeat ? __ldg(a.feat + (size_t)gi * kFeat + o) : 0.f;
+                    }
+                    h0 = make_float4(f[0], f[1], f[2], f[3]);
+                    if (a.h_in) h = __ldg(reinterpret_cast<const float4 *>(a.h_in + (size_t)gi * H) + f4);
+                }
+                const float4 x = gate ? h : (a.h_in ? h : h0);
+                const uint32_t o = (uint32_t)(((f4 >> 1) * kTileM + r) * 16 + (f4 & 1) * 8);
+                uint2 hi, lo;
+                split4(x, hi, lo);
+                *reinterpret_cast<uint2 *>(smem + P::oXhi + o) = hi;
+                *reinterpret_cast<uint2 *>(smem + P::oXlo + o) = lo;
+                if (gate) {
+                    split4(h0, hi, lo);
+                    *reinterpret_cast<uint2 *>(smem + P::oYhi + o) = hi;
+                    *reinterpret_cast<uint2 *>(smem + P::oYlo + o) = lo;
+                } else if (gi < A) {
+                    reinterpret_cast<float4 *>(a.x_out + (size_t)gi * H)[f4] = x;
+                }
+            }
+        }
+        tc::fence_proxy_async();
+        tc::tc_fence_before();
+        __syncthreads();
+        tc::tc_fence_after();
+
+        const int gi = i0 + row;
+        const bool valid = gi < A;
+        if (gate) {
+            bool issued = true;
+            if (tid == 0) {
+                if (!w_ready) {
+                    w_ready = tc::mbar_wait(w_bar, 0, deadline, a.err, FUSION_ERR_TIMEOUT);
+                    issued = w_ready;
+                }
+                if (issued) {
+                    tc::tc_fence_after();
+                    constexpr uint32_t I2 = tc::idesc_bf16(kTileM, 2 * H), I1 = tc::idesc_bf16(kTileM, H);
+                    product3<H>(tbase, sXhi, sXlo, s0, s0 + P::kGa, 2 * H, I2, false);
+                    product3<H>(tbase, sYhi, sYlo, s0 + P::oGb, s0 + P::oGb + P::kGb, H, I1, true);
+                    tc::mma_commit(mma_bar);
+                    pending = true;
+                }
+            }
+            if (!__syncthreads_and(issued)) { ok = false; break; }
+            if (!__syncthreads_and(tc::mbar_wait(mma_bar, phase, deadline, a.err, FUSION_ERR_TIMEOUT))) {
+                ok = false;
+                break;
+            }
+            phase ^= 1;
+            pending = false;
+            tc::tc_fence_after();
+            // ---- x = sigmoid(gi + b_i) * (gj + b_j): to global and as the transforms' operand ----
+            uint32_t vi[C], vj[C];
+            tmem_ld_cols<C>(tbase + lane_addr + o0, vi);
+            tmem_ld_cols<C>(tbase + lane_addr + H + o0, vj);
+            tc::tmem_ld_wait();
+            float x[C];
+#pragma unroll
+            for (int q = 0; q < C; ++q)
+                x[q] = sigm_fast(__uint_as_float(vi[q]) + sb[o0 + q]) * (__uint_as_float(vj[q]) + sb[H + o0 + q]);
+            if (valid) {
+                float4 *dst = reinterpret_cast<float4 *>(a.x_out + (size_t)gi * H + o0);
+#pragma unroll
+                for (int q = 0; q < C / 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+            }
+#pragma unroll
+            for (int s = 0; s < C / 8; ++s) {
+                uint2 h0, l0, h1, l1;
+                split4(make_float4(x[8 * s], x[8 * s + 1], x[8 * s + 2], x[8 * s + 3]), h0, l0);
+                split4(make_float4(x[8 * s + 4], x[8 * s + 5], x[8 * s + 6], x[8 * s + 7]), h1, l1);
+                const uint32_t o = (uint32_t)((((o0 >> 3) + s) * kTileM + row) * 16);
+                *reinterpret_cast<uint4 *>(smem + P::oXhi + o) = make_uint4(h0.x, h0.y, h1.x, h1.y);
+                *reinterpret_cast<uint4 *>(smem + P::oXlo + o) = make_uint4(l0.x, l0.y, l1.x, l1.y);
+            }
+            tc::fence_proxy_async();
+            tc::tc_fence_before();
+            __syncthreads();
+            tc::tc_fence_after();
+        }
+
+        if (any_T) {
+            // ---- T_e = x W_e^T + b_e (columns e H .. (e + 1) H) ----
+            bool issued = true;
+            if (tid == 0) {
+                if (!w_ready) {
+                    w_ready = tc::mbar_wait(w_bar, 0, deadline, a.err, FUSION_ERR_TIMEOUT);
+                    issued = w_ready;
+                }
+                if (issued) {
+                    tc::tc_fence_after();
+                    constexpr uint32_t I1 = tc::idesc_bf16(kTileM, H);
+#pragma unroll
+                    for (int e = 0; e < 2; ++e)
+                        if (a.T_out[e]) {
+                            const uint32_t we = s0 + P::oE + e * 2 * P::kE;
+                            product3<H>(tbase + e * H, sXhi, sXlo, we, we + P::kE, H, I1, false);
+                        }
+                    tc::mma_commit(mma_bar);
+                    pending = true;
+                }
+            }
+            if (!__syncthreads_and(issued)) { ok = false; break; }
+            if (!__syncthreads_and(tc::mbar_wait(mma_bar, phase, deadline, a.err, FUSION_ERR_TIMEOUT))) {
+                ok = false;
+                break;
+            }
+            phase ^= 1;
+            pending = false;
+            tc::tc_fence_after();
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (!a.T_out[e]) continue;
+                uint32_t v[C];
+                tmem_ld_cols<C>(tbase + lane_addr + e * H + o0, v);
+                tc::tmem_ld_wait();
+                if (valid) {
+                    const float *be = sb + (2 + e) * H + o0;
+                    float4 *dst = reinterpret_cast<float4 *>(a.T_out[e] + (size_t)gi * H + o0);
+#pragma unroll
+                    for (int q = 0; q < C / 4; ++q)
+                        dst[q] = make_float4(__uint_as_float(v[4 * q]) + be[4 * q], __uint_as_float(v[4 * q + 1]) + be[4 * q + 1],
+                                             __uint_as_float(v[4 * q + 2]) + be[4 * q + 2],
+                                             __uint_as_float(v[4 * q + 3]) + be[4 * q + 3]);
+                }
+            }
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+        tc::tc_fence_after();
+    }
+
+    if (!ok) atomicOr(a.err, FUSION_ERR_TIMEOUT);
+    if (tid == 0) {
+        const uint64_t dl = tc::globaltimer() + 100000000ull;
+        if (w_issued && !w_ready && !tc::mbar_wait(w_bar, 0, dl)) atomicOr(a.err, FUSION_ERR_TIMEOUT);
+        if (pending && !tc::mbar_wait(mma_bar, phase, dl)) atomicOr(a.err, FUSION_ERR_TIMEOUT);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tbase, P::kTmemCols);
+}
+
 uint16_t host_bf16(float v) {
     uint32_t u;
     std::memcpy(&u, &v, 4);
@@ -379,6 +621,21 @@ void pack_parts(const float *w, int rows, int H, uint16_t *dst) {
 
 size_t sg_gru_tc_image_elems(int H) { return (size_t)16 * H * H; }
 
+size_t sg_stage_tc_image_elems(int H) { return (size_t)6 * H * H; }
+
+void sg_stage_tc_pack(const float *wi, const float *wj, int H, uint16_t *img) {
+    // [W_i,h ; W_j] ([2H][H]: W_i's columns of h, then W_j), then W_i,h0 ([H][H]: W_i's columns of h0)
+    std::vector<float> ga((size_t)2 * H * H), gb((size_t)H * H);
+    for (int r = 0; r < H; ++r)
+        for (int k = 0; k < H; ++k) {
+            ga[(size_t)r * H + k] = wi[(size_t)r * 2 * H + k];
+            ga[(size_t)(H + r) * H + k] = wj[(size_t)r * H + k];
+            gb[(size_t)r * H + k] = wi[(size_t)r * 2 * H + H + k];
+        }
+    pack_parts(ga.data(), 2 * H, H, img);
+    pack_parts(gb.data(), H, H, img + (size_t)4 * H * H);
+}
+
 void sg_gru_tc_pack(const float *wih, const float *whh, const float *we0, const float *we1, int H, uint16_t *img) {
     const size_t nIH = (size_t)3 * H * H, nE = (size_t)H * H;
     pack_parts(wih, 3 * H, H, img);
@@ -391,38 +648,62 @@ void sg_gru_tc_pack(const float *wih, const float *whh, const float *we0, const 
     }
 }
 
-// Persistent grid: the SMs times the CTAs of this width that fit one SM (one at H = 64, two at H = 32).
+// Persistent grid: the SMs times the CTAs of the kernel that fit one SM.
+template <class K>
+static int grid_cap(K kernel, uint32_t smem) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+    return (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+}
+
 template <int H>
-static int grid_cap() {
-    static int cap = 0;
-    if (!cap) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(sg_gru_tc_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Plan<H>::kSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sg_gru_tc_kernel<H>, kThreads, Plan<H>::kSmem);
-        cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    }
+static int gru_cap() {
+    static int cap = grid_cap(sg_gru_tc_kernel<H>, Plan<H>::kSmem);
+    return cap;
+}
+
+template <int H>
+static int stage_cap() {
+    static int cap = grid_cap(sg_stage_tc_kernel<H>, StagePlan<H>::kSmem);
     return cap;
 }
 
 void sg_gru_tc_prepare(int H) {
-    if (H == 64) grid_cap<64>();
-    else grid_cap<32>();
+    if (H == 64) {
+        gru_cap<64>();
+        stage_cap<64>();
+    } else {
+        gru_cap<32>();
+        stage_cap<32>();
+    }
 }
 
-template <int H>
-static void launch_h(const SgGruTcArgs &a, cudaStream_t s) {
-    const int tiles = (a.A + kTileM - 1) / kTileM;
-    const int cap = grid_cap<H>();
-    const int grid = tiles < cap ? tiles : cap;
-    if (grid <= 0) return;
-    sg_gru_tc_kernel<H><<<grid, kThreads, Plan<H>::kSmem, s>>>(a);
+static int persistent_grid(int A, int cap) {
+    const int tiles = (A + kTileM - 1) / kTileM;
+    return tiles < cap ? tiles : cap;
 }
 
 void launch_sg_gru_tc(const SgGruTcArgs &a, cudaStream_t s) {
-    if (a.H == 64) launch_h<64>(a, s);
-    else launch_h<32>(a, s);
+    if (a.H == 64) {
+        const int g = persistent_grid(a.A, gru_cap<64>());
+        if (g > 0) sg_gru_tc_kernel<64><<<g, kThreads, Plan<64>::kSmem, s>>>(a);
+    } else {
+        const int g = persistent_grid(a.A, gru_cap<32>());
+        if (g > 0) sg_gru_tc_kernel<32><<<g, kThreads, Plan<32>::kSmem, s>>>(a);
+    }
+}
+
+void launch_sg_stage_tc(const SgStageTcArgs &a, cudaStream_t s) {
+    if (a.H == 64) {
+        const int g = persistent_grid(a.A, stage_cap<64>());
+        if (g > 0) sg_stage_tc_kernel<64><<<g, kThreads, StagePlan<64>::kSmem, s>>>(a);
+    } else {
+        const int g = persistent_grid(a.A, stage_cap<32>());
+        if (g > 0) sg_stage_tc_kernel<32><<<g, kThreads, StagePlan<32>::kSmem, s>>>(a);
+    }
 }
 
 }  // namespace fusion

@@ -1,16 +1,16 @@
-"""Gated graph steps on the tensor cores (FUSION_OPT_GRAPH_TENSOR_CORES, Section 3.3.1's gated graph
+"""Gated graph convolution on the tensor cores (FUSION_OPT_GRAPH_TENSOR_CORES, Section 3.3.1's gated graph
 convolution).
 
-The GRU update and the next step's edge transforms run as three BF16 MMAs per product: each operand x is
+The stage gate, the GRU updates and the edge transforms run as three BF16 MMAs per product: each operand x is
 split into x_hi = bf16(x) and x_lo = bf16(x - x_hi), and x y = x_lo y_hi + x_hi y_lo + x_hi y_hi with FP32
 accumulation.  What is dropped (x_lo y_lo and the remainders of both splits) is at most about 3 * 2^-16
 (4.6e-5) of |x y| per term, and a dot product over K <= 64 inputs errs by a few 1e-6 of the sum of its
 |terms| (the rounding errors cancel).  Node states are bounded by 1 (a GRU's h' is a convex mix of tanh and
-h); the message sums add up to ~60 transforms and the errors carry through up to 9 steps.  Measured worst
-node-state deviations from the FP32 CUDA-core graph: 1.5e-4 (full-size model, 6 steps) and 5.2e-4
-(paper-final model, 9 steps, 160 poses); STATE_TOL = 2e-3 keeps 4x room.  A product with a term missing,
-or plain BF16 products, errs by over 100x more per dot product (tests/test_split_bf16.py checks both
-figures on the CPU), and a gate out of order or a missing bias moves states by far more.
+h); the message sums add up to ~60 transforms and the errors carry through the stage gate and up to 9
+steps.  Measured worst node-state deviations from the FP32 CUDA-core graph: 1.4e-4 (full-size model, 6
+steps) and 9.0e-4 (paper-final model, 9 steps, 160 poses); STATE_TOL = 2e-3 keeps 2x room.  A product with
+a term missing, or plain BF16 products, errs by over 100x more per dot product (tests/test_split_bf16.py
+checks both figures on the CPU), and a gate out of order or a missing bias moves states by far more.
 
 * FP32 full-size model (H = 64) on the 64-pose workload with the graph on the tensor cores: every pose's
   SG latent against the stored FP64 oracle values, the affinities within 1e-3 of them; the same batch on
