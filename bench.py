@@ -345,6 +345,31 @@ def time_steps(model, devb, B, out, stream, flush, steps, warmup, barrier):
     return [s.elapsed_time(e) for s, e in ev], stage_ms
 
 
+def paper_final_run(F, torch, batch, devb, B, stream, flush, steps, warmup, barrier):
+    """The `fusion-paper-final` model on this batch: BF16 and FP8 poses/s (K timed calls each, as for the main
+    line), and each dtype's |affinity difference| against the model's FP32 path (one call)."""
+    import numpy as np
+    from synth import configs, weights
+    name = "fusion-paper-final"
+    W = weights.init_weights(configs.model(name), WEIGHTS_SEED)
+    d32 = configs.model(name, dtype="f32")
+    m32 = F.Model(d32, weights.to_blob(d32, W), max_poses=B, max_atoms=1200, max_degree=64, stream=stream.cuda_stream)
+    ref = m32.score(batch).copy()
+    m32.close()
+    res = {"model": f"{name} (3D-CNN 32/64 filters, SG-CNN widths 19 and 24, 6 + 3 graph steps)"}
+    for dt in ("bf16", "fp8"):
+        d = configs.model(name, dtype=dt)
+        m = F.Model(d, weights.to_blob(d, W), max_poses=B, max_atoms=1200, max_degree=64, stream=stream.cuda_stream)
+        o = torch.empty(B, dtype=torch.float32, device="cuda")
+        sm, _st = time_steps(m, devb, B, o, stream, flush, steps, warmup, barrier)
+        got = o.float().cpu().numpy().copy()
+        m.close()
+        dd = np.abs(got.astype(np.float64) - ref)
+        res[dt] = {"value": B * steps / (sum(sm) / 1000.0), "unit": "poses/s", "ms_per_step": sum(sm) / steps,
+                   "delta_vs_fp32_path": {"mean": float(dd.mean()), "max": float(dd.max()), "tolerance": 0.05}}
+    return res
+
+
 def conv_roofline(desc, dtype, B, stage_ms, pk, pk_src, model_name, fp8_peak=None):
     import statistics as st
     conv_names = [f"conv{i}" for i in range(len(desc["conv"]))]
@@ -669,6 +694,12 @@ def run_ours(args):
         extra["fp8_peak_tflops"] = {"value": fp8_peak, "how": "torch._scaled_mm E4M3 8192^3, best of 10 "
                                                               "(with and without fast accumulation), this run"}
 
+    # the paper's final architecture (Tables II, III, V) on the same batch: BF16 and FP8 throughput under the same
+    # timing rules, |affinity difference| against its FP32 path
+    if rank == 0 and args.model == MODEL and not args.no_extras and B == 64:
+        extra["paper_final"] = paper_final_run(F, torch, batch, devb, B, stream, flush, args.steps, args.warmup,
+                                               barrier)
+
     if rank == 0 and world == 1 and not args.no_serving and args.model == MODEL:
         extra["serving"] = serving_run(F, args.model, W, lambda dt: weights.to_blob(configs.model(args.model, dt), W),
                                        args.serving_requests)
@@ -721,7 +752,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f32-compare", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the per-kernel-group rooflines and the other tensor-core dtype's run")
+                    help="skip the per-kernel-group rooflines, the other tensor-core dtype's run and the "
+                         "paper-final model's run")
     ap.add_argument("--no-serving", action="store_true", help="skip the bounded serving measurement")
     ap.add_argument("--serving-requests", type=int, default=4000)
     ap.add_argument("--poses", type=int, default=64, help="first N poses of the batch (small profiling captures)")
