@@ -232,12 +232,12 @@ int fusion_last_timings(fusion_model *m, float *out, int32_t n);
                                           0 restores the default.  Scores are the same.  Drops captured
                                           graphs.  Any dtype */
 
-#define FUSION_OPT_GRAPH_TENSOR_CORES 6   /* graph convolution: value 1 runs each gated step's GRU update and
-                                            the next step's edge transforms (Section 3.3.1) on the tcgen05
+#define FUSION_OPT_GRAPH_TENSOR_CORES 6   /* graph convolution: value 1 runs the stage gate, each gated step's
+                                            GRU update and the edge transforms (Section 3.3.1) on the tcgen05
                                             tensor cores, 128 nodes per tile, each product as three BF16 MMAs
                                             of the operands' BF16 high and low parts with FP32 accumulation
                                             (each product within 3 x 2^-16 of FP32's; node states within
-                                            about 5e-4 of the FP32 path's after 9 steps); 0 runs them on the CUDA
+                                            about 1e-3 of the FP32 path's after 9 steps); 0 runs them on the CUDA
                                             cores in FP32; -1 = the default, 1 for BF16 / FP8 models and 0
                                             for FP32 ones.  The message sums stay in their order either way.
                                             Drops captured graphs.  Any dtype */

@@ -1,6 +1,7 @@
-// Gated graph step on the tcgen05 tensor cores: the GRU update of Section 3.3.1's gated graph convolution
-// (PotentialNet's gated graph sequence steps, Table II) and the next step's edge transforms, for the
-// tensor-core models (BF16 / FP8).
+// The contractions of Section 3.3.1's gated graph convolution (PotentialNet's gated graph sequence steps,
+// Table II) on the tcgen05 tensor cores, for the tensor-core models (BF16 / FP8): sg_gru_tc_kernel does a
+// step's GRU update and the next step's edge transforms, sg_stage_tc_kernel a stage's input (the gate between
+// stages) and its first transforms.
 //
 // Per step the message m_i (the segment sum of the neighbours' transforms, summed by sg_message_kernel in
 // the SIMT path's order) and the node state h_i enter
