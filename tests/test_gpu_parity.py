@@ -129,10 +129,14 @@ def test_pose_alone_equals_pose_in_batch(F):
     np.testing.assert_array_equal(rev, full[::-1])
 
 
-def test_device_pointer_path_matches_host_path(F):
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_device_pointer_path_matches_host_path(F, dtype):
+    """Device pointers: the atom count is read on the device and the kernels are launched for the capacity
+    (the tensor-core graph kernels' persistent CTAs then skip the tiles past the count); scores equal the
+    host path's bit for bit."""
     import torch
-    desc = configs.model("fusion-20grid-ragged")
-    W = weights.init_weights(desc, 7)
+    desc = configs.model("fusion-20grid-ragged", dtype=dtype)
+    W = weights.init_weights(configs.model("fusion-20grid-ragged"), 7)
     batch = _ragged_batch()
     stream = torch.cuda.current_stream()
     m = F.Model(desc, weights.to_blob(desc, W), max_poses=8, max_atoms=512, stream=stream.cuda_stream)
