@@ -219,7 +219,9 @@ int fusion_last_timings(fusion_model *m, float *out, int32_t n);
                                             bounded waits run out (about 1 s): the call returns
                                             FUSION_ETIMEOUT with the output untouched, and later calls are
                                             normal.  Nothing faults or hangs.  FUSION_EUNSUPPORTED on the
-                                            FP32 path or with CUDA graphs on */
+                                            FP32 path or with CUDA graphs on.  Value 2: the same for the
+                                            first tensor-core graph launch (its weight copy is not issued);
+                                            FUSION_EUNSUPPORTED unless the graph runs on the tensor cores */
 
 #define FUSION_OPT_GRAPH_NODES_PER_WARP 4   /* graph convolution (gated graph steps and stage transforms on
                                                the CUDA cores; the message sums alone with the graph on the

@@ -300,6 +300,8 @@ struct fusion_model {
     int sg_npw = 4;                               // graph convolution: nodes per warp (1, 2, 4, 8)
     bool serial_branches = false;                 // both branches on the grid stream, one after the other
     bool sg_tc = false;                           // graph steps' GRU and transforms on the tensor cores
+    bool sg_stall_next = false;                   // wait-timeout test: the next call's first graph TC launch stalls
+    bool stall_armed = false;                     // a wait-timeout test waits for the next forward pass
     std::map<int, cudaGraphExec_t> graph_exec;
     std::map<int, cudaGraph_t> graph;
 
@@ -880,6 +882,7 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
                            const int32_t *nlig_d, const float *xyz_d, const float *feat_d, bool timed, int *map) {
     const fusion_model_desc &d = m->d;
     cudaStream_t ms = m->stream;        // the model's (caller-visible) stream: prep, join, head
+    m->stall_armed = false;             // this pass consumes an armed wait-timeout test
     cudaStream_t st = m->cnn_stream;    // the grid branch, at the highest stream priority
     CU(cudaMemsetAsync(m->err, 0, 4 * sizeof(unsigned), ms));
 
@@ -966,6 +969,8 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
                 ga.H = H;
                 ga.A_dev = A_dev;
                 ga.err = m->err;
+                ga.stall = m->sg_stall_next ? 1 : 0;
+                m->sg_stall_next = false;
                 launch_sg_stage_tc(ga, sgs);
                 RC(check_launch("sg_stage_tc"));
             } else {
@@ -1012,6 +1017,8 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
                     ga.H = H;
                     ga.A_dev = A_dev;
                     ga.err = m->err;
+                    ga.stall = m->sg_stall_next ? 1 : 0;
+                    m->sg_stall_next = false;
                     launch_sg_gru_tc(ga, sgs);
                     RC(check_launch("sg_gru_tc"));
                 } else {
@@ -1414,13 +1421,22 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
     if (!m) return fail(FUSION_EINVAL, "NULL model");
     switch (option) {
     case FUSION_OPT_CUDA_GRAPH:
+        // a captured graph would replay an armed wait-timeout test's stalled launch on every call
+        if (value != 0 && m->stall_armed)
+            return fail(FUSION_EUNSUPPORTED, "a wait-timeout test is armed: score once before turning graphs on");
         m->use_graph = value != 0;
         return FUSION_OK;
     case FUSION_OPT_TEST_WAIT_TIMEOUT: {
-        if (value != 1) return fail(FUSION_EINVAL, "the wait-timeout test takes value 1");
-        if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "the FP32 path has no bounded tensor-core waits");
+        if (value != 1 && value != 2) return fail(FUSION_EINVAL, "the wait-timeout test takes value 1 or 2");
         if (m->use_graph) return fail(FUSION_EUNSUPPORTED, "turn CUDA graphs off for the wait-timeout test");
-        conv_tc_stall_next(m->tcplan[0]);
+        if (value == 1) {
+            if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "the FP32 path has no bounded tensor-core waits");
+            conv_tc_stall_next(m->tcplan[0]);
+        } else {
+            if (!m->sg_tc) return fail(FUSION_EUNSUPPORTED, "the graph convolution is not on the tensor cores");
+            m->sg_stall_next = true;
+        }
+        m->stall_armed = true;
         return FUSION_OK;
     }
     case FUSION_OPT_GRAPH_NODES_PER_WARP:

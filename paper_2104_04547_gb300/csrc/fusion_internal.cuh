@@ -254,6 +254,7 @@ struct SgGruTcArgs {
     int A, H;              // H = 32 or 64
     const int32_t *A_dev;  // non-null: the atom count is *A_dev (A is then the launch capacity)
     unsigned *err;
+    int stall;             // test of the bounded waits: no weight copy is issued, so the first wait runs out
 };
 void launch_sg_gru_tc(const SgGruTcArgs &a, cudaStream_t s);
 // Sets the tensor-core graph kernels' shared-memory limits and sizes their persistent grids (call before
@@ -274,6 +275,7 @@ struct SgStageTcArgs {
     int A, H;
     const int32_t *A_dev;
     unsigned *err;
+    int stall;             // as SgGruTcArgs::stall
 };
 void launch_sg_stage_tc(const SgStageTcArgs &a, cudaStream_t s);
 // The gate image: BF16 hi / lo parts of [W_i columns of h ; W_j] ([2H][H]) then of W_i's columns of h0

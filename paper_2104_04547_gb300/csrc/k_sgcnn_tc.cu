@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1) sg_gru_tc_kernel(SgGruTcArgs a) {
 
     // the stage's weights: W_ih and W_hh always, W_e where the next step's transforms are wanted
     bool w_issued = false, w_ready = false;
-    if (tid == 0 && (int)blockIdx.x < n_tiles) {
+    if (tid == 0 && (int)blockIdx.x < n_tiles && !a.stall) {
         const unsigned char *g = reinterpret_cast<const unsigned char *>(a.w);
         uint32_t bytes = 4 * P::kIH;
 #pragma unroll
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1) sg_stage_tc_kernel(SgStageTcArgs 
     const uint32_t tbase = *tmem_slot;
 
     bool w_issued = false, w_ready = false;
-    if (tid == 0 && (int)blockIdx.x < n_tiles && (gate || any_T)) {
+    if (tid == 0 && (int)blockIdx.x < n_tiles && (gate || any_T) && !a.stall) {
         uint32_t bytes = gate ? 2 * P::kGa + 2 * P::kGb : 0;
 #pragma unroll
         for (int e = 0; e < 2; ++e)

@@ -130,3 +130,28 @@ def test_bounded_wait_runs_out_and_model_recovers(F):
     m.use_cuda_graphs(True)
     _expect(F, F.FUSION_EUNSUPPORTED, lambda: F.fusion_set_option(m.handle, F.FUSION_OPT_TEST_WAIT_TIMEOUT, 1))
     m.close()
+
+
+def test_graph_bounded_wait_runs_out_and_model_recovers(F):
+    """The same for the tensor-core graph convolution: the next call's first graph launch issues no weight
+    copy, its bounded wait runs out and sets the timeout flag (the later graph launches see the flag and give
+    up at once); the call returns FUSION_ETIMEOUT with the output untouched and the next call is normal."""
+    import time
+    desc = configs.model("fusion-20grid-ragged", dtype="bf16")
+    W = weights.init_weights(configs.model("fusion-20grid-ragged"), 3)
+    m = F.Model(desc, weights.to_blob(desc, W), max_poses=4, max_atoms=256)
+    batch = poses.pack([poses.make_pose(s, (10, 20), (40, 80)) for s in (1, 2, 3)])
+    ref = m.score(batch).copy()
+    F.fusion_set_option(m.handle, F.FUSION_OPT_TEST_WAIT_TIMEOUT, 2)
+    # an armed test keeps CUDA graphs off (a capture would replay the stalled launch)
+    _expect(F, F.FUSION_EUNSUPPORTED, lambda: m.use_cuda_graphs(True))
+    out = np.full(3, 7.0, dtype=np.float32)
+    t0 = time.perf_counter()
+    _expect(F, F.FUSION_ETIMEOUT, lambda: m.score(batch, out=out))
+    assert time.perf_counter() - t0 < 10.0
+    assert np.all(out == 7.0)
+    np.testing.assert_array_equal(m.score(batch), ref)
+    _expect(F, F.FUSION_EINVAL, lambda: F.fusion_set_option(m.handle, F.FUSION_OPT_TEST_WAIT_TIMEOUT, 3))
+    m.graph_tensor_cores(0)
+    _expect(F, F.FUSION_EUNSUPPORTED, lambda: F.fusion_set_option(m.handle, F.FUSION_OPT_TEST_WAIT_TIMEOUT, 2))
+    m.close()
