@@ -145,10 +145,34 @@ __device__ void head_layer(const float *in, int fin, float *out, int fout, const
 // Coherent Fusion: fusion layers on [cnn, sg].  Mid-level: each latent through its branch layers (SELU
 // after each), the two results appended after the latents, then the fusion layers.  Late: each latent
 // through its own affinity stack (ReLU between, last linear), the mean of the two.
+// Ask L2 for the CTA's share of a weight matrix's 128-byte lines (the head's weights, used by every CTA, are
+// usually out of L2 after the convolutions' streams; each CTA otherwise walks them from DRAM in dependent rounds).
+__device__ __forceinline__ void prefetch_share(const float *w, size_t n) {
+    if (!w) return;
+    const size_t lines = (n * 4 + 127) / 128;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < lines; q += (size_t)gridDim.x * blockDim.x)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(w) + q * 128));
+}
+
 __global__ void __launch_bounds__(256) head_kernel(HeadArgs a) {
     __shared__ float v[3][kHeadMaxWidth];
     const int p = blockIdx.x;
     const int fin0 = a.Dc + a.G;
+    {
+        int fin = fin0;
+        for (int br = 0; br < 2; ++br) {
+            int bin = br == 0 ? a.Dc : a.G;
+            for (int l = 0; l < a.n_branch[br]; ++l) {
+                prefetch_share(a.bwt[br][l], (size_t)bin * a.bwidth[br][l]);
+                bin = a.bwidth[br][l];
+            }
+            if (a.mode == FUSION_MID) fin += bin;
+        }
+        for (int l = 0; l < a.n_layers; ++l) {
+            prefetch_share(a.wt[l], (size_t)fin * a.width[l]);
+            fin = a.width[l];
+        }
+    }
     for (int i = threadIdx.x; i < fin0; i += blockDim.x)
         v[0][i] = i < a.Dc ? a.cnn[(size_t)p * a.Dc + i] : a.sg[(size_t)p * a.G + (i - a.Dc)];
     __syncthreads();
