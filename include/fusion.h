@@ -226,7 +226,8 @@ int fusion_last_timings(fusion_model *m, float *out, int32_t n);
 #define FUSION_OPT_GRAPH_NODES_PER_WARP 4   /* graph convolution (gated graph steps and stage transforms on
                                                the CUDA cores; the message sums alone with the graph on the
                                                tensor cores): value 1, 2, 4 or 8 nodes per warp, each weight
-                                               load serving them all; -1 = the default, 4.  Every node's sums keep their
+                                               load serving them all; -1 = the default, 2 with the graph on the
+                                               tensor cores, else 4.  Every node's sums keep their
                                                order, so scores are the same for every value.  Drops
                                                captured graphs.  Any dtype */
 #define FUSION_OPT_SERIAL_BRANCHES 5   /* measurement mode: value 1 runs the graph branch after the grid

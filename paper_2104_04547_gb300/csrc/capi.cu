@@ -298,6 +298,7 @@ struct fusion_model {
     bool use_graph = false;                       // replay captured CUDA graphs, one per batch size
     int group_mode = -1;                          // conv output slices per MMA: -1 default per layer, or 1, 2, 4
     int sg_npw = 4;                               // graph convolution: nodes per warp (1, 2, 4, 8)
+    bool sg_npw_set = false;                      // chosen by the caller or the autotuner (else the default)
     bool serial_branches = false;                 // both branches on the grid stream, one after the other
     bool sg_tc = false;                           // graph steps' GRU and transforms on the tensor cores
     bool sg_stall_next = false;                   // wait-timeout test: the next call's first graph TC launch stalls
@@ -675,6 +676,10 @@ int alloc_workspace(fusion_model *m) {
 
 // FP8 inputs of the stride-1 layers are stored channel-blocked (whole W-lines per TMA box row); the
 // stride-2 layers read NDHWC, since their halos step through x by 2.
+// Nodes per warp by default: 4 where the CUDA-core graph shares each weight load over them, 2 where only the
+// message sums use them (the graph on the tensor cores; measured fastest on the 64-pose calls).
+static int default_npw(const fusion_model *m) { return m->sg_tc ? 2 : 4; }
+
 static bool fp8_blocked(const fusion_model *m, int i) { return m->fp8 && m->d.conv[i].stride == 1; }
 
 // BF16 model: layer i reads its input in place, channel-blocked when it is a stride-1 layer and that
@@ -843,6 +848,7 @@ int fusion_create(const fusion_model_desc *desc, const void *weights, size_t wei
     m->bf16 = (m->d.dtype == FUSION_BF16 || m->d.dtype == FUSION_FP8);
     m->fp8 = (m->d.dtype == FUSION_FP8);
     m->sg_tc = m->bf16;
+    m->sg_npw = default_npw(m);
     m->esz = m->bf16 ? 2 : 4;
     m->grid_cx = m->bf16 ? 32 : kGridCxF32;
     {
@@ -1442,7 +1448,8 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
     case FUSION_OPT_GRAPH_NODES_PER_WARP:
         if (value != -1 && value != 1 && value != 2 && value != 4 && value != 8)
             return fail(FUSION_EINVAL, "graph nodes per warp must be -1 (default), 1, 2, 4 or 8");
-        m->sg_npw = value == -1 ? 4 : (int)value;
+        m->sg_npw = value == -1 ? default_npw(m) : (int)value;
+        m->sg_npw_set = value != -1;
         drop_graphs(m);
         return FUSION_OK;
     case FUSION_OPT_SERIAL_BRANCHES:
@@ -1454,6 +1461,7 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
         if (value != -1 && value != 0 && value != 1)
             return fail(FUSION_EINVAL, "graph tensor cores takes -1 (default), 0 or 1");
         m->sg_tc = value == -1 ? m->bf16 : value != 0;
+        if (!m->sg_npw_set) m->sg_npw = default_npw(m);
         drop_graphs(m);
         return FUSION_OK;
     case FUSION_OPT_CONV_SLICES_PER_MMA: {
@@ -1622,6 +1630,7 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
     }
     restore.armed = false;
     m->sg_npw = best_npw;
+    m->sg_npw_set = true;
     m->use_graph = graphs;
     drop_graphs(m);
     return FUSION_OK;

@@ -42,7 +42,13 @@ def test_nodes_per_warp_bit_identical(F, dtype):
             np.testing.assert_array_equal(got, ref, err_msg=f"{npw} nodes per warp")
             for p in range(len(state)):
                 np.testing.assert_array_equal(state[p], ref_state[p], err_msg=f"pose {p}, {npw} nodes per warp")
-    assert m.graph_nodes_per_warp(-1) == 4
+    # the default: 2 with the graph on the tensor cores (BF16), 4 on the CUDA cores (FP32); it follows the
+    # graph mode while the caller has not chosen a value
+    assert m.graph_nodes_per_warp(-1) == (2 if dtype == "bf16" else 4)
+    m.graph_tensor_cores(0 if dtype == "bf16" else 1)
+    assert m.graph_nodes_per_warp() == (4 if dtype == "bf16" else 2)
+    m.graph_tensor_cores(-1)
+    assert m.graph_nodes_per_warp() == (2 if dtype == "bf16" else 4)
     with pytest.raises(F.FusionError):
         m.graph_nodes_per_warp(3)
     m.close()
