@@ -127,14 +127,43 @@ __device__ __forceinline__ float selu(float x) {
     return x > 0.f ? scale * x : scale * alpha * expm1f(x);
 }
 
+constexpr int kHeadThreads = 512;
+
 // One dense layer of the head for one pose, all threads of the CTA: out[o] = act(b[o] + sum_k in[k] W[o][k])
 // (weights stored transposed, [in][out]); act 0 = none, 1 = ReLU, 2 = SELU; `res` adds in[o] after the
-// activation.  `in` and `out` are distinct shared-memory buffers.
+// activation.  `in` and `out` are distinct shared-memory buffers.  A narrow layer splits its inputs into ks
+// contiguous ranges (ks = 2, 4 or 8, as many as the CTA's threads allow), summed by different threads and
+// added in range order after the bias, so its chains of dependent multiply-adds (and weight loads) are ks
+// times shorter; the order depends only on the layer's shape.
 __device__ void head_layer(const float *in, int fin, float *out, int fout, const float *wt, const float *bias,
                            int act, bool res) {
-    for (int o = threadIdx.x; o < fout; o += blockDim.x) {
+    __shared__ float part[kHeadThreads];
+    int ks = 1;
+    while (ks < 8 && fout * ks * 2 <= (int)blockDim.x) ks *= 2;
+    if (ks == 1) {
+        for (int o = threadIdx.x; o < fout; o += blockDim.x) {
+            float s = bias[o];
+            for (int k = 0; k < fin; ++k) s = fmaf(wt[(size_t)k * fout + o], in[k], s);
+            if (act == 1) s = fmaxf(s, 0.f);
+            else if (act == 2) s = selu(s);
+            out[o] = res ? in[o] + s : s;
+        }
+        __syncthreads();
+        return;
+    }
+    const int chunk = (fin + ks - 1) / ks;
+    if ((int)threadIdx.x < fout * ks) {
+        const int o = threadIdx.x % fout, q = threadIdx.x / fout;
+        const int k1 = min(fin, (q + 1) * chunk);
+        float s = 0.f;
+        for (int k = q * chunk; k < k1; ++k) s = fmaf(wt[(size_t)k * fout + o], in[k], s);
+        part[q * fout + o] = s;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < fout) {
+        const int o = threadIdx.x;
         float s = bias[o];
-        for (int k = 0; k < fin; ++k) s = fmaf(wt[(size_t)k * fout + o], in[k], s);
+        for (int q = 0; q < ks; ++q) s += part[q * fout + o];
         if (act == 1) s = fmaxf(s, 0.f);
         else if (act == 2) s = selu(s);
         out[o] = res ? in[o] + s : s;
@@ -142,9 +171,6 @@ __device__ void head_layer(const float *in, int fin, float *out, int fout, const
     __syncthreads();
 }
 
-// Coherent Fusion: fusion layers on [cnn, sg].  Mid-level: each latent through its branch layers (SELU
-// after each), the two results appended after the latents, then the fusion layers.  Late: each latent
-// through its own affinity stack (ReLU between, last linear), the mean of the two.
 // Ask L2 for the CTA's share of a weight matrix's 128-byte lines (the head's weights, used by every CTA, are
 // usually out of L2 after the convolutions' streams; each CTA otherwise walks them from DRAM in dependent rounds).
 __device__ __forceinline__ void prefetch_share(const float *w, size_t n) {
@@ -154,7 +180,10 @@ __device__ __forceinline__ void prefetch_share(const float *w, size_t n) {
         asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(w) + q * 128));
 }
 
-__global__ void __launch_bounds__(256) head_kernel(HeadArgs a) {
+// Coherent Fusion: fusion layers on [cnn, sg].  Mid-level: each latent through its branch layers (SELU
+// after each), the two results appended after the latents, then the fusion layers.  Late: each latent
+// through its own affinity stack (ReLU between, last linear), the mean of the two.
+__global__ void __launch_bounds__(kHeadThreads) head_kernel(HeadArgs a) {
     __shared__ float v[3][kHeadMaxWidth];
     const int p = blockIdx.x;
     const int fin0 = a.Dc + a.G;
@@ -244,7 +273,7 @@ void launch_dense_reduce(const DenseArgs &a, cudaStream_t s) {
 }
 
 void launch_head(const HeadArgs &a, cudaStream_t s) {
-    head_kernel<<<a.B, 256, 0, s>>>(a);
+    head_kernel<<<a.B, kHeadThreads, 0, s>>>(a);
 }
 
 }  // namespace fusion
