@@ -33,9 +33,11 @@ __global__ void amax_per_pose_kernel(const __nv_bfloat16 *x, size_t per_pose, fl
     if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<unsigned *>(amax + b), __float_as_uint(m));
 }
 
+// The quantizers take the poses last to first: the producer wrote them first to last, so the last ones are
+// still in L2, and the quantized first poses, which the next convolution reads first, stay there for it.
 __global__ void quantize_per_pose_kernel(const __nv_bfloat16 *x, uint8_t *q, size_t per_pose, const float *amax,
                                          float *scale) {
-    const int b = blockIdx.y;
+    const int b = gridDim.y - 1 - blockIdx.y;
     const float am = amax[b];
     const float s = am > 0.f ? am / kE4M3Max : 1.f;
     const float inv = 1.f / s;
@@ -62,7 +64,7 @@ __global__ void quantize_per_pose_kernel(const __nv_bfloat16 *x, uint8_t *q, siz
 // block's writes form runs of consecutive x.
 __global__ void quantize_blocked_kernel(const __nv_bfloat16 *x, uint8_t *q, int n, int C, const float *amax,
                                         float *scale) {
-    const int b = blockIdx.y;
+    const int b = gridDim.y - 1 - blockIdx.y;       // last pose first, as in quantize_per_pose_kernel
     const float am = amax[b];
     const float s = am > 0.f ? am / kE4M3Max : 1.f;
     const float inv = 1.f / s;
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(256) quantize_fold_fp8_kernel(const __nv_bfloa
                                                                  int p, const float *amax, float *scale, int blocked) {
     extern __shared__ __align__(16) uint8_t s_code[];     // [kFoldRows][n][20] (19 channels + pad)
     const int rows = B * n * n;
-    const int r0 = blockIdx.x * kFoldRows;
+    const int r0 = (gridDim.x - 1 - blockIdx.x) * kFoldRows;   // last rows first, as in quantize_per_pose_kernel
     const int nr = min(kFoldRows, rows - r0);
     const int nn = n * n;
     for (int e = threadIdx.x; e < nr * n * 3; e += blockDim.x) {
