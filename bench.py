@@ -598,7 +598,11 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(desc, W, batch, 1)
 
-    stream = torch.cuda.current_stream()
+    # a stream of our own, made current: the model launches on it (a NULL handle, torch's legacy default stream,
+    # would make the model create a stream of its own), so the L2 flush, the timing events and the model's work
+    # are ordered on one stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     model = F.Model(desc, blob, max_poses=B, max_atoms=1200, max_degree=64, stream=stream.cuda_stream)
     devb = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in batch.items()}
     out = torch.empty(B, dtype=torch.float32, device="cuda")

@@ -71,7 +71,8 @@ def run(args):
     batches = pack_by_atoms(sizes, args.max_batch, args.max_batch * 700)
     packed = [poses.pack([pool[i] for i in b]) for b in batches]
     dev = [{k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in pb.items()} for pb in packed]
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()          # non-NULL, so the model launches on it and the events order with it
+    torch.cuda.set_stream(stream)
     m = F.Model(desc, blob, max_poses=args.max_batch, max_atoms=1200, stream=stream.cuda_stream)
     out = torch.empty(args.max_batch, device="cuda")
     base = {"workload": f"{len(pool)} poses = {args.groups} ligands x 10 rigid poses, ligands log-normal "
