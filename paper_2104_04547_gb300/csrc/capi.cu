@@ -1045,8 +1045,6 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
         sg_mark(3);
         return FUSION_OK;
     };
-    if (!m->serial_branches) RC(graph_branch());
-
     VoxArgs va{off_d, B, d.grid_n, d.support, d.max_atoms, m->grid, m->grid_cx,
                m->bf16 ? 1 : 0, m->grid_fold, bf16_blocked_in(m, 0) ? 1 : 0, m->cell_row, m->atom_rec,
                m->fp8 ? m->amax : nullptr};
@@ -1055,6 +1053,9 @@ static int enqueue_forward(fusion_model *m, int B, int A, const int32_t *A_dev, 
     launch_voxelize(va, st);
     RC(check_launch("voxelize"));
     map[1] = ei; mark(st);
+    // the graph branch is enqueued after voxelize, so that voxelize (on the critical path) takes the SMs first:
+    // measured on the 64-pose batch, voxelize 0.186 -> 0.158 ms in the step, the whole call unchanged
+    if (!m->serial_branches) RC(graph_branch());
 
     // 3D-CNN
     const void *x = m->grid;
