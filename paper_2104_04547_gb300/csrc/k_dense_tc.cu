@@ -8,11 +8,12 @@
 // order reduction over the splits (shared with the SIMT path) adds bias and ReLU.  The split
 // boundaries depend on K and the output width only, so a pose's result does not depend on its batch.
 //
-// Operands: both matrices are K-major in global memory ([rows][K] bf16).  A 3-D tensor-map view
-// (8 elements, rows, K / 8) with box (8, rows of the tile, 8) lands each 64-wide K stage in shared
-// memory as [k-slice of 8][row][8 elements]: the K-major, no-swizzle core-matrix layout (8 rows x 16
-// bytes contiguous, 8-row groups 128 bytes apart, k-slices one tile apart) the MMA descriptors read.
-// Rows beyond the matrix and K beyond its end are zero-filled by TMA.
+// Operands: both matrices are K-major in global memory ([rows][K] bf16).  A 2-D tensor map with a box of
+// 64 elements (128 bytes) x the tile's rows and 128-byte swizzling lands each 64-wide K stage in shared
+// memory as rows of 128 bytes whose 16-byte chunks are permuted by the row index mod 8: the K-major
+// 128-byte-swizzle layout of the MMA descriptors (8-row atoms of 1 KB, 1 KB apart; a K step of 16 moves the
+// start address 32 bytes along the row).  Each TMA request then moves whole 128-byte rows.  Rows beyond the
+// matrix and K beyond its end are zero-filled by TMA.
 //
 // Roles: warp 0 lane 0 issues the TMA loads into a ring of stages; warp 1 owns tensor memory and
 // its lane 0 issues 4 MMAs (K = 16 each) per stage; warps 2..5 (one per tensor-memory lane quarter)
@@ -39,6 +40,23 @@ constexpr uint32_t kBBytes = kBN * kBK * 2;
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr int kThreads = 192;
 constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
+
+// 2-D tiled TMA load into shared memory, completing on `bar` (coordinates: K element, row).
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, uint64_t *bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            tc::smem_u32(dst)),
+        "l"(tmap), "r"(tc::smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major with 128-byte swizzling (layout type 2 in bits 61..63): rows of
+// 128 bytes, 8-row atoms 1024 bytes apart (stride byte offset), the leading byte offset unused (1); the
+// tile starts on a 1024-byte boundary, so the base-offset field is 0.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
 
 struct TcArgs {
     float *part;          // [splits][B][N]
@@ -87,9 +105,9 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
             if (!tc::mbar_wait(&empty[st], ((it / kStages) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
             tc::mbar_expect_tx(&full[st], kStageBytes);
             unsigned char *sa = smem + st * kStageBytes;
-            const int ks = (kbeg + it * kBK) / 8;
-            tc::tma_load_3d(sa, &tw, &full[st], 0, m0, ks);
-            tc::tma_load_3d(sa + kABytes, &tx, &full[st], 0, b0, ks);
+            const int kk = kbeg + it * kBK;
+            tma_load_2d(sa, &tw, &full[st], kk, m0);
+            tma_load_2d(sa + kABytes, &tx, &full[st], kk, b0);
             ++issued;
         }
     } else if (warp == 1 && lane == 0) {
@@ -100,13 +118,13 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const __grid_cons
             if (!tc::mbar_wait(&full[st], (it / kStages) & 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
             tc::tc_fence_after();
             const uint32_t sa = a0 + st * kStageBytes;
-            // k-slices of 8 are kBM * 16 (A) and kBN * 16 (B) bytes apart; an MMA takes two of them
-            const uint64_t ad = tc::desc_kmajor(sa, kBM * 16, 128);
-            const uint64_t bd = tc::desc_kmajor(sa + bofs, kBN * 16, 128);
+            // 128-byte-swizzled K-major tiles: 8-row atoms 1 KB apart; MMA j reads K 16 j .. 16 j + 15, 32 bytes
+            // into each row (the start-address field counts 16-byte units)
+            const uint64_t ad = desc_sw128(sa);
+            const uint64_t bd = desc_sw128(sa + bofs);
 #pragma unroll
             for (int j = 0; j < kBK / 16; ++j)
-                tc::mma_bf16(tbase, ad + (uint64_t)(j * 2 * kBM), bd + (uint64_t)(j * 2 * kBN), IDESC,
-                             (it > 0 || j > 0) ? 1u : 0u);
+                tc::mma_bf16(tbase, ad + (uint64_t)(j * 2), bd + (uint64_t)(j * 2), IDESC, (it > 0 || j > 0) ? 1u : 0u);
             tc::mma_commit(&empty[st]);
         }
         tc::mma_commit(acc_full);
@@ -164,16 +182,16 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// [rows][K] bf16 as the 3-D view (8 elements, rows, K / 8), box (8, box_rows, 8).
+// [rows][K] bf16 as a 2-D map, box (64 elements, box_rows), 128-byte swizzling.
 int encode_kmajor(CUtensorMap *map, const void *base, int rows, int K, int box_rows) {
     auto enc = get_encode();
     if (!enc) return -2;
-    cuuint64_t dims[3] = {8, (cuuint64_t)rows, (cuuint64_t)(K / 8)};
-    cuuint64_t strides[2] = {(cuuint64_t)K * 2, 16};
-    cuuint32_t box[3] = {8, (cuuint32_t)box_rows, 8};
-    cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : (int)r;
 }
