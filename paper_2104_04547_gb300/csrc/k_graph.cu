@@ -158,6 +158,38 @@ __device__ __forceinline__ bool cand_run(const CellList &cl, int c, int r, int &
     return true;
 }
 
+// The query's candidates as one sequence: the 9 runs in order, each run's atoms in cell order.  Lane r < 9
+// computes run r; on return every lane holds its run's first position (q0) and the run's offset in the
+// sequence (pre, an exclusive prefix over the runs), and the sequence's length is returned.  Candidate idx
+// of the sequence lies in the last run r with pre_r <= idx (empty runs share the next run's offset).
+__device__ __forceinline__ int cand_seq(const CellList &cl, int c, int lane, int &q0, int &pre) {
+    int len = 0;
+    q0 = 0;
+    if (lane < 9) {
+        int a, b;
+        if (cand_run(cl, c, lane, a, b)) {
+            q0 = a;
+            len = b - a;
+        }
+    }
+    int incl = len;
+    for (int o = 1; o < 16; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    pre = incl - len;
+    return __shfl_sync(0xffffffffu, incl, 8);
+}
+
+// Position in cl.sorted of candidate idx of the sequence cand_seq described (q0, pre: this lane's values).
+__device__ __forceinline__ int cand_at(int idx, int q0, int pre) {
+    int r = 0;
+#pragma unroll
+    for (int t = 1; t < 9; ++t)
+        if (__shfl_sync(0xffffffffu, pre, t) <= idx) r = t;
+    return __shfl_sync(0xffffffffu, q0, r) + (idx - __shfl_sync(0xffffffffu, pre, r));
+}
+
 // Count pass: a warp per query atom, its lanes over the candidates of the 27 neighbouring cells.
 __global__ void __launch_bounds__(kThreads) radius_count_kernel(GraphArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -175,15 +207,17 @@ __global__ void __launch_bounds__(kThreads) radius_count_kernel(GraphArgs a) {
     for (int i = i0 + warp; i < i1; i += kThreads / 32) {
         const float xi = cl.sx[i], yi = cl.sy[i], zi = cl.sz[i];
         int d0 = 0, d1 = 0;
-        for (int r = 0; r < 9; ++r) {
-            int q0, q1;
-            if (!cand_run(cl, cl.cell[i], r, q0, q1)) continue;
-            for (int q = q0 + lane; q < q1; q += 32) {
+        int q0r, prer;
+        const int total = cand_seq(cl, cl.cell[i], lane, q0r, prer);
+        for (int base = 0; base < total; base += 32) {
+            const int q = cand_at(base + lane, q0r, prer);    // every lane takes part in the shuffles
+            if (base + lane < total) {
                 const int j = cl.sorted[q];
-                if (j == i) continue;
-                const float s = dist2_rn(xi, yi, zi, cl.sx[j], cl.sy[j], cl.sz[j]);
-                if (s < c2) ++d0;
-                else if (s < n2) ++d1;
+                if (j != i) {
+                    const float s = dist2_rn(xi, yi, zi, cl.sx[j], cl.sy[j], cl.sz[j]);
+                    if (s < c2) ++d0;
+                    else if (s < n2) ++d1;
+                }
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -223,12 +257,18 @@ __global__ void __launch_bounds__(kThreads) radius_scan_kernel(GraphArgs a) {
     }
 }
 
-// Sort row[0..n) (distinct atom indices) ascending by the warp: each lane ranks up to kRankPerLane elements
-// against the whole row, then all write after all have read; longer rows fall back to one lane's insertion
-// sort.
+// Sort row[0..n) (distinct atom indices) ascending by the warp into dst[0..n) (dst == row: in place): each
+// lane ranks up to kRankPerLane elements against the whole row, then all write after all have read; longer
+// rows (only ever sorted in place) fall back to one lane's insertion sort.
 constexpr int kRankPerLane = 4;
-__device__ void warp_sort_row(int32_t *row, int n, int lane) {
-    if (n <= 1) return;
+constexpr int kRowSmem = 32 * kRankPerLane;    // rows packed in shared memory (the fill pass)
+__device__ void warp_sort_row(int32_t *row, int n, int lane, int32_t *dst) {
+    if (n <= 0) return;
+    if (n == 1) {
+        if (lane == 0 && dst != row) dst[0] = row[0];
+        __syncwarp();
+        return;
+    }
     if (n > 32 * kRankPerLane) {
         if (lane == 0)
             for (int u = 1; u < n; ++u) {
@@ -255,14 +295,16 @@ __device__ void warp_sort_row(int32_t *row, int n, int lane) {
     __syncwarp();
 #pragma unroll
     for (int t = 0; t < kRankPerLane; ++t)
-        if (lane + 32 * t < n) row[rank[t]] = val[t];
+        if (lane + 32 * t < n) dst[rank[t]] = val[t];
     __syncwarp();
 }
 
-// Fill pass: a warp per query atom writes its neighbours into the row the scan placed (hits in candidate order,
-// packed by ballot), then sorts each row by neighbour index so the output is canonical.
+// Fill pass: a warp per query atom packs its neighbours by ballot in candidate order (in shared memory while a
+// row has at most kRowSmem entries, else in place in the row the scan placed), then sorts each row by
+// neighbour index into its place, so the output is canonical.
 __global__ void __launch_bounds__(kThreads) radius_fill_kernel(GraphArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int32_t s_rows[kThreads / 32][2][kRowSmem];   // each warp's two rows while they are short
     const int p = blockIdx.x / kGraphSplit, part = blockIdx.x % kGraphSplit;
     const int a0 = a.atom_off[p];
     const int N = a.atom_off[p + 1] - a0;
@@ -280,32 +322,34 @@ __global__ void __launch_bounds__(kThreads) radius_fill_kernel(GraphArgs a) {
         int32_t *r0 = a.col[0] + a.beg[0][a0 + i];
         int32_t *r1 = a.col[1] + a.beg[1][a0 + i];
         const float xi = cl.sx[i], yi = cl.sy[i], zi = cl.sz[i];
+        // rows of at most kRowSmem entries are packed and sorted in this warp's shared-memory rows, longer
+        // ones in place in global memory
+        int32_t *w0 = n0 <= kRowSmem ? s_rows[warp][0] : r0;
+        int32_t *w1 = n1 <= kRowSmem ? s_rows[warp][1] : r1;
         int k0 = 0, k1 = 0;
-        for (int r = 0; r < 9; ++r) {
-            int q0, q1;
-            if (!cand_run(cl, cl.cell[i], r, q0, q1)) continue;
-            for (int qb = q0; qb < q1; qb += 32) {
-                const int q = qb + lane;
-                bool h0 = false, h1 = false;
-                int j = 0;
-                if (q < q1) {
-                    j = cl.sorted[q];
-                    if (j != i) {
-                        const float s = dist2_rn(xi, yi, zi, cl.sx[j], cl.sy[j], cl.sz[j]);
-                        h0 = s < c2;
-                        h1 = !h0 && s < n2;
-                    }
+        int q0r, prer;
+        const int total = cand_seq(cl, cl.cell[i], lane, q0r, prer);
+        for (int base = 0; base < total; base += 32) {
+            const int q = cand_at(base + lane, q0r, prer);
+            bool h0 = false, h1 = false;
+            int j = 0;
+            if (base + lane < total) {
+                j = cl.sorted[q];
+                if (j != i) {
+                    const float s = dist2_rn(xi, yi, zi, cl.sx[j], cl.sy[j], cl.sz[j]);
+                    h0 = s < c2;
+                    h1 = !h0 && s < n2;
                 }
-                const unsigned b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
-                if (h0 && k0 + __popc(b0 & below) < n0) r0[k0 + __popc(b0 & below)] = a0 + j;
-                if (h1 && k1 + __popc(b1 & below) < n1) r1[k1 + __popc(b1 & below)] = a0 + j;
-                k0 += __popc(b0);
-                k1 += __popc(b1);
             }
+            const unsigned b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
+            if (h0 && k0 + __popc(b0 & below) < n0) w0[k0 + __popc(b0 & below)] = a0 + j;
+            if (h1 && k1 + __popc(b1 & below) < n1) w1[k1 + __popc(b1 & below)] = a0 + j;
+            k0 += __popc(b0);
+            k1 += __popc(b1);
         }
         __syncwarp();
-        warp_sort_row(r0, n0, lane);
-        warp_sort_row(r1, n1, lane);
+        warp_sort_row(w0, n0, lane, r0);
+        warp_sort_row(w1, n1, lane, r1);
     }
 }
 
