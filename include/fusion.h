@@ -246,6 +246,17 @@ int fusion_last_timings(fusion_model *m, float *out, int32_t n);
                                             for FP32 ones.  The message sums stay in their order either way.
                                             Drops captured graphs.  Any dtype */
 
+#define FUSION_OPT_CONV_STRIDE2_SPLIT 7   /* tensor-core convs: value 1 (the default, also -1) = a stride-2
+                                             layer after the first with an even input size reads its input
+                                             parity-split (the previous layer's epilogue, or the FP8
+                                             quantizer, stores the 8 sub-grids of one coordinate parity
+                                             apart, each channel-blocked), so each parity phase's halo is one
+                                             TMA box of whole W-lines; 0 = it reads NDHWC through the TMA
+                                             element stride of 2.  The MMAs and their order are the same, so
+                                             scores and conv maps are the same in both modes.  Re-plans the
+                                             layers and drops captured graphs; FUSION_EUNSUPPORTED on the
+                                             FP32 path */
+
 /* Set a runtime option of a model (FUSION_OPT_*). */
 int fusion_set_option(fusion_model *m, int32_t option, int64_t value);
 

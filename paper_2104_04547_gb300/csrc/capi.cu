@@ -297,6 +297,7 @@ struct fusion_model {
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr, cnn_join_ev = nullptr, ev_sg[4] = {};
     bool use_graph = false;                       // replay captured CUDA graphs, one per batch size
     int group_mode = -1;                          // conv output slices per MMA: -1 default per layer, or 1, 2, 4
+    bool split2 = true;                           // stride-2 layers read a parity-split input where they can
     int sg_npw = 4;                               // graph convolution: nodes per warp (1, 2, 4, 8)
     bool sg_npw_set = false;                      // chosen by the caller or the autotuner (else the default)
     bool serial_branches = false;                 // both branches on the grid stream, one after the other
@@ -308,6 +309,7 @@ struct fusion_model {
 
     // last call
     int last_B = 0;
+    bool last_split2 = true;                      // the conv maps' layout of the last call
     std::vector<int32_t> last_off, last_nlig;
     const void *last_conv_out[FUSION_MAX_CONV] = {};
     const float *last_h = nullptr;
@@ -674,21 +676,35 @@ int alloc_workspace(fusion_model *m) {
 
 }  // namespace
 
-// FP8 inputs of the stride-1 layers are stored channel-blocked (whole W-lines per TMA box row); the
-// stride-2 layers read NDHWC, since their halos step through x by 2.
+// FP8 inputs of the stride-1 layers are stored channel-blocked (whole W-lines per TMA box row), those of
+// the stride-2 layers parity-split (fp8_split; a first layer and an odd size read NDHWC with the TMA
+// element stride).
 // Nodes per warp by default: 4 where the CUDA-core graph shares each weight load over them, 2 where only the
 // message sums use them (the graph on the tensor cores; measured fastest on the 64-pose calls).
 static int default_npw(const fusion_model *m) { return m->sg_tc ? 2 : 4; }
 
 static bool fp8_blocked(const fusion_model *m, int i) { return m->fp8 && m->d.conv[i].stride == 1; }
 
+// A stride-2 layer after the first reads its input parity-split when the size is even: the blocked layout
+// of each of the 8 sub-grids of voxels of one coordinate parity, so that each parity phase's halo is one
+// plain TMA box of whole W-lines instead of single voxels at an element stride of 2.
+// (FUSION_OPT_CONV_STRIDE2_SPLIT 0 keeps them NDHWC.)
+static bool split_in(const fusion_model *m, int i, bool on) {
+    return on && i > 0 && i < m->d.n_conv && m->d.conv[i].stride == 2 && m->conv[i].n_in % 2 == 0;
+}
+static bool fp8_split(const fusion_model *m, int i) { return m->fp8 && split_in(m, i, m->split2); }
+static bool bf16_split_in(const fusion_model *m, int i, bool on) { return m->bf16 && !m->fp8 && split_in(m, i, on); }
+
 // BF16 model: layer i reads its input in place, channel-blocked when it is a stride-1 layer and that
 // input is a conv output (the previous layer then stores it so) or the folded grid.
 static bool bf16_blocked_in(const fusion_model *m, int i) {
     return m->bf16 && !m->fp8 && i < m->d.n_conv && m->d.conv[i].stride == 1 && (i > 0 || m->grid_fold >= 0);
 }
-// Layout of conv layer l's bf16 output.
-static bool conv_out_blocked(const fusion_model *m, int l) { return bf16_blocked_in(m, l + 1); }
+// Layout of conv layer l's bf16 output: 0 NDHWC, 1 channel-blocked, 2 parity-split (with stride-2 inputs
+// split when `split`).
+static int conv_out_blocked(const fusion_model *m, int l, bool split) {
+    return bf16_blocked_in(m, l + 1) ? 1 : bf16_split_in(m, l + 1, split) ? 2 : 0;
+}
 
 // FP8: quantize layer i's bf16 input xb per pose into m->qbuf, in the layout its conv plan reads.
 static void quantize_conv_input(fusion_model *m, int i, const void *xb, int B, cudaStream_t st) {
@@ -696,8 +712,8 @@ static void quantize_conv_input(fusion_model *m, int i, const void *xb, int B, c
     const Shape si = conv_out(d, i);
     if (i == 0 && m->fp8_fold >= 0)
         launch_quantize_fold_fp8(xb, m->qbuf, B, d.grid_n, m->fp8_fold, m->amax, m->qscale, fp8_blocked(m, i) ? 1 : 0, st);
-    else if (fp8_blocked(m, i))
-        launch_quantize_blocked(xb, m->qbuf, B, si.n, m->conv[i].cx_in, m->amax, m->qscale, st);
+    else if (fp8_blocked(m, i) || fp8_split(m, i))
+        launch_quantize_blocked(xb, m->qbuf, B, si.n, m->conv[i].cx_in, m->amax, m->qscale, fp8_split(m, i) ? 1 : 0, st);
     else
         launch_quantize_per_pose(xb, m->qbuf, B, (size_t)si.n * si.n * si.n * m->conv[i].cx_in, m->amax, m->qscale, st);
 }
@@ -729,8 +745,8 @@ static ConvTcSpec conv_spec(fusion_model *m, int i) {
     sp.group = m->group_mode;
     sp.fold = i != 0 ? 0 : m->grid_fold >= 0 ? 1 : m->fp8_fold >= 0 ? 2 : 0;
     if (sp.fold == 2) sp.cin_pad = 64;
-    sp.blocked = (fp8_blocked(m, i) || bf16_blocked_in(m, i)) ? 1 : 0;
-    sp.out_blocked = conv_out_blocked(m, i) ? 1 : 0;
+    sp.blocked = (fp8_blocked(m, i) || bf16_blocked_in(m, i)) ? 1 : (fp8_split(m, i) || bf16_split_in(m, i, m->split2)) ? 2 : 0;
+    sp.out_blocked = conv_out_blocked(m, i, m->split2);
     sp.res_blocked = bf16_blocked_in(m, i) ? 1 : 0;   // BF16: the residual source is the input itself
     return sp;
 }
@@ -1268,6 +1284,7 @@ int fusion_score(fusion_model *m, const fusion_poses *poses, int32_t n_poses, fl
         for (int k = 0; k < 3; ++k) cudaEventElapsedTime(&m->last_ms[12 + k], m->ev_sg[k], m->ev_sg[k + 1]);
     }
     m->last_B = B;
+    m->last_split2 = m->split2;
     m->last_off = off;
     if (!poses->on_device) m->last_nlig = nlig;
     else m->last_nlig.clear();
@@ -1311,6 +1328,22 @@ static std::vector<float> unblock(const std::vector<float> &t, int n, int C) {
             for (int x = 0; x < n; ++x)
                 for (int c = 0; c < 8; ++c)
                     o[(row * n + x) * C + cb * 8 + c] = t[((row * (C / 8) + cb) * n + x) * 8 + c];
+    return o;
+}
+
+// One pose's parity-split map [8][h][h][C / 8][h][8] (h = n / 2, sub-grid (z&1) 4 + (y&1) 2 + (x&1)) in
+// NDHWC order.
+static std::vector<float> unsplit(const std::vector<float> &t, int n, int C) {
+    std::vector<float> o(t.size());
+    const size_t h = (size_t)n / 2;
+    for (int z = 0; z < n; ++z)
+        for (int y = 0; y < n; ++y)
+            for (int x = 0; x < n; ++x) {
+                const size_t p = (size_t)(z & 1) * 4 + (y & 1) * 2 + (x & 1);
+                const size_t row = ((p * h + z / 2) * h + y / 2) * (C / 8);
+                for (int c = 0; c < C; ++c)
+                    o[(((size_t)z * n + y) * n + x) * C + c] = t[((row + c / 8) * h + x / 2) * 8 + c % 8];
+            }
     return o;
 }
 
@@ -1377,7 +1410,9 @@ int fusion_fetch_stage(fusion_model *m, int32_t stage, int32_t index, void *dst,
         if (!d.keep_stages && l != d.n_conv - 1) return fail(FUSION_EINVAL, "conv stages need keep_stages");
         std::vector<float> t;
         RC(copy_as_f32(m, m->last_conv_out[l], (size_t)p * (need / 4), need / 4, t));
-        if (conv_out_blocked(m, l)) t = unblock(t, conv_out(d, l + 1).n, conv_out(d, l + 1).c);
+        const int layout = conv_out_blocked(m, l, m->last_split2);
+        if (layout == 1) t = unblock(t, conv_out(d, l + 1).n, conv_out(d, l + 1).c);
+        if (layout == 2) t = unsplit(t, conv_out(d, l + 1).n, conv_out(d, l + 1).c);
         std::memcpy(dst, t.data(), need);
         return FUSION_OK;
     }
@@ -1465,6 +1500,21 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value) {
         if (!m->sg_npw_set) m->sg_npw = default_npw(m);
         drop_graphs(m);
         return FUSION_OK;
+    case FUSION_OPT_CONV_STRIDE2_SPLIT: {
+        if (value != -1 && value != 0 && value != 1)
+            return fail(FUSION_EINVAL, "stride-2 split takes -1 (default), 0 or 1");
+        if (!m->bf16) return fail(FUSION_EUNSUPPORTED, "the FP32 path has no tensor-core tiles");
+        const bool old = m->split2;
+        m->split2 = value != 0;
+        const int rc = plan_tensor_core_convs(m);
+        if (rc) {
+            m->split2 = old;
+            plan_tensor_core_convs(m);
+            return rc;
+        }
+        drop_graphs(m);
+        return FUSION_OK;
+    }
     case FUSION_OPT_CONV_SLICES_PER_MMA: {
         if (value != -1 && value != 1 && value != 2 && value != 4 && value != 8)
             return fail(FUSION_EINVAL, "slices per MMA must be -1 (default), 1, 2, 4 or 8");

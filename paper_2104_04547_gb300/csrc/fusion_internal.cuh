@@ -161,10 +161,14 @@ struct ConvTcSpec {
     int group;              // output slices per MMA (1, 2, 4; N = group x c_out); <= 0: default for the layer
     int fold;               // x-folded first-layer input: 0 no, 1 bf16 grid (VoxArgs::fold_pad = k / 2),
                             // 2 FP8 grid of launch_quantize_fold_fp8 (cin_pad 64, stored from x = -1)
-    int blocked;            // input stored channel-blocked, [pose][z][y][16-byte channel block][x][16 bytes],
+    int blocked;            // 1: input stored channel-blocked, [pose][z][y][16-byte channel block][x][16 bytes],
                             // so a halo row is hw x 16 contiguous bytes (one TMA box row per 16-byte block and
-                            // W-line instead of one per voxel); stride 1 only
-    int out_blocked;        // write the bf16 output channel-blocked, [pose][z][y][c_out / 8][x][8]
+                            // W-line instead of one per voxel); stride 1 only.  2: parity-split (stride 2, n_in
+                            // even, no fold): the blocked layout of each of the 8 sub-grids of one coordinate
+                            // parity, [pose][(z&1) 4 + (y&1) 2 + (x&1)][z/2][y/2][block][x/2][16 bytes], so that
+                            // each parity phase's halo is one plain box of whole W-lines
+    int out_blocked;        // write the bf16 output 1: channel-blocked, [pose][z][y][c_out / 8][x][8];
+                            // 2: parity-split, [pose][8][n_out/2][n_out/2][c_out / 8][n_out/2][8] (n_out even)
     int res_blocked;        // the bf16 residual source is channel-blocked, [pose][z][y][cres / 8][x][8]
 };
 // Build the plan; returns 0, or nonzero with a reason in `why`.
@@ -187,9 +191,11 @@ void launch_amax_per_pose(const void *x_bf16, int B, size_t per_pose, float *ama
 void launch_quantize_per_pose(const void *x_bf16, void *q_fp8, int B, size_t per_pose, const float *amax, float *scale,
                               cudaStream_t s);
 // The same codes for bf16 NDHWC activations [B][n]^3[C] (C a multiple of 16), stored channel-blocked:
-// [B][n][n][C / 16][n][16] (z, y, 16-channel block, x, channel in block).
+// [B][n][n][C / 16][n][16] (z, y, 16-channel block, x, channel in block).  split != 0 and n even: stored
+// parity-split (ConvTcSpec::blocked 2), [B][8][h][h][C / 16][h][16] with h = n / 2 and sub-grid
+// (z&1) 4 + (y&1) 2 + (x&1); an odd n is stored channel-blocked.
 void launch_quantize_blocked(const void *x_bf16, void *q_fp8, int B, int n, int C, const float *amax, float *scale,
-                             cudaStream_t s);
+                             int split, cudaStream_t s);
 
 // ---- radius graph ----------------------------------------------------------
 

@@ -26,6 +26,12 @@
 // of 4.7-4.9 us (measured on all SMs at once), and the tensor pipe waits that
 // much less at each chunk.  The halo buffer is then [z][y][K half][x][16 bytes]:
 // the descriptor's K-half offset is hw x 16 bytes and its W-line stride 2 hw x 16.
+// Parity-split inputs (stride 2, written so by the previous layer or the
+// quantizer): the blocked layout of each of the 8 sub-grids of voxels of one
+// coordinate parity.  Input voxel 2 o + p - pad of parity phase p is voxel
+// o + ((p - pad) >> 1) of sub-grid (p - pad) & 1, so a phase's halo is one
+// plain box of whole W-lines of that sub-grid instead of single voxels at the
+// TMA element stride of 2, and lands in the same buffer layout.
 //
 // Operand B (the weights) streams through a ring of shared-memory stages with
 // plain bulk copies.  The host arranges them per in-plane offset (ty, tx) as a
@@ -263,7 +269,14 @@ __global__ void __launch_bounds__(Roles<N, T, G>::THREADS, 1) conv3d_tc_kernel(c
                     if (!tc::mbar_wait(&a_empty[buf], ((ai / g.na) & 1) ^ 1, deadline, a.err, FUSION_ERR_TIMEOUT)) { fail(); break; }
                     tc::mbar_expect_tx(&a_full[buf], a_tx);
                     const int S = a.stride;
-                    if (a.blocked) {
+                    if (a.blocked == 2) {
+                        // parity-split input: input coordinate 2 o + p - pad = 2 (o + (p - pad) >> 1) + ((p - pad) & 1),
+                        // so the phase's halo is one plain box of the parity sub-grid (p - pad) & 1 per dimension,
+                        // starting (p - pad) >> 1 voxels from the tile (arithmetic shift: rounds down)
+                        const int qx = px - a.pad, qy = py - a.pad, qz = pz - a.pad;
+                        tc::tma_load_5d(sA + buf * a_bytes, &tmap, &a_full[buf], (x0 + (qx >> 1)) * CPR, 2 * c,
+                                        y0 + (qy >> 1), z0 + (qz >> 1), b * 8 + (qz & 1) * 4 + (qy & 1) * 2 + (qx & 1));
+                    } else if (a.blocked) {
                         // buffer [z][y][K half][x][16 bytes]: the chunk's two 16-byte channel blocks in one box
                         tc::tma_load_5d(sA + buf * a_bytes, &tmap, &a_full[buf], (x0 - a.pad + a.x_shift) * CPR, 2 * c,
                                         y0 - a.pad, z0 - a.pad, b);
@@ -395,11 +408,20 @@ __global__ void __launch_bounds__(Roles<N, T, G>::THREADS, 1) conv3d_tc_kernel(c
             //   NDHWC    ((b n + zz) n + yy) n + xx) C + c
             //   blocked  ((((b n + zz) n + yy) C/8 + c/8) n + xx) 8
             //   = b n^3 C + zz n^2 C + yy n C + (blocked ? xx 8 + c n : xx C + c)
+            // The parity-split output (out_blocked 2, read by a stride-2 layer) is the blocked layout of each of
+            // the 8 parity sub-grids of half the size, [pose][(z&1) 4 + (y&1) 2 + (x&1)][z/2][y/2][C/8][x/2][8]:
+            //   b n^3 C + ((y&1) 2 + (x&1)) h^3 C + (y/2) h C + (x/2) 8 + c h  +  (z&1) 4 h^3 C + (z/2) h^2 C
             const int n = a.n_out;
-            const size_t zstep_y = (size_t)n * n * N, zstep_r = (size_t)n * n * a.cres;
-            const size_t ybase = (size_t)b * n * zstep_y + (size_t)yy * n * N + (a.out_blocked ? xx * 8 : xx * N);
+            const bool split = a.out_blocked == 2;
+            const int hn = n >> 1;
+            const size_t hcube = (size_t)hn * hn * hn * N;
+            const size_t zstep_y = split ? (size_t)hn * hn * N : (size_t)n * n * N, zstep_r = (size_t)n * n * a.cres;
+            const size_t zpar_y = 4 * hcube;    // parity-split: the odd slices' sub-grids
+            const size_t ybase = split ? (size_t)b * n * n * n * N + (size_t)((yy & 1) * 2 + (xx & 1)) * hcube +
+                                             (size_t)(yy >> 1) * hn * N + (size_t)(xx >> 1) * 8
+                                       : (size_t)b * n * zstep_y + (size_t)yy * n * N + (a.out_blocked ? xx * 8 : xx * N);
             const size_t rbase = (size_t)b * n * zstep_r + (size_t)yy * n * a.cres + (a.res_blocked ? xx * 8 : xx * a.cres);
-            const int ycc = a.out_blocked ? n : 1, rcc = a.res_blocked ? n : 1;   // per channel
+            const int ycc = split ? hn : a.out_blocked ? n : 1, rcc = a.res_blocked ? n : 1;   // per channel
             if (a.residual && yy < a.n_out && xx < a.n_out) {
                 // ask L2 for the residual input this tile's stores will add, while its MMAs run (one line per
                 // voxel row of a 16-byte block when blocked, taken by the lane at the row's first voxel)
@@ -469,7 +491,8 @@ __global__ void __launch_bounds__(Roles<N, T, G>::THREADS, 1) conv3d_tc_kernel(c
                             }
                         }
                     }
-                    __nv_bfloat16 *const ydst = a.y + ybase + zz * zstep_y + (size_t)cc * ycc;
+                    const size_t zoff = split ? (size_t)(zz & 1) * zpar_y + (size_t)(zz >> 1) * zstep_y : zz * zstep_y;
+                    __nv_bfloat16 *const ydst = a.y + ybase + zoff + (size_t)cc * ycc;
                     const int ystep = 8 * ycc;
 #pragma unroll
                     for (int k4 = 0; k4 < 4; ++k4) {
@@ -775,8 +798,13 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     g.hd = T + ntmax - 1;
     g.hh = 16 + ntmax - 1;
     g.hw = 8 + ntmax - 1;
-    if (sp.blocked && stride != 1) {
-        snprintf(why, why_len, "a channel-blocked input needs stride 1");
+    if ((sp.blocked == 1 && stride != 1) || (sp.blocked == 2 && (stride != 2 || sp.n_in % 2 != 0 || sp.fold)) ||
+        sp.blocked < 0 || sp.blocked > 2) {
+        snprintf(why, why_len, "a channel-blocked input needs stride 1, a parity-split one stride 2 and an even size");
+        return -1;
+    }
+    if (sp.out_blocked < 0 || sp.out_blocked > 2 || (sp.out_blocked == 2 && sp.n_out % 2 != 0)) {
+        snprintf(why, why_len, "a parity-split output needs an even size");
         return -1;
     }
     g.plane_bytes = ((uint32_t)(g.hd * g.hh * g.hw) * 16 + 127) / 128 * 128;
@@ -855,7 +883,15 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     cuuint32_t box[5] = {(cuuint32_t)cpr, (cuuint32_t)(g.hw * stride), (cuuint32_t)(g.hh * stride),
                          (cuuint32_t)(g.hd * stride), 1};
     cuuint32_t estr[5] = {1, (cuuint32_t)stride, (cuuint32_t)stride, (cuuint32_t)stride, 1};
-    if (sp.blocked) {
+    if (sp.blocked == 2) {
+        // parity-split: dims (x' * cpr + channel in block, block, y', z', pose * 8 + parity), x' y' z' < n / 2;
+        // a box row is hw voxels x 16 bytes, and the element strides are 1
+        const cuuint64_t blocks = (cuuint64_t)sp.cin_pad / cpr, h = n / 2;
+        dims[0] = h * cpr; dims[1] = blocks; dims[2] = h; dims[3] = h; dims[4] = (cuuint64_t)sp.max_poses * 8;
+        strides[0] = h * 16; strides[1] = blocks * h * 16; strides[2] = strides[1] * h; strides[3] = strides[2] * h;
+        box[0] = (cuuint32_t)(g.hw * cpr); box[1] = 2; box[2] = (cuuint32_t)g.hh; box[3] = (cuuint32_t)g.hd; box[4] = 1;
+        for (int i = 0; i < 5; ++i) estr[i] = 1;
+    } else if (sp.blocked) {
         // dims (x * cpr + channel in block, block, y, z, pose); a box row is hw voxels x 16 bytes
         const cuuint64_t blocks = (cuuint64_t)sp.cin_pad / cpr;
         dims[0] = nx_in * cpr; dims[1] = blocks; dims[2] = n; dims[3] = n; dims[4] = (cuuint64_t)sp.max_poses;

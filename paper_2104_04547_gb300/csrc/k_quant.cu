@@ -61,9 +61,10 @@ __global__ void quantize_per_pose_kernel(const __nv_bfloat16 *x, uint8_t *q, siz
 
 // Channel-blocked output: item (voxel v, 16-channel block cb) reads 16 bf16 (32 bytes) and writes 16 codes
 // to [b][z][y][cb][x][16]; cb varies fastest across threads, so the reads are contiguous and each
-// block's writes form runs of consecutive x.
+// block's writes form runs of consecutive x.  split != 0 (n even, h = n / 2): the same blocks of each of the
+// 8 parity sub-grids, [b][(z&1) 4 + (y&1) 2 + (x&1)][z/2][y/2][cb][x/2][16], read by a stride-2 layer.
 __global__ void quantize_blocked_kernel(const __nv_bfloat16 *x, uint8_t *q, int n, int C, const float *amax,
-                                        float *scale) {
+                                        float *scale, int split) {
     const int b = gridDim.y - 1 - blockIdx.y;       // last pose first, as in quantize_per_pose_kernel
     const float am = amax[b];
     const float s = am > 0.f ? am / kE4M3Max : 1.f;
@@ -92,7 +93,16 @@ __global__ void quantize_blocked_kernel(const __nv_bfloat16 *x, uint8_t *q, int 
                 o16[hlf * 4 + e] = __nv_cvt_float2_to_fp8x2(make_float2(f.x * inv, f.y * inv), __NV_SATFINITE, __NV_E4M3);
             }
         }
-        *reinterpret_cast<uint4 *>(qb + ((row * ncb + cb) * n + xx) * 16) = out;
+        size_t dst;
+        if (split) {
+            const size_t h = (size_t)(n >> 1);
+            const int yy = (int)(row % n), zz = (int)(row / n);
+            const size_t p = (size_t)(zz & 1) * 4 + (yy & 1) * 2 + (xx & 1);
+            dst = ((((p * h + (zz >> 1)) * h + (yy >> 1)) * ncb + cb) * h + (xx >> 1)) * 16;
+        } else {
+            dst = ((row * ncb + cb) * n + xx) * 16;
+        }
+        *reinterpret_cast<uint4 *>(qb + dst) = out;
     }
 }
 
@@ -176,11 +186,12 @@ void launch_quantize_fold_fp8(const void *grid_bf16, void *q_fp8, int B, int n, 
 }
 
 void launch_quantize_blocked(const void *x_bf16, void *q_fp8, int B, int n, int C, const float *amax, float *scale,
-                             cudaStream_t s) {
+                             int split, cudaStream_t s) {
     const size_t items = (size_t)n * n * n * (C / 16);
     const unsigned gx = (unsigned)((items + 255) / 256 < 128 ? (items + 255) / 256 : 128);
     quantize_blocked_kernel<<<dim3(gx > 0 ? gx : 1, B), 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(x_bf16),
-                                                                    static_cast<uint8_t *>(q_fp8), n, C, amax, scale);
+                                                                    static_cast<uint8_t *>(q_fp8), n, C, amax, scale,
+                                                                    split && n % 2 == 0 ? 1 : 0);
 }
 
 void launch_amax_per_pose(const void *x_bf16, int B, size_t per_pose, float *amax, cudaStream_t s) {

@@ -45,6 +45,7 @@ FUSION_OPT_TEST_WAIT_TIMEOUT = 3
 FUSION_OPT_GRAPH_NODES_PER_WARP = 4
 FUSION_OPT_SERIAL_BRANCHES = 5
 FUSION_OPT_GRAPH_TENSOR_CORES = 6
+FUSION_OPT_CONV_STRIDE2_SPLIT = 7
 
 EXPORTED = ["fusion_weights_bytes", "fusion_create", "fusion_score", "fusion_destroy", "fusion_last_error",
             "fusion_stage_bytes", "fusion_fetch_stage", "fusion_last_timings", "fusion_cnn_dense_noalloc",
@@ -383,6 +384,10 @@ class Model:
         """1: graph steps' GRU and transforms on the tensor cores (three-term BF16 split); 0: FP32 CUDA
         cores; -1: the dtype's default (tensor cores for BF16 / FP8)."""
         fusion_set_option(self.handle, FUSION_OPT_GRAPH_TENSOR_CORES, int(on))
+
+    def conv_stride2_split(self, on=-1):
+        """1 / -1: stride-2 layers read a parity-split input (even sizes); 0: NDHWC at the TMA element stride."""
+        fusion_set_option(self.handle, FUSION_OPT_CONV_STRIDE2_SPLIT, int(on))
 
     def conv_slices_per_mma(self, mode):
         """-1: default per layer; 1, 2 or 4: output slices per MMA on every layer."""

@@ -37,6 +37,15 @@ def test_every_declared_symbol_is_exported(F):
         assert hasattr(lib, n), n
 
 
+def test_binding_constants_match_the_header(F):
+    src = open(os.path.join(ROOT, "include", "fusion.h")).read()
+    defs = dict(re.findall(r"#define\s+(FUSION_(?:OPT|STAGE)_[A-Z0-9_]+)\s+(-?\d+)", src))
+    assert len([k for k in defs if k.startswith("FUSION_OPT_")]) >= 7
+    for name, value in defs.items():
+        py = name if name.startswith("FUSION_OPT_") else name[len("FUSION_"):]   # stages: F.STAGE_*
+        assert getattr(F, py, None) == int(value), name
+
+
 def test_blob_size_matches_generator(F):
     for name in configs.MODELS:
         d = configs.model(name)
