@@ -264,7 +264,9 @@ int fusion_set_option(fusion_model *m, int32_t option, int64_t value);
  * fastest tile configuration (output slices per CTA, output slices per MMA,
  * kernel-offset groups per weight stage, weight stages) by timing
  * every configuration that fits shared memory on the given batch (scored once
- * first), then the graph convolution's nodes per warp (1, 2, 4, 8) by timing
+ * first); the sweep's winner replaces the layer's default only if, timed
+ * against it three more times in alternation, its best time is at least 2%
+ * under the default's.  Then the graph convolution's nodes per warp (1, 2, 4, 8) by timing
  * whole scoring calls of the batch, since that branch runs beside the
  * convolutions.  Every configuration sums each output in the same order, so
  * the scores do not change.  Replaces the layer plans and the graph schedule;

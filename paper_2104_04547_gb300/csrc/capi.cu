@@ -1595,8 +1595,6 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
         std::vector<int> Ts = co <= 32   ? std::vector<int>{16, 8, 4}
                               : co <= 64 ? std::vector<int>{8, 4}
                               : co == 128 ? std::vector<int>{4, 2} : std::vector<int>{2};
-        float best_ms = 1e30f;
-        int best[4] = {0, 0, 0, 0};
         auto prepare_input = [&]() {
             if (!m->fp8) return;
             // the FP8 input of layer i is re-derived from its bf16 input (the buffer holds another layer's)
@@ -1607,6 +1605,27 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
             launch_amax_per_pose(xb, B, per_pose, m->amax, st);
             quantize_conv_input(m, i, xb, B, st);
         };
+        // one untimed launch, then three timed back to back
+        auto time_plan = [&](ConvTcPlan &pl, float &ms) -> int {
+            prepare_input();
+            conv_tc_launch(pl, B, st);
+            CU(cudaEventRecord(e0, st));
+            for (int r = 0; r < 3; ++r) conv_tc_launch(pl, B, st);
+            CU(cudaEventRecord(e1, st));
+            CU(cudaStreamSynchronize(st));
+            RC(check_launch("autotune conv"));
+            ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            return FUSION_OK;
+        };
+        // the layer's default plan (the caller's slices-per-MMA mode, default tiles) is the one to beat
+        ConvTcPlan def;
+        {
+            char why[256] = {0};
+            if (conv_tc_plan(def, conv_spec(m, i), why, sizeof(why))) return fail(FUSION_ECUDA, why);
+        }
+        float best_ms = 1e30f;
+        int best[4] = {0, 0, 0, 0};
         for (int T : Ts)
             for (int group : {8, 4, 2, 1})
             for (int groups : {1, 2, 3, 4, 6})
@@ -1619,15 +1638,8 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
                     sp.nbs = nbs;
                     char why[256] = {0};
                     if (conv_tc_plan(trial, sp, why, sizeof(why))) continue;   // does not fit: skip
-                    prepare_input();
-                    conv_tc_launch(trial, B, st);
-                    CU(cudaEventRecord(e0, st));
-                    for (int r = 0; r < 3; ++r) conv_tc_launch(trial, B, st);
-                    CU(cudaEventRecord(e1, st));
-                    CU(cudaStreamSynchronize(st));
-                    RC(check_launch("autotune conv"));
                     float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
+                    RC(time_plan(trial, ms));
                     if (ms < best_ms) {
                         best_ms = ms;
                         best[0] = T;
@@ -1642,8 +1654,25 @@ int fusion_autotune(fusion_model *m, const fusion_poses *poses, int32_t n_poses)
         sp.groups_per_stage = best[1];
         sp.nbs = best[2];
         sp.group = best[3];
+        ConvTcPlan cand;
+        {
+            char why[256] = {0};
+            if (conv_tc_plan(cand, sp, why, sizeof(why))) return fail(FUSION_ECUDA, why);
+        }
+        // The sweep's winner among many close configurations is partly noise (measured: picks 2-3% slower
+        // than the default on the full-size residual layers): time it against the default three times
+        // more, alternating, and take it only if its best time is at least 2% under the default's.
+        float def_best = 1e30f, cand_best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            float ms = 0.f;
+            RC(time_plan(def, ms));
+            def_best = std::min(def_best, ms);
+            RC(time_plan(cand, ms));
+            cand_best = std::min(cand_best, ms);
+        }
+        ConvTcSpec chosen = cand_best < 0.98f * def_best ? sp : conv_spec(m, i);
         char why[256] = {0};
-        if (conv_tc_plan(m->tcplan[i], sp, why, sizeof(why))) return fail(FUSION_ECUDA, why);
+        if (conv_tc_plan(m->tcplan[i], chosen, why, sizeof(why))) return fail(FUSION_ECUDA, why);
     }
     drop_graphs(m);
 
