@@ -822,7 +822,12 @@ int conv_tc_plan(ConvTcPlan &plan, const ConvTcSpec &sp, char *why, size_t why_l
     // about 48 KB of weights per stage in a ring of two: each stage hand-off costs a fixed few
     // hundred cycles, and fewer, larger stages measured faster than deeper rings of smaller ones
     const uint32_t gbytes_max = (uint32_t)ntmax * c_out * 32;
-    g.groups_per_stage = sp.groups_per_stage > 0 ? sp.groups_per_stage : (int)(49152 / gbytes_max);
+    // stride 2: about 72 KB per stage, at most one parity phase's groups (a stage never spans phases).  Its
+    // small halos leave the room, and fewer weight copies per phase measured faster (full-size conv3, 64
+    // poses: 1.47 -> 1.39-1.40 ms BF16, 1.04 -> 1.00-1.01 ms FP8 with 6 groups instead of 4)
+    const uint32_t stage_target = stride == 2 ? 73728u : 49152u;
+    g.groups_per_stage = sp.groups_per_stage > 0 ? sp.groups_per_stage : (int)(stage_target / gbytes_max);
+    if (sp.groups_per_stage <= 0 && stride == 2 && g.groups_per_stage > ntmax * ntmax) g.groups_per_stage = ntmax * ntmax;
     if (g.groups_per_stage < 1) g.groups_per_stage = 1;
     g.stage_bytes = ((uint32_t)g.groups_per_stage * gbytes_max + 127) / 128 * 128;
     // output slices per MMA: by default the most (4, else 2) that fit, for stride 1.  Measured on the
